@@ -1,0 +1,314 @@
+"""Benchmark: steps/s of the density-matrix propagation step on one GB300.
+
+Workload (default): SCC frozen-nuclei hexagonal flake, 256 atoms x 4 orbitals
+(N = 1024), half filling, delta kick 1e-3 a.u. along x, dt = 0.2 a.u.  A step
+is one pass of the whole hot path: Mulliken charges, SCC potential and
+dipole, M = S^-1 H, X = M rho, leapfrog update (eq:leapfrog, eq:eomrho).
+
+The headline value is the reduced-precision form (the fastest form built);
+the FP64 form runs on the same trajectory as the accuracy reference (it is
+itself pinned to the CPU oracle by the parity tests) and as the speed
+baseline.  One JSON line is printed by rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "steps/s at N=1024/2048 orbitals: mixed-precision vs FP64 at fixed dipole error"
+WORKLOAD = ("SCC frozen-nuclei hexagonal flake, 256 atoms x 4 orbitals (N=1024), "
+            "half filling, kick 1e-3 a.u. along x, dt=0.2 a.u.")
+L2_FLUSH_BYTES = 256 << 20
+
+# algorithmic FLOPs per launch of each kernel of a frozen-nuclei step, as a function of N
+KERNEL_FLOPS = {
+    "gemm_M_f64": lambda N: 2 * N ** 3,
+    "gemm_Xre_f64": lambda N: 2 * N ** 3,
+    "gemm_Xim_f64": lambda N: 2 * N ** 3,
+    "gemm_dM_f32": lambda N: 2 * N ** 3,
+    "gemm_Xre_f32": lambda N: 4 * N ** 3,
+    "gemm_Xim_f32": lambda N: 2 * N ** 3,
+}
+# algorithmic bytes per launch of the O(N^2) kernels
+KERNEL_BYTES = {
+    # reads X (re, im; both halves once), rho_{n-1}, S; writes rho_{n+1} (+ operands)
+    "update_f64": lambda N: N * N * 8 * (2 + 2 + 1 + 2),
+    "update_f32": lambda N: N * N * (4 * 2 + 8 * 2 + 8 + 8 * 2 + 4 * 2),
+}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+def alu_peak_tflops(kind: str, sm_mhz: float) -> float:
+    """SIMT peaks from unit counts: 152 SMs x 128 FP32 lanes x 2 flop/FMA x clock;
+    FP64 at the GB300 nominal 1.25 TFLOP/s (its FP64 units are 1/64 of FP32)."""
+    if kind == "f32":
+        return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    return 1.25
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (clocks and throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r.split(",") for r in (getattr(self, "out", "") or "").strip().splitlines() if r.strip()]
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_form(B, torch, sysm, run, precision, steps, warmup, flush, stream):
+    """Ground state + kick, W warm-up steps, K timed steps (per-step events, L2
+    flushed between them).  Returns timing and the dipole trajectory."""
+    p = B.Propagator(sysm, run, precision, stream=stream.cuda_stream, history_cap=warmup + steps + 8)
+    try:
+        p.setup()
+        with torch.cuda.stream(stream):
+            p.step(warmup)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(steps)]
+            launches = 0
+            for k in range(steps):
+                flush.add_(1.0)                         # > L2: evicts the working set
+                ev[k][0].record(stream)
+                p.step(1)
+                ev[k][1].record(stream)
+                launches += B.tdb_last_launch_count(p.ctx)
+            torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        hist = B.tdb_dipole_history(p.ctx, warmup + steps)
+        # per-kernel times (events between the kernels of a step, same stream)
+        prof = {}
+        for _ in range(10):
+            flush.add_(1.0)
+            torch.cuda.synchronize()
+            for name, t in B.tdb_step_profiled(p.ctx):
+                prof.setdefault(name, []).append(t)
+        obs = p.observables()
+    finally:
+        p.close()
+    return dict(ms=ms, hist=hist, prof={k: float(np.mean(v)) for k, v in prof.items()}, obs=obs,
+                launches=launches)
+
+
+def e2e_run(B, sysm, run, precision, steps, warmup):
+    """End to end through the public API: per step the field is set from the host
+    (H2D), one step runs, and the observables with charges are read back (D2H)."""
+    p = B.Propagator(sysm, run, precision)
+    try:
+        p.setup()
+        from paper_1912_03174_gb300 import inputs as I
+        fld = B.make_field(I.Field(E0=0.0, omega=0.0))
+        for _ in range(warmup):
+            B.tdb_set_field(p.ctx, fld)
+            p.step(1)
+            p.observables()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            B.tdb_set_field(p.ctx, fld)
+            p.step(1)
+            p.observables(charges=True)
+        dt = time.perf_counter() - t0
+    finally:
+        p.close()
+    h2d = 88                                     # field parameters
+    d2h = 8 * 8 + 8 * 32 + 8 * sysm.n_atoms      # reductions + scalars + charges
+    return {"value": steps / dt, "unit": "steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+def cpu_baseline(sysm, run, n_steps):
+    """The CPU oracle as it stands, timed on this host's cores."""
+    from oracle import tdb_oracle as O
+    rho, gs, S, Sinv = O.setup(sysm, run)
+    O.propagate(sysm, run, rho, 1)                   # warm caches / BLAS threads
+    t0 = time.perf_counter()
+    O.propagate(sysm, run, rho, n_steps)
+    dt = time.perf_counter() - t0
+    # propagate() also evaluates observables of rho_0..rho_K: K+1 evaluations, K steps
+    return n_steps / dt
+
+
+def reference_arm(args, sysm, run, rank):
+    if rank != 0:
+        return
+    n = max(1, min(args.steps, 40))
+    cores = len(os.sched_getaffinity(0))
+    v = cpu_baseline(sysm, run, n)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
+            "steps": n, "warmup": 1, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": sysm.n_orb, "parallelism": "replicas"},
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"ground state untimed, then {n} oracle steps of the same workload"},
+            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--forms", default="fp64,fp32")
+    ap.add_argument("--atoms", type=int, default=256)
+    ap.add_argument("--cpu-steps", type=int, default=12)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    from paper_1912_03174_gb300 import inputs as I
+    sysm, run = I.flake_c2(n_atoms=args.atoms)
+
+    if args.impl == "reference":
+        reference_arm(args, sysm, run, rank)
+        return
+
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo", init_method="env://")
+    import __graft_entry__ as g
+    g.build()
+    from paper_1912_03174_gb300 import binding as B
+
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    forms = args.forms.split(",")
+    res = {}
+    with ClockSampler(local) as clk:
+        if dist:
+            dist.barrier()
+        for f in forms:
+            res[f] = run_form(B, torch, sysm, run, f, args.steps, args.warmup, flush, stream)
+        if dist:
+            dist.barrier()
+    clocks = clk.summary()
+
+    head = forms[-1]
+    r = res[head]
+    ms_step = float(np.mean(r["ms"]))
+    # max over ranks of the time per step (replicas run the same workload)
+    if dist:
+        t = torch.tensor([ms_step], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * 1000.0 / ms_step
+    ms64 = float(np.mean(res["fp64"]["ms"])) if "fp64" in res else None
+    err = None
+    if "fp64" in res and head != "fp64":
+        err = float(np.max(np.abs(r["hist"] - res["fp64"]["hist"])))
+    # dominant kernel of the headline form
+    name, t_ms = max(r["prof"].items(), key=lambda kv: kv[1])
+    peaks, src = _peaks()
+    N = sysm.n_orb
+    sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    if name in KERNEL_FLOPS:
+        kind = "f64" if name.endswith("f64") else "f32"
+        ach = KERNEL_FLOPS[name](N) / (t_ms * 1e-3) / 1e12
+        peak = alu_peak_tflops(kind, peaks.get("sm_max_mhz", 2070.0))
+        roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_source": f"derived from unit counts at {peaks.get('sm_max_mhz', 2070.0):.0f} MHz"
+                if kind == "f32" else "GB300 nominal FP64 1.25 TFLOP/s"}
+    else:
+        key = "update_f64" if head == "fp64" else "update_f32"
+        ach = KERNEL_BYTES[key](N) / (t_ms * 1e-3) / 1e9
+        roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": src}
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "bf16x3"}[head],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "precision": head, "parallelism": "replicas",
+                   "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)",
+                   "fp64_steps_per_s": (1000.0 / ms64) if ms64 else None,
+                   "speedup_vs_fp64": (ms64 / float(np.mean(r['ms']))) if ms64 else None,
+                   "max_dipole_err_vs_fp64_au": err,
+                   "kernel_ms": {f: res[f]["prof"] for f in forms}},
+        "roofline": roof,
+        "gpu_launches": int(r["launches"]),
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = len(os.sched_getaffinity(0))
+        v = cpu_baseline(sysm, run, args.cpu_steps)
+        line["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                                "sample": f"ground state untimed, then {args.cpu_steps} oracle steps "
+                                          f"of the same workload"}
+    if rank == 0:
+        line["e2e"] = e2e_run(B, sysm, run, head, min(args.steps, 100), args.warmup)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

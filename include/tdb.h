@@ -1,0 +1,198 @@
+/*
+ * tdb.h -- C ABI of the GB300 real-time TD-DFTB density-matrix propagator.
+ *
+ * The library propagates the one-body density matrix rho of a tight-binding
+ * (DFTB-form) system under the generalised Liouville-von Neumann equation of
+ * Bonafe et al., "A real-time time-dependent density functional tight-binding
+ * implementation for semiclassical excited state electron-nuclear dynamics
+ * and pump-probe spectroscopy simulations" (arXiv 1912.03174):
+ *
+ *   drho/dt = -i (S^-1 H rho - rho H S^-1) - (S^-1 D rho + rho D^T S^-1)   (eq:eomrho)
+ *
+ * with the leapfrog scheme rho_{n+1} = rho_{n-1} + 2 dt drho_n and an Euler
+ * first step (eq:leapfrog, Sec. 2.3), SCC Hamiltonian rebuild from Mulliken
+ * charges (eq:hscc, eq:hsccvext, eq:qmulik), the delta kick of eq:rhokick, the
+ * laser pulse of eq:pumpf, Ehrenfest forces (eq:forces) and velocity-Verlet
+ * nuclei (Sec. 2.3).  Units: Hartree atomic units throughout.
+ *
+ * Conventions for every call:
+ *  - Host pointers are read during the call only; the caller keeps ownership.
+ *    Device memory is owned by the context (or by the caller when a workspace
+ *    is passed to tdb_create; the library then never frees it).
+ *  - Matrices on the device are row-major, orbitals atom-major with
+ *    orbs_per_atom (1 or 4: s, px, py, pz) consecutive orbitals per atom.
+ *  - No call aborts or exits, and no call falls back to a CPU path.  Errors are
+ *    returned as tdb_status; tdb_last_error() gives a message for the calling
+ *    thread.  After TDB_ERR_NUMERIC or TDB_ERR_TIMEOUT a context is "sticky":
+ *    only tdb_observables, tdb_get_state, tdb_get_rho and tdb_destroy work.
+ *  - A context is thread-compatible, not thread-safe.  All GPU work of a
+ *    context runs on the stream given in tdb_params (NULL = a stream the
+ *    context creates).  tdb_step is asynchronous; calls that return host
+ *    data synchronise that stream.
+ */
+#ifndef TDB_H
+#define TDB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tdb_ctx tdb_ctx;
+
+typedef enum {
+    TDB_OK = 0,
+    TDB_ERR_ARG = 1,          /* invalid argument (NULL, size, range) */
+    TDB_ERR_STATE = 2,        /* call out of order (e.g. tdb_step before tdb_ground_state) */
+    TDB_ERR_CUDA = 3,         /* a CUDA runtime / library call failed */
+    TDB_ERR_NOT_SPD = 4,      /* overlap matrix S is not positive definite */
+    TDB_ERR_SCC_NOCONV = 5,   /* ground-state charge self-consistency did not converge */
+    TDB_ERR_UNSTABLE = 6,     /* dt * (spectral width of S^-1 H) >= 0.9: leapfrog unstable */
+    TDB_ERR_NUMERIC = 7,      /* NaN/Inf or invariant violation found by tdb_check */
+    TDB_ERR_TIMEOUT = 8,      /* a bounded device-side wait gave up */
+    TDB_ERR_NOMEM = 9,        /* device allocation failed or workspace too small */
+    TDB_ERR_UNSUPPORTED = 10  /* valid request this build does not implement */
+} tdb_status;
+
+/* Arithmetic of the per-step matrix products (eq:eomrho).  The density matrix
+ * master copy, charges, potentials, energies and forces are FP64 in every mode. */
+typedef enum {
+    TDB_FP64 = 0,     /* FP64 products (SIMT DFMA) */
+    TDB_FP32 = 1,     /* FP32 products (SIMT FFMA) on the deviation rho - rho_gs */
+    TDB_BF16X3 = 2    /* tcgen05 tensor cores: BF16 hi/lo split, 3 products, FP32 accumulate,
+                         on the deviation rho - rho_gs */
+} tdb_precision;
+
+/* The system (geometry and synthetic two-centre model).  Radial integrals:
+ *   hopping  V_k(r) =  eta_k * t0 * exp(-r / lam_H)
+ *   overlap  S_k(r) = -eta_k * s0 * exp(-r / lam_S),  k = ss-sigma, sp-sigma, pp-sigma, pp-pi
+ * combined by the Slater-Koster s/p table (these stand in for the tabulated
+ * H0/S of Sec. 2.1).  On-site: H0_AA = diag(eps_s, eps_p, eps_p, eps_p), S_AA = 1.
+ * gamma_AB (eq:coul): U_A on-site, 1/R - zeta(R) off-site with the closed form
+ * for exponential densities, tau = 16 U / 5.  E_rep = sum_{A<B} rep_A exp(-r / rep_b). */
+typedef struct {
+    int n_atoms;               /* >= 1 */
+    int orbs_per_atom;         /* 1 (s) or 4 (s, px, py, pz) */
+    int n_species;             /* >= 1 */
+    const int* species;        /* [n_atoms], values in [0, n_species) */
+    const double* R;           /* [n_atoms][3] positions, bohr */
+    const double* V;           /* [n_atoms][3] velocities (bohr / a.u. time), or NULL (= 0) */
+    const double* eps_s;       /* [n_species] on-site s energy, Ha */
+    const double* eps_p;       /* [n_species] on-site p energy, Ha */
+    const double* hubbard_U;   /* [n_species] Hubbard U, Ha (> 0 when scc) */
+    const double* mass;        /* [n_species] amu */
+    double t0, lam_H, s0, lam_S;
+    double eta[4];
+    double rep_A, rep_b;
+    double n_electrons;        /* 0 < n_electrons <= 2 N */
+} tdb_system;
+
+typedef struct {
+    double dt;                 /* time step, a.u. (negative: run backwards) */
+    int scc;                   /* 1: SCC Hamiltonian rebuild every step (eq:hscc) */
+    int move_nuclei;           /* 1: Ehrenfest nuclei (eq:forces, velocity Verlet); 0: frozen */
+    int precision;             /* tdb_precision */
+    int window;                /* steps between invariant checks in tdb_check (>= 1) */
+    double scc_tol;            /* ground-state tolerance on max |dq_out - dq_in| */
+    int scc_max_iter;
+    double kT;                 /* ground-state electronic temperature (Ha); 0 = aufbau */
+    double scc_mix;            /* Anderson mixing parameter of the ground state (0, 1] */
+    long history_cap;          /* dipole ring-buffer length (steps), >= 1 */
+    void* cuda_stream;         /* cudaStream_t, or NULL */
+} tdb_params;
+
+/* Laser pulse E(t) = E0 sin(omega t + phase) f(t) dir (eq:pumpf).
+ * envelope: 0 none (f = 1); 1 Gaussian exp(-4 ln2 (t - t_center)^2 / fwhm^2);
+ *           2 sin^2(pi t / fwhm) on 0 <= t <= fwhm, zero elsewhere. */
+typedef struct {
+    double E0, omega, phase, t_center, fwhm;
+    double dir[3];
+    int envelope;
+} tdb_field;
+
+typedef struct {
+    double t;                  /* time of rho_n */
+    long step;                 /* n */
+    double dipole[3];          /* mu = -sum_A dq_A R_A (Sec. 2.2, monopole charges) */
+    double E_total;            /* E_band + E_coul + E_rep + E_kin + E_ext */
+    double E_band;             /* Re Tr(rho H0) */
+    double E_coul;             /* 1/2 sum_AB gamma_AB dq_A dq_B (eq:coul) */
+    double E_rep;              /* pair repulsion */
+    double E_kin;              /* nuclear kinetic energy at V_n */
+    double E_ext;              /* sum_A dq_A R_A . E(t) */
+    double work;               /* int_0^t P dt, P = Re Tr[S^-1 H rho (D - D^T)] (trapezoid) */
+    double trace_re, trace_im; /* Tr(rho S) */
+    double herm_err;           /* max |rho - rho^dagger| */
+} tdb_obs;
+
+/* Default parameters (dt 0.2, scc 1, frozen nuclei, FP64, window 100,
+ * scc_tol 1e-12, 400 iterations, kT 0, mix 0.1, history 65536, stream NULL). */
+void tdb_default_params(tdb_params* out);
+
+/* Device bytes a context needs for this system and these parameters. */
+size_t tdb_workspace_bytes(const tdb_system* sys, const tdb_params* prm);
+
+/* Create a context: copy the system to the device and build S, H0, gamma
+ * (Sec. 2.1).  workspace: caller-owned device memory of at least
+ * tdb_workspace_bytes() bytes, 256-byte aligned, or NULL (the library
+ * allocates).  Returns TDB_ERR_NOT_SPD if S is not positive definite. */
+tdb_status tdb_create(const tdb_system* sys, const tdb_params* prm, void* workspace,
+                      size_t workspace_bytes, tdb_ctx** out);
+
+/* Ground state (Sec. 2.1: cycles of diagonalisation and Hamiltonian build to
+ * self-consistency): rho_0 = C f C^T of H C = S C eps, charges mixed until
+ * max |dq_out - dq_in| <= scc_tol.  Resets t = 0, n = 0, next step Euler. */
+tdb_status tdb_ground_state(tdb_ctx* ctx, int* iters_out, double* residual_out);
+
+/* Delta kick of eq:rhokick applied to the current rho (and to the previous
+ * leapfrog level, so that the next step is Euler): V = -E0 diag(dir . R_A(mu)). */
+tdb_status tdb_kick(tdb_ctx* ctx, double strength, const double dir[3]);
+
+/* Set (or clear with NULL) the laser field of eq:pumpf; takes effect from the next step. */
+tdb_status tdb_set_field(tdb_ctx* ctx, const tdb_field* field);
+
+/* Advance n >= 0 leapfrog steps (asynchronous on the context stream). */
+tdb_status tdb_step(tdb_ctx* ctx, long n);
+
+/* Observables of the current rho_n (synchronises).  charges: [n_atoms] Mulliken
+ * populations q_A or NULL; forces: [n_atoms][3] Ehrenfest forces (eq:forces,
+ * velocity terms dropped) or NULL. */
+tdb_status tdb_observables(tdb_ctx* ctx, tdb_obs* obs, double* charges, double* forces);
+
+/* The dipoles mu_k of the last min(steps, cap) steps, oldest first:
+ * out[3 * cap] host doubles; *n_out = number written. */
+tdb_status tdb_dipole_history(tdb_ctx* ctx, double* out, long cap, long* n_out);
+
+/* Copy rho_n (and rho_{n-1} when prev_re/prev_im are non-NULL) to host,
+ * row-major N x N doubles. */
+tdb_status tdb_get_rho(tdb_ctx* ctx, double* re, double* im, double* prev_re, double* prev_im);
+
+/* Checkpoint: bytes of a state blob, and copy it out / back in (rho_{n-1},
+ * rho_n, R, V, t, n, Euler flag, work integral).  set_state makes a context
+ * continue bitwise as the one it was taken from. */
+size_t tdb_state_bytes(const tdb_ctx* ctx);
+tdb_status tdb_get_state(tdb_ctx* ctx, void* host_buf, size_t bytes);
+tdb_status tdb_set_state(tdb_ctx* ctx, const void* host_buf, size_t bytes);
+
+/* Invariant monitor (synchronises): NaN/Inf, |Tr(rho S) - N_e| / N_e <= tol_trace.
+ * Violation returns TDB_ERR_NUMERIC and makes the context sticky. */
+tdb_status tdb_check(tdb_ctx* ctx, double tol_trace);
+
+/* Device kernel launches issued by the last tdb_step call (for accounting). */
+long tdb_last_launch_count(const tdb_ctx* ctx);
+
+/* Advance one step like tdb_step(ctx, 1) but without the captured graph, with a
+ * CUDA event recorded on the context stream before each kernel; synchronises.
+ * ms[i] = device time of kernel i (milliseconds), names[i] = a static string
+ * naming it (names may be NULL); *n_out = kernels timed (<= cap). */
+tdb_status tdb_step_profiled(tdb_ctx* ctx, double* ms, const char** names, int cap, int* n_out);
+
+void tdb_destroy(tdb_ctx* ctx);
+const char* tdb_status_string(tdb_status s);
+const char* tdb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDB_H */

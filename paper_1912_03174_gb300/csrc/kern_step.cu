@@ -1,0 +1,655 @@
+// O(N^2) kernels of the propagation step and of the setup: model build
+// (S, H0, gamma), Mulliken charges, SCC potential, leapfrog update, kick
+// helpers and observable reductions.  All arithmetic is FP64.
+#include <cmath>
+
+#include "tdb_internal.h"
+
+namespace tdb {
+
+namespace {
+
+// E(t) of eq:pumpf: E0 sin(omega t + phase) f(t) dir.
+__device__ void field_at(const FieldDev& f, double t, double E[3]) {
+    if (!f.on) {
+        E[0] = E[1] = E[2] = 0.0;
+        return;
+    }
+    double env = 1.0;
+    if (f.envelope == 1) {
+        const double x = t - f.t_center;
+        env = exp(-x * x * 4.0 * 0.69314718055994530942 / (f.fwhm * f.fwhm));
+    } else if (f.envelope == 2) {
+        if (t >= 0.0 && t <= f.fwhm) {
+            const double s = sin(3.14159265358979323846 * t / f.fwhm);
+            env = s * s;
+        } else {
+            env = 0.0;
+        }
+    }
+    const double a = f.E0 * sin(f.omega * t + f.phase) * env;
+    E[0] = a * f.dir[0];
+    E[1] = a * f.dir[1];
+    E[2] = a * f.dir[2];
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One thread per (A, B) atom pair writes the nper x nper blocks of S and H0.
+// Off-site: Slater-Koster s/p table with direction cosines c of R_B - R_A:
+//   ss = K0, s-a = c_a K1, a-s = -c_a K1, a-b = c_a c_b (K2 - K3) + delta_ab K3,
+// with hopping K = eta t0 exp(-r/lam_H) and overlap K = -eta s0 exp(-r/lam_S).
+__global__ void k_build_model(int nat, int nper, const double* __restrict__ R,
+                              const double* __restrict__ onsite, ModelParams mp,
+                              double* __restrict__ S, double* __restrict__ H0) {
+    const int B = blockIdx.x * blockDim.x + threadIdx.x;
+    const int A = blockIdx.y * blockDim.y + threadIdx.y;
+    if (A >= nat || B >= nat) return;
+    const int N = nat * nper;
+    double hb[4][4], sb[4][4];
+    if (A == B) {
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) {
+                sb[i][j] = (i == j) ? 1.0 : 0.0;
+                hb[i][j] = (i == j && i < nper) ? onsite[A * nper + i] : 0.0;
+            }
+    } else {
+        const double dx = R[3 * B] - R[3 * A], dy = R[3 * B + 1] - R[3 * A + 1],
+                     dz = R[3 * B + 2] - R[3 * A + 2];
+        const double r = sqrt(dx * dx + dy * dy + dz * dz);
+        const double c[3] = {dx / r, dy / r, dz / r};
+        const double eh = exp(-r / mp.lam_H), es = exp(-r / mp.lam_S);
+        double kh[4], ks[4];
+        for (int k = 0; k < 4; ++k) {
+            kh[k] = mp.eta[k] * mp.t0 * eh;
+            ks[k] = -mp.eta[k] * mp.s0 * es;
+        }
+        hb[0][0] = kh[0];
+        sb[0][0] = ks[0];
+        for (int a = 0; a < 3; ++a) {
+            hb[0][1 + a] = c[a] * kh[1];
+            sb[0][1 + a] = c[a] * ks[1];
+            hb[1 + a][0] = -c[a] * kh[1];
+            sb[1 + a][0] = -c[a] * ks[1];
+            for (int b = 0; b < 3; ++b) {
+                const double cc = c[a] * c[b];
+                hb[1 + a][1 + b] = cc * (kh[2] - kh[3]) + (a == b ? kh[3] : 0.0);
+                sb[1 + a][1 + b] = cc * (ks[2] - ks[3]) + (a == b ? ks[3] : 0.0);
+            }
+        }
+    }
+    for (int i = 0; i < nper; ++i) {
+        const size_t row = (size_t)(A * nper + i) * N + (size_t)B * nper;
+        for (int j = 0; j < nper; ++j) {
+            S[row + j] = sb[i][j];
+            H0[row + j] = hb[i][j];
+        }
+    }
+}
+
+// Short-range part zeta(R) of gamma for exponents ta, tb (tau = 16 U / 5):
+// Coulomb integral of two normalised exp(-tau r) densities is 1/R - zeta(R).
+__device__ double gamma_short(double ta, double tb, double R) {
+    const double tmax = ta > tb ? ta : tb;
+    if (fabs(ta - tb) < 3e-4 * tmax) {
+        const double t = 0.5 * (ta + tb);
+        return exp(-t * R) * (1.0 / R + 11.0 * t / 16.0 + 3.0 * t * t * R / 16.0 +
+                              t * t * t * R * R / 48.0);
+    }
+    double z = 0.0;
+    for (int s = 0; s < 2; ++s) {
+        const double a = s ? tb : ta, b = s ? ta : tb;
+        const double a2 = a * a, b2 = b * b, d = a2 - b2;
+        const double b4 = b2 * b2;
+        z += exp(-a * R) * (b4 * a / (2.0 * d * d) - (b4 * b2 - 3.0 * a2 * b4) / (d * d * d * R));
+    }
+    return z;
+}
+
+__global__ void k_build_gamma(int nat, const double* __restrict__ R, const double* __restrict__ U,
+                              double* __restrict__ G) {
+    const int B = blockIdx.x * blockDim.x + threadIdx.x;
+    const int A = blockIdx.y * blockDim.y + threadIdx.y;
+    if (A >= nat || B >= nat) return;
+    double g;
+    if (A == B) {
+        g = U[A];
+    } else {
+        const double dx = R[3 * B] - R[3 * A], dy = R[3 * B + 1] - R[3 * A + 1],
+                     dz = R[3 * B + 2] - R[3 * A + 2];
+        const double r = sqrt(dx * dx + dy * dy + dz * dz);
+        g = 1.0 / r - gamma_short(3.2 * U[A], 3.2 * U[B], r);
+    }
+    G[(size_t)A * nat + B] = g;
+}
+
+// Row-major upper triangle -> lower triangle (after a column-major lower potri).
+__global__ void k_sym_upper_to_lower(int N, double* A) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    if (r < N && c < N && r > c) A[(size_t)r * N + c] = A[(size_t)c * N + r];
+}
+
+__global__ void k_transpose(int N, const double* __restrict__ in, double* __restrict__ out) {
+    __shared__ double t[kTile][kTile + 1];
+    const int bx = blockIdx.x * kTile, by = blockIdx.y * kTile;
+    for (int y = threadIdx.y; y < kTile; y += blockDim.y) {
+        const int r = by + y, c = bx + threadIdx.x;
+        if (r < N && c < N) t[y][threadIdx.x] = in[(size_t)r * N + c];
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < kTile; y += blockDim.y) {
+        const int r = bx + y, c = by + threadIdx.x;
+        if (r < N && c < N) out[(size_t)r * N + c] = t[threadIdx.x][y];
+    }
+}
+
+// partial[ct][row] = sum over the 32 columns of tile ct of Re rho[row][col] * S[row][col]
+// (eq:qmulik: q_A = sum_{nu in A} Re (rho S)_{nu nu}; S is symmetric).
+__global__ void k_mulliken_partials(int N, const double* __restrict__ rre,
+                                    const double* __restrict__ S, double* __restrict__ partial) {
+    const int ct = blockIdx.x;
+    const int col = ct * kTile + threadIdx.x;
+    for (int y = threadIdx.y; y < kTile; y += blockDim.y) {
+        const int row = blockIdx.y * kTile + y;
+        if (row >= N) continue;
+        double v = 0.0;
+        if (col < N) v = rre[(size_t)row * N + col] * S[(size_t)row * N + col];
+        v = warp_sum(v);
+        if (threadIdx.x == 0) partial[(size_t)ct * N + row] = v;
+    }
+}
+
+__global__ void k_charges(int nat, int nper, int nct, int N, const double* __restrict__ partial,
+                          const double* __restrict__ q0, double* __restrict__ q,
+                          double* __restrict__ dq) {
+    const int A = blockIdx.x * blockDim.x + threadIdx.x;
+    if (A >= nat) return;
+    double s = 0.0;
+    for (int i = 0; i < nper; ++i)
+        for (int ct = 0; ct < nct; ++ct) s += partial[(size_t)ct * N + A * nper + i];
+    q[A] = s;
+    dq[A] = s - q0[A];
+}
+
+// Warp per atom A: gdq_A = sum_B gamma_AB dq_B;  v_A = [scc] gdq_A + R_A . E(t_n)
+// (eq:hscc, eq:hsccvext with V_ext,A = R_A . E).  Block 0 also records E(t_n),
+// the dipole mu = -sum_A dq_A R_A into the history ring, and sum_A dq_A V_ext,A.
+__global__ void k_potential(int nat, int nper, int scc, const double* __restrict__ gamma,
+                            const double* __restrict__ dq, const double* __restrict__ R,
+                            DevScalars* __restrict__ sc, double* __restrict__ v_orb,
+                            double* __restrict__ v_atom, double* __restrict__ gdq,
+                            double* __restrict__ hist, const double* __restrict__ v_ref,
+                            float* __restrict__ dv_f) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarp = blockDim.x >> 5;
+    const long long n = sc->step;
+    const double t = sc->t_base + (double)(n - sc->n_base) * sc->dt;
+    double E[3];
+    field_at(sc->field, t, E);
+    for (int A = blockIdx.x * nwarp + warp; A < nat; A += gridDim.x * nwarp) {
+        double s = 0.0;
+        if (scc)
+            for (int B = lane; B < nat; B += 32) s += gamma[(size_t)A * nat + B] * dq[B];
+        s = warp_sum(s);
+        const double vA = s + R[3 * A] * E[0] + R[3 * A + 1] * E[1] + R[3 * A + 2] * E[2];
+        if (lane < nper) {
+            const int o = A * nper + lane;
+            v_orb[o] = vA;
+            if (dv_f) dv_f[o] = (float)(vA - v_ref[o]);
+        }
+        if (lane == 0) {
+            v_atom[A] = vA;
+            gdq[A] = s;
+        }
+    }
+    if (blockIdx.x == 0) {
+        __shared__ double red[4][32];
+        double m0 = 0, m1 = 0, m2 = 0, ee = 0;
+        for (int A = threadIdx.x; A < nat; A += blockDim.x) {
+            const double d = dq[A];
+            m0 -= d * R[3 * A];
+            m1 -= d * R[3 * A + 1];
+            m2 -= d * R[3 * A + 2];
+            ee += d * (R[3 * A] * E[0] + R[3 * A + 1] * E[1] + R[3 * A + 2] * E[2]);
+        }
+        m0 = warp_sum(m0);
+        m1 = warp_sum(m1);
+        m2 = warp_sum(m2);
+        ee = warp_sum(ee);
+        if (lane == 0) {
+            red[0][warp] = m0;
+            red[1][warp] = m1;
+            red[2][warp] = m2;
+            red[3][warp] = ee;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0, b = 0, c = 0, e = 0;
+            for (int w = 0; w < nwarp; ++w) {
+                a += red[0][w];
+                b += red[1][w];
+                c += red[2][w];
+                e += red[3][w];
+            }
+            sc->mu[0] = a;
+            sc->mu[1] = b;
+            sc->mu[2] = c;
+            sc->e_ext = e;
+            sc->E[0] = E[0];
+            sc->E[1] = E[1];
+            sc->E[2] = E[2];
+            const long long slot = n % sc->hist_cap;
+            const long long s2 = slot < 0 ? slot + sc->hist_cap : slot;
+            hist[3 * s2] = a;
+            hist[3 * s2 + 1] = b;
+            hist[3 * s2 + 2] = c;
+        }
+    }
+}
+
+__global__ void k_build_hamiltonian(int N, const double* __restrict__ H0,
+                                    const double* __restrict__ S, const double* __restrict__ v,
+                                    double* __restrict__ H) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    if (r >= N || c >= N) return;
+    const size_t i = (size_t)r * N + c;
+    H[i] = H0[i] + 0.5 * S[i] * (v[r] + v[c]);
+}
+
+// Leapfrog / Euler update (eq:leapfrog with eq:eomrho, frozen nuclei):
+//   out = base + factor * rhodot,  rhodot = -i (X - X^dagger),  X = S^-1 H rho.
+// Re rhodot_ij = Im X_ij + Im X_ji;  Im rhodot_ij = -(Re X_ij - Re X_ji).
+// A block owns the tile pair (bi, bj), bi <= bj, so both halves come out of the
+// same operands and rho stays exactly Hermitian.  The Mulliken row partials of
+// the new rho are fused in.  T is the type of X.
+template <typename T>
+__global__ void k_update(int N, int nct, const T* __restrict__ Xre, const T* __restrict__ Xim,
+                         const double* __restrict__ bre, const double* __restrict__ bim,
+                         double* __restrict__ ore, double* __restrict__ oim, double factor,
+                         const double* __restrict__ S, double* __restrict__ partial,
+                         DevScalars* __restrict__ sc, const double* __restrict__ rho_ref,
+                         float* __restrict__ op_re, float* __restrict__ op_im,
+                         __nv_bfloat16* __restrict__ hre, __nv_bfloat16* __restrict__ lre,
+                         __nv_bfloat16* __restrict__ him, __nv_bfloat16* __restrict__ lim) {
+    const int bi = blockIdx.y, bj = blockIdx.x;
+    if (bi > bj) return;
+    __shared__ T xr_ij[kTile][kTile + 1], xi_ij[kTile][kTile + 1];
+    __shared__ T xr_ji[kTile][kTile + 1], xi_ji[kTile][kTile + 1];
+    const int tx = threadIdx.x;
+    for (int y = threadIdx.y; y < kTile; y += blockDim.y) {
+        int r = bi * kTile + y, c = bj * kTile + tx;
+        T a = 0, b = 0;
+        if (r < N && c < N) {
+            a = Xre[(size_t)r * N + c];
+            b = Xim[(size_t)r * N + c];
+        }
+        xr_ij[y][tx] = a;
+        xi_ij[y][tx] = b;
+        r = bj * kTile + y;
+        c = bi * kTile + tx;
+        a = 0;
+        b = 0;
+        if (r < N && c < N) {
+            a = Xre[(size_t)r * N + c];
+            b = Xim[(size_t)r * N + c];
+        }
+        xr_ji[y][tx] = a;
+        xi_ji[y][tx] = b;
+    }
+    __syncthreads();
+    for (int half = 0; half < (bi == bj ? 1 : 2); ++half) {
+        const int ti = half ? bj : bi, tj = half ? bi : bj;
+        for (int y = threadIdx.y; y < kTile; y += blockDim.y) {
+            const int r = ti * kTile + y, c = tj * kTile + tx;
+            double pv = 0.0;
+            if (r < N && c < N) {
+                double x_ij_re, x_ij_im, x_ji_re, x_ji_im;
+                if (!half) {
+                    x_ij_re = (double)xr_ij[y][tx];
+                    x_ij_im = (double)xi_ij[y][tx];
+                    x_ji_re = (double)xr_ji[tx][y];
+                    x_ji_im = (double)xi_ji[tx][y];
+                } else {
+                    x_ij_re = (double)xr_ji[y][tx];
+                    x_ij_im = (double)xi_ji[y][tx];
+                    x_ji_re = (double)xr_ij[tx][y];
+                    x_ji_im = (double)xi_ij[tx][y];
+                }
+                const double dre = x_ij_im + x_ji_im;
+                const double dim = -(x_ij_re - x_ji_re);
+                const size_t i = (size_t)r * N + c;
+                const double nre = bre[i] + factor * dre;
+                const double nim = bim[i] + factor * dim;
+                ore[i] = nre;
+                oim[i] = nim;
+                pv = nre * S[i];
+                if (rho_ref) {
+                    const double d_re = nre - rho_ref[i];
+                    if (op_re) {
+                        op_re[i] = (float)d_re;
+                        op_im[i] = (float)nim;
+                    }
+                    if (hre) {
+                        // rho operands are stored K-major for the tensor-core products:
+                        // Re is symmetric, the transposed Im is -Im.
+                        const __nv_bfloat16 h1 = __double2bfloat16(d_re);
+                        hre[i] = h1;
+                        lre[i] = __double2bfloat16(d_re - (double)__bfloat162float(h1));
+                        const double ni = -nim;
+                        const __nv_bfloat16 h2 = __double2bfloat16(ni);
+                        him[i] = h2;
+                        lim[i] = __double2bfloat16(ni - (double)__bfloat162float(h2));
+                    }
+                }
+            }
+            pv = warp_sum(pv);
+            if (tx == 0 && r < N) partial[(size_t)tj * N + r] = pv;
+        }
+    }
+    if (bi == 0 && bj == 0 && threadIdx.x == 0 && threadIdx.y == 0) sc->step += 1;
+}
+
+// C = diag(p) P diag(conj p), p_mu = exp(-i E0 dir . R_A(mu)): the phase factors of
+// eq:rhokick with V = -E0 diag(dir . R).
+__global__ void k_kick_phase(int N, int nper, const double* __restrict__ R, double E0, double d0,
+                             double d1, double d2, const double* __restrict__ Pre,
+                             const double* __restrict__ Pim, double* __restrict__ Cre,
+                             double* __restrict__ Cim) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    if (r >= N || c >= N) return;
+    const int A = r / nper, B = c / nper;
+    const double xa = d0 * R[3 * A] + d1 * R[3 * A + 1] + d2 * R[3 * A + 2];
+    const double xb = d0 * R[3 * B] + d1 * R[3 * B + 1] + d2 * R[3 * B + 2];
+    // p_r conj(p_c) = exp(-i E0 (x_a - x_b))
+    double sn, cs;
+    sincos(-E0 * (xa - xb), &sn, &cs);
+    const size_t i = (size_t)r * N + c;
+    const double pr = Pre[i], pi = Pim[i];
+    Cre[i] = cs * pr - sn * pi;
+    Cim[i] = cs * pi + sn * pr;
+}
+
+// out = 1/2 (T + T^dagger)
+__global__ void k_hermitian_half(int N, const double* __restrict__ Tre,
+                                 const double* __restrict__ Tim, double* __restrict__ ore,
+                                 double* __restrict__ oim) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    if (r >= N || c >= N) return;
+    const size_t i = (size_t)r * N + c, j = (size_t)c * N + r;
+    ore[i] = 0.5 * (Tre[i] + Tre[j]);
+    oim[i] = 0.5 * (Tim[i] - Tim[j]);
+}
+
+// Per block: sum Re rho * H0, sum Re rho * S, sum Im rho * S, max |rho_ij - conj rho_ji|.
+__global__ void k_obs_reduce(int N, const double* __restrict__ rre, const double* __restrict__ rim,
+                             const double* __restrict__ H0, const double* __restrict__ S,
+                             double* __restrict__ out) {
+    double a = 0, b = 0, c = 0, m = 0;
+    const size_t NN = (size_t)N * N;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < NN;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const size_t r = i / N, col = i % N, j = col * N + r;
+        const double re = rre[i], im = rim[i];
+        a += re * H0[i];
+        b += re * S[i];
+        c += im * S[i];
+        const double e1 = fabs(re - rre[j]), e2 = fabs(im + rim[j]);
+        m = fmax(m, fmax(e1, e2));
+    }
+    __shared__ double red[4][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    c = warp_sum(c);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) {
+        red[0][w] = a;
+        red[1][w] = b;
+        red[2][w] = c;
+        red[3][w] = m;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s0 = 0, s1 = 0, s2 = 0, mx = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            s0 += red[0][k];
+            s1 += red[1][k];
+            s2 += red[2][k];
+            mx = fmax(mx, red[3][k]);
+        }
+        out[4 * blockIdx.x] = s0;
+        out[4 * blockIdx.x + 1] = s1;
+        out[4 * blockIdx.x + 2] = s2;
+        out[4 * blockIdx.x + 3] = mx;
+    }
+}
+
+__global__ void k_obs_finish(int nb, const double* __restrict__ in, double* __restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s0 = 0, s1 = 0, s2 = 0, mx = 0;
+    for (int k = 0; k < nb; ++k) {
+        s0 += in[4 * k];
+        s1 += in[4 * k + 1];
+        s2 += in[4 * k + 2];
+        mx = fmax(mx, in[4 * k + 3]);
+    }
+    out[0] = s0;
+    out[1] = s1;
+    out[2] = s2;
+    out[3] = mx;
+}
+
+// out[m][k] = in[m][k] * f[k]
+__global__ void k_scale_cols(int N, const double* __restrict__ in, const double* __restrict__ f,
+                             double* __restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    if (r >= N || c >= N) return;
+    out[(size_t)r * N + c] = in[(size_t)r * N + c] * f[c];
+}
+
+inline dim3 grid2(int nx, int ny, dim3 b) {
+    return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y);
+}
+
+}  // namespace
+
+void launch_build_model(const Ctx& c, const double* R, double* S, double* H0, cudaStream_t st) {
+    dim3 b(32, 8);
+    k_build_model<<<grid2(c.nat, c.nat, b), b, 0, st>>>(c.nat, c.nper, R, c.d_onsite, c.mp, S, H0);
+}
+
+void launch_build_gamma(const Ctx& c, const double* R, double* gamma, cudaStream_t st) {
+    dim3 b(32, 8);
+    k_build_gamma<<<grid2(c.nat, c.nat, b), b, 0, st>>>(c.nat, R, c.d_U, gamma);
+}
+
+void launch_symmetrize_upper_to_lower(int N, double* A, cudaStream_t st) {
+    dim3 b(32, 8);
+    k_sym_upper_to_lower<<<grid2(N, N, b), b, 0, st>>>(N, A);
+}
+
+void launch_transpose(int N, const double* in, double* out, cudaStream_t st) {
+    dim3 b(kTile, 8);
+    dim3 g((N + kTile - 1) / kTile, (N + kTile - 1) / kTile);
+    k_transpose<<<g, b, 0, st>>>(N, in, out);
+}
+
+void launch_mulliken_partials(int N, const double* rho_re, const double* S, double* partial,
+                              cudaStream_t st) {
+    const int nct = (N + kTile - 1) / kTile;
+    dim3 b(kTile, 8);
+    k_mulliken_partials<<<dim3(nct, nct), b, 0, st>>>(N, rho_re, S, partial);
+}
+
+void launch_charges(const Ctx& c, const double* partial, double* q, double* dq, cudaStream_t st) {
+    k_charges<<<(c.nat + 127) / 128, 128, 0, st>>>(c.nat, c.nper, c.nct, c.N, partial, c.d_q0, q,
+                                                   dq);
+}
+
+void launch_potential(const Ctx& c, const double* gamma, const double* dq, const double* R,
+                      DevScalars* sc, double* v_orb, double* v_atom, double* gdq, double* hist,
+                      const double* v_ref, float* dv_orb, cudaStream_t st) {
+    const int warps = 8;
+    const int blocks = (c.nat + warps - 1) / warps;
+    k_potential<<<blocks, warps * 32, 0, st>>>(c.nat, c.nper, c.prm.scc, gamma, dq, R, sc, v_orb,
+                                               v_atom, gdq, hist, v_ref, dv_orb);
+}
+
+void launch_build_hamiltonian(int N, const double* H0, const double* S, const double* v_orb,
+                              double* H, cudaStream_t st) {
+    dim3 b(32, 8);
+    k_build_hamiltonian<<<grid2(N, N, b), b, 0, st>>>(N, H0, S, v_orb, H);
+}
+
+void launch_update(const Ctx& c, const double* Xre, const double* Xim, const double* base_re,
+                   const double* base_im, double* out_re, double* out_im, double factor,
+                   const double* S, double* partial, DevScalars* sc, cudaStream_t st) {
+    dim3 b(kTile, 8);
+    k_update<double><<<dim3(c.nct, c.nct), b, 0, st>>>(
+        c.N, c.nct, Xre, Xim, base_re, base_im, out_re, out_im, factor, S, partial, sc, nullptr,
+        nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+}
+
+void launch_update_f32(const Ctx& c, const float* Xre, const float* Xim, const double* base_re,
+                       const double* base_im, double* out_re, double* out_im, double factor,
+                       const double* S, double* partial, DevScalars* sc, const double* rho_ref,
+                       float* op_re, float* op_im, __nv_bfloat16* opb_re_hi,
+                       __nv_bfloat16* opb_re_lo, __nv_bfloat16* opb_im_hi,
+                       __nv_bfloat16* opb_im_lo, cudaStream_t st) {
+    dim3 b(kTile, 8);
+    k_update<float><<<dim3(c.nct, c.nct), b, 0, st>>>(
+        c.N, c.nct, Xre, Xim, base_re, base_im, out_re, out_im, factor, S, partial, sc, rho_ref,
+        op_re, op_im, opb_re_hi, opb_re_lo, opb_im_hi, opb_im_lo);
+}
+
+void launch_kick_phase(int N, int n_per, const double* R, double strength, const double* dir,
+                       const double* Pre, const double* Pim, double* Cre, double* Cim,
+                       cudaStream_t st) {
+    dim3 b(32, 8);
+    k_kick_phase<<<grid2(N, N, b), b, 0, st>>>(N, n_per, R, strength, dir[0], dir[1], dir[2], Pre,
+                                               Pim, Cre, Cim);
+}
+
+void launch_hermitian_half(int N, const double* Tre, const double* Tim, double* out_re,
+                           double* out_im, cudaStream_t st) {
+    dim3 b(32, 8);
+    k_hermitian_half<<<grid2(N, N, b), b, 0, st>>>(N, Tre, Tim, out_re, out_im);
+}
+
+void launch_obs_reduce(int N, const double* rho_re, const double* rho_im, const double* H0,
+                       const double* S, double* block_out, int n_blocks, cudaStream_t st) {
+    k_obs_reduce<<<n_blocks, 256, 0, st>>>(N, rho_re, rho_im, H0, S, block_out);
+}
+
+void launch_obs_finish(int n_blocks, const double* block_out, double* out4, cudaStream_t st) {
+    k_obs_finish<<<1, 32, 0, st>>>(n_blocks, block_out, out4);
+}
+
+void launch_scale_rows_f(int N, const double* in, const double* f, double* out, cudaStream_t st) {
+    dim3 b(32, 8);
+    k_scale_cols<<<grid2(N, N, b), b, 0, st>>>(N, in, f, out);
+}
+
+}  // namespace tdb
+
+namespace tdb {
+
+namespace {
+
+__global__ void k_f64_to_f32(size_t n, const double* __restrict__ in, float* __restrict__ out) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+
+// out = (float)(a - b), b may be null
+__global__ void k_sub_to_f32(size_t n, const double* __restrict__ a, const double* __restrict__ b,
+                             float* __restrict__ out) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        out[i] = (float)(b ? a[i] - b[i] : a[i]);
+}
+
+// out[r][c] = a[r][c] + b[r][c] with row strides N (a), ldb (b), ldo (out)
+__global__ void k_add_f32(int N, const float* __restrict__ a, const float* __restrict__ b, int ldb,
+                          float* __restrict__ out, int ldo) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    if (r >= N || c >= N) return;
+    out[(size_t)r * ldo + c] = a[(size_t)r * N + c] + b[(size_t)r * ldb + c];
+}
+
+// out[0] = 1/2 sum_A dq_A (gamma dq)_A (eq:coul), out[1] = sum_{A<B} rep_A exp(-r/rep_b),
+// out[2] = nuclear kinetic energy (moving nuclei only)
+__global__ void k_small_energies(int nat, const double* __restrict__ dq,
+                                 const double* __restrict__ gdq, const double* __restrict__ R,
+                                 const double* __restrict__ V, const double* __restrict__ mass,
+                                 double rep_A, double rep_b, int kinetic,
+                                 double* __restrict__ out) {
+    double ec = 0, er = 0, ek = 0;
+    for (int A = threadIdx.x; A < nat; A += blockDim.x) {
+        ec += 0.5 * dq[A] * gdq[A];
+        if (kinetic)
+            ek += 0.5 * mass[A] * 1822.888486 *
+                  (V[3 * A] * V[3 * A] + V[3 * A + 1] * V[3 * A + 1] + V[3 * A + 2] * V[3 * A + 2]);
+        if (rep_A != 0.0)
+            for (int B = A + 1; B < nat; ++B) {
+                const double dx = R[3 * B] - R[3 * A], dy = R[3 * B + 1] - R[3 * A + 1],
+                             dz = R[3 * B + 2] - R[3 * A + 2];
+                er += rep_A * exp(-sqrt(dx * dx + dy * dy + dz * dz) / rep_b);
+            }
+    }
+    __shared__ double red[3][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    ec = warp_sum(ec);
+    er = warp_sum(er);
+    ek = warp_sum(ek);
+    if (lane == 0) {
+        red[0][w] = ec;
+        red[1][w] = er;
+        red[2][w] = ek;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0, c = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            a += red[0][k];
+            b += red[1][k];
+            c += red[2][k];
+        }
+        out[0] = a;
+        out[1] = b;
+        out[2] = c;
+    }
+}
+
+}  // namespace
+
+void launch_f64_to_f32(size_t n, const double* in, float* out, cudaStream_t st) {
+    k_f64_to_f32<<<1216, 256, 0, st>>>(n, in, out);
+}
+
+void launch_sub_to_f32(size_t n, const double* a, const double* b, float* out, cudaStream_t st) {
+    k_sub_to_f32<<<1216, 256, 0, st>>>(n, a, b, out);
+}
+
+void launch_add_f32_strided(int N, const float* a, const float* b, int ldb, float* out, int ldo,
+                            cudaStream_t st) {
+    dim3 bl(32, 8);
+    k_add_f32<<<grid2(N, N, bl), bl, 0, st>>>(N, a, b, ldb, out, ldo);
+}
+
+void launch_small_energies(const Ctx& c, double* out, cudaStream_t st) {
+    k_small_energies<<<1, 256, 0, st>>>(c.nat, c.dq, c.gdq, c.d_R, c.d_V, c.d_mass, c.mp.rep_A,
+                                        c.mp.rep_b, c.prm.move_nuclei, out);
+}
+
+}  // namespace tdb

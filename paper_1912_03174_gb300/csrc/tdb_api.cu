@@ -1,0 +1,1079 @@
+// C ABI of the propagator: context lifetime, ground state, kick, field,
+// stepping (CUDA graphs), observables and checkpoints.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "tdb_internal.h"
+
+namespace tdb {
+void gemm_f32_dham(int N, const float* A, const float* S, const float* dv, float* C, int ldc,
+                   const float* Cadd, cudaStream_t st);
+void gemm_f32_add(int M, int Ncol, int K, const float* A, int lda, const float* B, int ldb,
+                  float* C, int ldc, const float* Cadd, cudaStream_t st);
+void launch_f64_to_f32(size_t n, const double* in, float* out, cudaStream_t st);
+void launch_sub_to_f32(size_t n, const double* a, const double* b, float* out, cudaStream_t st);
+void launch_add_f32_strided(int N, const float* a, const float* b, int ldb, float* out, int ldo,
+                            cudaStream_t st);
+void launch_small_energies(const Ctx& c, double* out, cudaStream_t st);
+}  // namespace tdb
+
+using namespace tdb;
+
+struct tdb_ctx : public Ctx {};
+
+namespace {
+
+thread_local std::string g_err;
+
+void set_err(const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            set_err("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_));   \
+            return TDB_ERR_CUDA;                                                          \
+        }                                                                                 \
+    } while (0)
+
+#define CKL()                                                                             \
+    do {                                                                                  \
+        cudaError_t e_ = cudaGetLastError();                                              \
+        if (e_ != cudaSuccess) {                                                          \
+            set_err("%s:%d kernel launch: %s", __FILE__, __LINE__, cudaGetErrorString(e_)); \
+            return TDB_ERR_CUDA;                                                          \
+        }                                                                                 \
+    } while (0)
+
+#define CKS(call)                                                                         \
+    do {                                                                                  \
+        cusolverStatus_t s_ = (call);                                                     \
+        if (s_ != CUSOLVER_STATUS_SUCCESS) {                                              \
+            set_err("%s:%d %s: cusolver status %d", __FILE__, __LINE__, #call, (int)s_);  \
+            return TDB_ERR_CUDA;                                                          \
+        }                                                                                 \
+    } while (0)
+
+#define TRY(x)                         \
+    do {                               \
+        tdb_status s_ = (x);           \
+        if (s_ != TDB_OK) return s_;   \
+    } while (0)
+
+constexpr int kObsBlocks = 304;  // 2 x 152 SMs
+
+// Carves named sub-buffers out of one workspace, 256-byte aligned.
+struct Carver {
+    char* base;
+    size_t off = 0;
+    template <typename T>
+    T* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+bool mixed(const Ctx& c) { return c.prm.precision != TDB_FP64; }
+
+size_t carve(Ctx& c, char* base) {
+    Carver k{base};
+    const size_t N = c.N, NN = N * N, nat = c.nat;
+    c.d_R = k.take<double>(3 * nat);
+    c.d_V = k.take<double>(3 * nat);
+    c.d_onsite = k.take<double>(N);
+    c.d_U = k.take<double>(nat);
+    c.d_mass = k.take<double>(nat);
+    c.d_q0 = k.take<double>(nat);
+    c.S = k.take<double>(NN);
+    c.Sinv = k.take<double>(NN);
+    c.H0 = k.take<double>(NN);
+    c.gamma = k.take<double>(nat * nat);
+    for (int i = 0; i < 2; ++i) {
+        c.rho_re[i] = k.take<double>(NN);
+        c.rho_im[i] = k.take<double>(NN);
+    }
+    c.Xre = k.take<double>(NN);
+    c.Xim = k.take<double>(NN);
+    c.M = k.take<double>(NN);
+    c.Hs = k.take<double>(NN);
+    c.partial = k.take<double>((size_t)c.nct * N);
+    c.q = k.take<double>(nat);
+    c.dq = k.take<double>(nat);
+    c.v_atom = k.take<double>(nat);
+    c.gdq = k.take<double>(nat);
+    c.v_orb = k.take<double>(N);
+    c.v_ref = k.take<double>(N);
+    c.hist = k.take<double>(3 * (size_t)c.prm.history_cap);
+    c.obs_blocks = k.take<double>(4 * kObsBlocks);
+    c.obs_out = k.take<double>(16 + 2 * N);   // reductions, small energies, eigenvalues, occupations
+    c.sc = k.take<DevScalars>(1);
+    if (mixed(c)) {
+        c.rho_ref = k.take<double>(NN);
+        c.dv_f = k.take<float>(N);
+        c.S_f = k.take<float>(NN);
+        c.Sinv_f = k.take<float>(NN);
+        c.Mgs_f = k.take<float>(NN);
+        c.dM_f = k.take<float>(2 * NN);     // [delta M | M], row stride 2N
+        c.M_f = c.dM_f ? c.dM_f + N : nullptr;
+        c.rref_f = k.take<float>(2 * NN);   // [rho_ref ; Re(rho - rho_ref)] stacked, 2N x N
+        c.dre_f = c.rref_f ? c.rref_f + NN : nullptr;
+        c.dim_f = k.take<float>(NN);
+        c.Xre_f = k.take<float>(NN);
+        c.Xim_f = k.take<float>(NN);
+    }
+    return k.off + 256;
+}
+
+tdb_status validate(const tdb_system* s, const tdb_params* p) {
+    if (!s || !p) {
+        set_err("NULL system or params");
+        return TDB_ERR_ARG;
+    }
+    if (s->n_atoms < 1 || (s->orbs_per_atom != 1 && s->orbs_per_atom != 4) || s->n_species < 1 ||
+        !s->species || !s->R || !s->eps_s || !s->eps_p || !s->hubbard_U || !s->mass) {
+        set_err("invalid system (sizes or NULL arrays)");
+        return TDB_ERR_ARG;
+    }
+    const long N = (long)s->n_atoms * s->orbs_per_atom;
+    if (N > 32768) {
+        set_err("N = %ld exceeds the supported 32768 orbitals", N);
+        return TDB_ERR_ARG;
+    }
+    if (!(s->n_electrons > 0) || s->n_electrons > 2.0 * N) {
+        set_err("n_electrons out of range");
+        return TDB_ERR_ARG;
+    }
+    for (int a = 0; a < s->n_atoms; ++a)
+        if (s->species[a] < 0 || s->species[a] >= s->n_species) {
+            set_err("species[%d] out of range", a);
+            return TDB_ERR_ARG;
+        }
+    if (!(std::isfinite(p->dt)) || p->dt == 0.0 || p->window < 1 || p->history_cap < 1 ||
+        p->scc_max_iter < 1 || !(p->scc_mix > 0 && p->scc_mix <= 1) || p->kT < 0 ||
+        p->precision < 0 || p->precision > 2) {
+        set_err("invalid params");
+        return TDB_ERR_ARG;
+    }
+    if (p->move_nuclei) {
+        set_err("moving nuclei are not implemented by this build");
+        return TDB_ERR_UNSUPPORTED;
+    }
+    if (p->precision == TDB_BF16X3) {
+        set_err("TDB_BF16X3 is not implemented by this build");
+        return TDB_ERR_UNSUPPORTED;
+    }
+    return TDB_OK;
+}
+
+void fill_host(Ctx& c, const tdb_system* s, const tdb_params* p) {
+    c.prm = *p;
+    c.nat = s->n_atoms;
+    c.nper = s->orbs_per_atom;
+    c.N = c.nat * c.nper;
+    c.nct = (c.N + kTile - 1) / kTile;
+    c.nspec = s->n_species;
+    c.n_electrons = s->n_electrons;
+    c.species.assign(s->species, s->species + c.nat);
+    c.R.assign(s->R, s->R + 3 * c.nat);
+    if (s->V)
+        c.V.assign(s->V, s->V + 3 * c.nat);
+    else
+        c.V.assign(3 * c.nat, 0.0);
+    c.eps_s.assign(s->eps_s, s->eps_s + c.nspec);
+    c.eps_p.assign(s->eps_p, s->eps_p + c.nspec);
+    c.U.assign(s->hubbard_U, s->hubbard_U + c.nspec);
+    c.mass.assign(s->mass, s->mass + c.nspec);
+    c.mp.t0 = s->t0;
+    c.mp.lam_H = s->lam_H;
+    c.mp.s0 = s->s0;
+    c.mp.lam_S = s->lam_S;
+    for (int k = 0; k < 4; ++k) c.mp.eta[k] = s->eta[k];
+    c.mp.rep_A = s->rep_A;
+    c.mp.rep_b = s->rep_b;
+}
+
+// Fermi-Dirac (kT > 0) or aufbau occupations, spin-degenerate (max 2 per level).
+void occupations(const std::vector<double>& eps, double ne, double kT, std::vector<double>& f) {
+    const int N = (int)eps.size();
+    f.assign(N, 0.0);
+    if (kT <= 0.0) {
+        const int k = (int)std::ceil(ne / 2.0);
+        const double ef = eps[std::max(k - 1, 0)];
+        int below = 0, shell = 0;
+        for (int i = 0; i < N; ++i) {
+            if (eps[i] < ef - 1e-8)
+                ++below;
+            else if (std::fabs(eps[i] - ef) <= 1e-8)
+                ++shell;
+        }
+        const double share = (ne - 2.0 * below) / shell;
+        for (int i = 0; i < N; ++i) {
+            if (eps[i] < ef - 1e-8)
+                f[i] = 2.0;
+            else if (std::fabs(eps[i] - ef) <= 1e-8)
+                f[i] = share;
+        }
+        return;
+    }
+    double lo = eps.front() - 50 * kT, hi = eps.back() + 50 * kT;
+    auto total = [&](double mu) {
+        double s = 0;
+        for (int i = 0; i < N; ++i) {
+            double x = (eps[i] - mu) / kT;
+            x = std::min(700.0, std::max(-700.0, x));
+            s += 2.0 / (1.0 + std::exp(x));
+        }
+        return s;
+    };
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (total(mid) > ne)
+            hi = mid;
+        else
+            lo = mid;
+    }
+    const double mu = 0.5 * (lo + hi);
+    for (int i = 0; i < N; ++i) {
+        double x = (eps[i] - mu) / kT;
+        x = std::min(700.0, std::max(-700.0, x));
+        f[i] = 2.0 / (1.0 + std::exp(x));
+    }
+}
+
+// Anderson mixing of the charge fluctuations (history of input/residual pairs).
+struct Anderson {
+    int hist;
+    double beta;
+    std::vector<std::vector<double>> xs, fs;
+    void next(std::vector<double>& x, const std::vector<double>& f) {
+        xs.push_back(x);
+        fs.push_back(f);
+        if ((int)xs.size() > hist) {
+            xs.erase(xs.begin());
+            fs.erase(fs.begin());
+        }
+        const int m = (int)xs.size() - 1, n = (int)x.size();
+        if (m < 1) {
+            for (int i = 0; i < n; ++i) x[i] += beta * f[i];
+            return;
+        }
+        // least squares: min |f - dF g|, dF[:, j] = f_{j+1} - f_j (normal equations,
+        // Tikhonov-guarded)
+        std::vector<double> A(m * m, 0.0), b(m, 0.0);
+        std::vector<std::vector<double>> dF(m, std::vector<double>(n)), dX(m, std::vector<double>(n));
+        for (int j = 0; j < m; ++j)
+            for (int i = 0; i < n; ++i) {
+                dF[j][i] = fs[j + 1][i] - fs[j][i];
+                dX[j][i] = xs[j + 1][i] - xs[j][i];
+            }
+        for (int a = 0; a < m; ++a) {
+            for (int c2 = 0; c2 < m; ++c2) {
+                double s = 0;
+                for (int i = 0; i < n; ++i) s += dF[a][i] * dF[c2][i];
+                A[a * m + c2] = s;
+            }
+            double s = 0;
+            for (int i = 0; i < n; ++i) s += dF[a][i] * f[i];
+            b[a] = s;
+        }
+        double tr = 0;
+        for (int a = 0; a < m; ++a) tr += A[a * m + a];
+        for (int a = 0; a < m; ++a) A[a * m + a] += 1e-12 * tr + 1e-300;
+        // Gaussian elimination with partial pivoting
+        std::vector<double> g(b);
+        std::vector<int> piv(m);
+        for (int col = 0; col < m; ++col) {
+            int p = col;
+            for (int r = col + 1; r < m; ++r)
+                if (std::fabs(A[r * m + col]) > std::fabs(A[p * m + col])) p = r;
+            if (p != col) {
+                for (int c2 = 0; c2 < m; ++c2) std::swap(A[p * m + c2], A[col * m + c2]);
+                std::swap(g[p], g[col]);
+            }
+            const double d = A[col * m + col];
+            for (int r = col + 1; r < m; ++r) {
+                const double fct = A[r * m + col] / d;
+                for (int c2 = col; c2 < m; ++c2) A[r * m + c2] -= fct * A[col * m + c2];
+                g[r] -= fct * g[col];
+            }
+        }
+        for (int col = m - 1; col >= 0; --col) {
+            double s = g[col];
+            for (int c2 = col + 1; c2 < m; ++c2) s -= A[col * m + c2] * g[c2];
+            g[col] = s / A[col * m + col];
+        }
+        for (int i = 0; i < n; ++i) {
+            double corr = 0;
+            for (int j = 0; j < m; ++j) corr += (dX[j][i] + beta * dF[j][i]) * g[j];
+            x[i] += beta * f[i] - corr;
+        }
+    }
+};
+
+tdb_status upload_field(Ctx& c) {
+    // staged through pinned memory; the previous upload has completed when the
+    // stream is synchronised by the caller (tdb_set_field synchronises)
+    FieldDev& f = *reinterpret_cast<FieldDev*>(c.h_pinned);
+    f = FieldDev{};
+    if (c.field_on) {
+        f.E0 = c.field.E0;
+        f.omega = c.field.omega;
+        f.phase = c.field.phase;
+        f.t_center = c.field.t_center;
+        f.fwhm = c.field.fwhm;
+        for (int k = 0; k < 3; ++k) f.dir[k] = c.field.dir[k];
+        f.envelope = c.field.envelope;
+        f.on = 1;
+    }
+    CK(cudaMemcpyAsync(&c.sc->field, &f, sizeof f, cudaMemcpyHostToDevice, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    return TDB_OK;
+}
+
+tdb_status upload_clock(Ctx& c, long long step, long long n_base, double t_base) {
+    DevScalars h{};
+    CK(cudaMemcpyAsync(&h, c.sc, sizeof h, cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    h.step = step;
+    h.n_base = n_base;
+    h.t_base = t_base;
+    h.dt = c.prm.dt;
+    h.hist_cap = c.prm.history_cap;
+    CK(cudaMemcpyAsync(c.sc, &h, sizeof h, cudaMemcpyHostToDevice, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    c.n = step;
+    return TDB_OK;
+}
+
+// After rho_n changes outside a step (ground state, kick, set_state): Mulliken
+// partials of rho_n and the reduced-precision operands.
+tdb_status refresh_derived(Ctx& c) {
+    launch_mulliken_partials(c.N, c.rho_re[c.cur], c.S, c.partial, c.stream);
+    CKL();
+    if (mixed(c)) {
+        const size_t NN = (size_t)c.N * c.N;
+        launch_sub_to_f32(NN, c.rho_re[c.cur], c.rho_ref, c.dre_f, c.stream);
+        launch_sub_to_f32(NN, c.rho_im[c.cur], nullptr, c.dim_f, c.stream);
+        CKL();
+    }
+    return TDB_OK;
+}
+
+// Optional per-kernel timing of an enqueued step: an event before each launch.
+struct StepTimer {
+    std::vector<cudaEvent_t> ev;
+    std::vector<const char*> names;
+    void mark(cudaStream_t st, const char* name) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        cudaEventRecord(e, st);
+        ev.push_back(e);
+        names.push_back(name);
+    }
+    ~StepTimer() {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
+};
+
+#define MARK(name) \
+    if (tm) tm->mark(c.stream, name)
+
+// Enqueue one propagation step for rho_n in buffer `cur` (eq:leapfrog, eq:eomrho).
+tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* tm = nullptr) {
+    const int prv = cur ^ 1;
+    const double factor = euler ? c.prm.dt : 2.0 * c.prm.dt;
+    const double* bre = euler ? c.rho_re[cur] : c.rho_re[prv];
+    const double* bim = euler ? c.rho_im[cur] : c.rho_im[prv];
+    int n = 0;
+    MARK("charges");
+    launch_charges(c, c.partial, c.q, c.dq, c.stream);
+    ++n;
+    MARK("potential");
+    launch_potential(c, c.gamma, c.dq, c.d_R, c.sc, c.v_orb, c.v_atom, c.gdq, c.hist, c.v_ref,
+                     mixed(c) ? c.dv_f : nullptr, c.stream);
+    ++n;
+    if (c.prm.precision == TDB_FP64) {
+        MARK("gemm_M_f64");
+        gemm_f64_ham(c.N, c.Sinv, c.H0, c.S, c.v_orb, c.M, c.stream);  // M = S^-1 H
+        MARK("gemm_Xre_f64");
+        gemm_f64(c.N, c.N, c.N, c.M, c.N, c.rho_re[cur], c.N, c.Xre, c.N, c.stream);
+        MARK("gemm_Xim_f64");
+        gemm_f64(c.N, c.N, c.N, c.M, c.N, c.rho_im[cur], c.N, c.Xim, c.N, c.stream);
+        n += 3;
+        MARK("update");
+        launch_update(c, c.Xre, c.Xim, bre, bim, c.rho_re[prv], c.rho_im[prv], factor, c.S,
+                      c.partial, c.sc, c.stream);
+        ++n;
+    } else {
+        const int N = c.N;
+        // delta M = S^-1 delta H (left half of [dM | M]), M = M_gs + delta M (right half)
+        MARK("gemm_dM_f32");
+        gemm_f32_dham(N, c.Sinv_f, c.S_f, c.dv_f, c.dM_f, 2 * N, nullptr, c.stream);
+        ++n;
+        MARK("add_M");
+        launch_add_f32_strided(N, c.Mgs_f, c.dM_f, 2 * N, c.M_f, 2 * N, c.stream);
+        ++n;
+        // X_re = dM rho_ref + M Re(rho - rho_ref);  X_im = M Im rho
+        MARK("gemm_Xre_f32");
+        gemm_f32_add(N, N, 2 * N, c.dM_f, 2 * N, c.rref_f, N, c.Xre_f, N, nullptr, c.stream);
+        MARK("gemm_Xim_f32");
+        gemm_f32_add(N, N, N, c.M_f, 2 * N, c.dim_f, N, c.Xim_f, N, nullptr, c.stream);
+        n += 2;
+        MARK("update");
+        launch_update_f32(c, c.Xre_f, c.Xim_f, bre, bim, c.rho_re[prv], c.rho_im[prv], factor,
+                          c.S, c.partial, c.sc, c.rho_ref, c.dre_f, c.dim_f, nullptr, nullptr,
+                          nullptr, nullptr, c.stream);
+        ++n;
+    }
+    MARK("end");
+    CKL();
+    if (launches) *launches = n;
+    return TDB_OK;
+}
+
+tdb_status ensure_graph(Ctx& c, int cur) {
+    if (c.graph[cur]) return TDB_OK;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
+    int nl = 0;
+    tdb_status st = enqueue_step(c, cur, false, &nl);
+    cudaError_t e = cudaStreamEndCapture(c.stream, &g);
+    if (st != TDB_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) {
+        set_err("graph capture failed: %s", cudaGetErrorString(e));
+        return TDB_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&c.graph[cur], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        set_err("graph instantiate failed: %s", cudaGetErrorString(e));
+        return TDB_ERR_CUDA;
+    }
+    c.graph_launches = nl;
+    return TDB_OK;
+}
+
+tdb_status build_inverse(Ctx& c) {
+    const int N = c.N;
+    CK(cudaMemcpyAsync(c.Sinv, c.S, sizeof(double) * N * N, cudaMemcpyDeviceToDevice, c.stream));
+    int lwork = 0;
+    CKS(cusolverDnDpotrf_bufferSize(c.solver, CUBLAS_FILL_MODE_LOWER, N, c.Sinv, N, &lwork));
+    int lwork2 = 0;
+    CKS(cusolverDnDpotri_bufferSize(c.solver, CUBLAS_FILL_MODE_LOWER, N, c.Sinv, N, &lwork2));
+    lwork = std::max(lwork, lwork2);
+    double* work = nullptr;
+    int* info = nullptr;
+    CK(cudaMalloc(&work, sizeof(double) * std::max(lwork, 1) + 256));
+    info = reinterpret_cast<int*>(reinterpret_cast<char*>(work) + sizeof(double) * std::max(lwork, 1));
+    tdb_status rc = TDB_OK;
+    int h_info = 0;
+    if (cusolverDnDpotrf(c.solver, CUBLAS_FILL_MODE_LOWER, N, c.Sinv, N, work, lwork, info) !=
+        CUSOLVER_STATUS_SUCCESS) {
+        set_err("cusolverDnDpotrf failed");
+        rc = TDB_ERR_CUDA;
+    }
+    if (rc == TDB_OK && cudaMemcpyAsync(&h_info, info, sizeof(int), cudaMemcpyDeviceToHost,
+                                        c.stream) == cudaSuccess &&
+        cudaStreamSynchronize(c.stream) == cudaSuccess && h_info != 0) {
+        set_err("overlap matrix is not positive definite (potrf info %d)", h_info);
+        rc = TDB_ERR_NOT_SPD;
+    }
+    if (rc == TDB_OK &&
+        cusolverDnDpotri(c.solver, CUBLAS_FILL_MODE_LOWER, N, c.Sinv, N, work, lwork, info) !=
+            CUSOLVER_STATUS_SUCCESS) {
+        set_err("cusolverDnDpotri failed");
+        rc = TDB_ERR_CUDA;
+    }
+    if (rc == TDB_OK) {
+        // column-major lower == row-major upper
+        launch_symmetrize_upper_to_lower(N, c.Sinv, c.stream);
+        if (cudaStreamSynchronize(c.stream) != cudaSuccess) rc = TDB_ERR_CUDA;
+    }
+    cudaFree(work);
+    return rc;
+}
+
+tdb_status check_ctx(tdb_ctx* c, bool need_gs, bool allow_sticky) {
+    if (!c) {
+        set_err("NULL context");
+        return TDB_ERR_ARG;
+    }
+    if (c->sticky && !allow_sticky) {
+        set_err("context is in an error state (numeric or timeout)");
+        return TDB_ERR_STATE;
+    }
+    if (need_gs && !c->have_gs) {
+        set_err("call tdb_ground_state (or tdb_set_state) first");
+        return TDB_ERR_STATE;
+    }
+    return TDB_OK;
+}
+
+constexpr unsigned long long kStateMagic = 0x7464625374617465ull;  // "tdbState"
+
+struct StateHeader {
+    unsigned long long magic;
+    long long N, nat, n, n_base;
+    double t_base, work, dt;
+    int euler_next, precision;
+};
+
+}  // namespace
+
+extern "C" {
+
+void tdb_default_params(tdb_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->dt = 0.2;
+    p->scc = 1;
+    p->move_nuclei = 0;
+    p->precision = TDB_FP64;
+    p->window = 100;
+    p->scc_tol = 1e-12;
+    p->scc_max_iter = 400;
+    p->kT = 0.0;
+    p->scc_mix = 0.1;
+    p->history_cap = 65536;
+    p->cuda_stream = nullptr;
+}
+
+size_t tdb_workspace_bytes(const tdb_system* sys, const tdb_params* prm) {
+    if (validate(sys, prm) != TDB_OK) return 0;
+    Ctx c;
+    fill_host(c, sys, prm);
+    return carve(c, nullptr);
+}
+
+tdb_status tdb_create(const tdb_system* sys, const tdb_params* prm, void* workspace,
+                      size_t workspace_bytes, tdb_ctx** out) {
+    if (!out) {
+        set_err("NULL out");
+        return TDB_ERR_ARG;
+    }
+    *out = nullptr;
+    TRY(validate(sys, prm));
+    tdb_ctx* c = new (std::nothrow) tdb_ctx();
+    if (!c) return TDB_ERR_NOMEM;
+    fill_host(*c, sys, prm);
+    const size_t need = carve(*c, nullptr);
+    auto fail = [&](tdb_status s) {
+        tdb_destroy(c);
+        return s;
+    };
+    c->h_pinned_bytes = 4096 + sizeof(double) * (size_t)c->nat;
+    if (cudaMallocHost(reinterpret_cast<void**>(&c->h_pinned), c->h_pinned_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        set_err("cudaMallocHost failed");
+        return fail(TDB_ERR_NOMEM);
+    }
+    if (prm->cuda_stream) {
+        c->stream = reinterpret_cast<cudaStream_t>(prm->cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            set_err("cudaStreamCreate failed");
+            return fail(TDB_ERR_CUDA);
+        }
+        c->own_stream = true;
+    }
+    if (workspace) {
+        if (workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) {
+            set_err("workspace too small (%zu < %zu) or not 256-byte aligned", workspace_bytes,
+                    need);
+            return fail(TDB_ERR_NOMEM);
+        }
+        c->ws = workspace;
+        c->ws_bytes = workspace_bytes;
+    } else {
+        if (cudaMalloc(&c->ws, need) != cudaSuccess) {
+            cudaGetLastError();
+            set_err("cudaMalloc of %zu bytes failed", need);
+            return fail(TDB_ERR_NOMEM);
+        }
+        c->own_ws = true;
+        c->ws_bytes = need;
+    }
+    char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(c->ws) + 255) & ~(uintptr_t)255);
+    carve(*c, base);
+    if (cudaMemsetAsync(c->ws, 0, c->ws_bytes, c->stream) != cudaSuccess) return fail(TDB_ERR_CUDA);
+    // per-atom / per-orbital host tables
+    std::vector<double> onsite(c->N), Ua(c->nat), ma(c->nat), q0(c->nat, c->n_electrons / c->nat);
+    for (int a = 0; a < c->nat; ++a) {
+        const int sp = c->species[a];
+        for (int i = 0; i < c->nper; ++i) onsite[a * c->nper + i] = i == 0 ? c->eps_s[sp] : c->eps_p[sp];
+        Ua[a] = c->U[sp];
+        ma[a] = c->mass[sp];
+    }
+    struct Up {
+        double* d;
+        const double* h;
+        size_t n;
+    } ups[] = {{c->d_R, c->R.data(), c->R.size()},       {c->d_V, c->V.data(), c->V.size()},
+               {c->d_onsite, onsite.data(), onsite.size()}, {c->d_U, Ua.data(), Ua.size()},
+               {c->d_mass, ma.data(), ma.size()},        {c->d_q0, q0.data(), q0.size()}};
+    for (auto& u : ups)
+        if (cudaMemcpyAsync(u.d, u.h, sizeof(double) * u.n, cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess)
+            return fail(TDB_ERR_CUDA);
+    if (upload_clock(*c, 0, 0, 0.0) != TDB_OK) return fail(TDB_ERR_CUDA);
+    if (upload_field(*c) != TDB_OK) return fail(TDB_ERR_CUDA);
+    launch_build_model(*c, c->d_R, c->S, c->H0, c->stream);
+    launch_build_gamma(*c, c->d_R, c->gamma, c->stream);
+    if (cudaGetLastError() != cudaSuccess) {
+        set_err("model build launch failed");
+        return fail(TDB_ERR_CUDA);
+    }
+    if (cusolverDnCreate(&c->solver) != CUSOLVER_STATUS_SUCCESS ||
+        cusolverDnSetStream(c->solver, c->stream) != CUSOLVER_STATUS_SUCCESS) {
+        set_err("cusolverDnCreate failed");
+        return fail(TDB_ERR_CUDA);
+    }
+    tdb_status s = build_inverse(*c);
+    if (s != TDB_OK) return fail(s);
+    if (mixed(*c)) {
+        const size_t NN = (size_t)c->N * c->N;
+        launch_f64_to_f32(NN, c->S, c->S_f, c->stream);
+        launch_f64_to_f32(NN, c->Sinv, c->Sinv_f, c->stream);
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        set_err("setup failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail(TDB_ERR_CUDA);
+    }
+    *out = c;
+    return TDB_OK;
+}
+
+tdb_status tdb_ground_state(tdb_ctx* c, int* iters_out, double* residual_out) {
+    TRY(check_ctx(c, false, false));
+    const int N = c->N, nat = c->nat;
+    double* d_eig = c->obs_out + 16;
+    double* d_occ = c->obs_out + 16 + N;
+    // the ground state is field-free; the field applies from t = 0 on
+    const bool saved_on = c->field_on;
+    c->field_on = false;
+    TRY(upload_field(*c));
+    TRY(upload_clock(*c, 0, 0, 0.0));
+    int lwork = 0;
+    CKS(cusolverDnDsygvd_bufferSize(c->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR,
+                                    CUBLAS_FILL_MODE_LOWER, N, c->Hs, N, c->M, N, d_eig, &lwork));
+    double* work = nullptr;
+    CK(cudaMalloc(&work, sizeof(double) * std::max(lwork, 1) + 256));
+    int* info = reinterpret_cast<int*>(reinterpret_cast<char*>(work) + sizeof(double) * std::max(lwork, 1));
+    std::vector<double> dq_in(nat, 0.0), dq_out(nat), eig(N), occ(N), resid(nat);
+    Anderson mixer{8, c->prm.scc_mix, {}, {}};
+    tdb_status rc = TDB_ERR_SCC_NOCONV;
+    double res = 0.0;
+    int it = 0;
+    for (it = 1; it <= c->prm.scc_max_iter; ++it) {
+        if (cudaMemcpyAsync(c->dq, dq_in.data(), sizeof(double) * nat, cudaMemcpyHostToDevice,
+                            c->stream) != cudaSuccess) {
+            rc = TDB_ERR_CUDA;
+            break;
+        }
+        launch_potential(*c, c->gamma, c->dq, c->d_R, c->sc, c->v_orb, c->v_atom, c->gdq, c->hist,
+                         c->v_ref, nullptr, c->stream);
+        launch_build_hamiltonian(N, c->H0, c->S, c->v_orb, c->Hs, c->stream);
+        cudaMemcpyAsync(c->M, c->S, sizeof(double) * N * N, cudaMemcpyDeviceToDevice, c->stream);
+        if (cusolverDnDsygvd(c->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR,
+                             CUBLAS_FILL_MODE_LOWER, N, c->Hs, N, c->M, N, d_eig, work, lwork,
+                             info) != CUSOLVER_STATUS_SUCCESS) {
+            set_err("cusolverDnDsygvd failed");
+            rc = TDB_ERR_CUDA;
+            break;
+        }
+        int h_info = 0;
+        cudaMemcpyAsync(&h_info, info, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+        cudaMemcpyAsync(eig.data(), d_eig, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream);
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            set_err("ground state: %s", cudaGetErrorString(cudaGetLastError()));
+            rc = TDB_ERR_CUDA;
+            break;
+        }
+        if (h_info != 0) {
+            set_err("generalised eigensolver failed (info %d)", h_info);
+            rc = h_info > N ? TDB_ERR_NOT_SPD : TDB_ERR_CUDA;
+            break;
+        }
+        occupations(eig, c->n_electrons, c->prm.kT, occ);
+        cudaMemcpyAsync(d_occ, occ.data(), sizeof(double) * N, cudaMemcpyHostToDevice, c->stream);
+        // rho_0 = sum_i f_i z_i z_i^T: Z (column-major) read row-major is Zr[i][:] = z_i
+        launch_transpose(N, c->Hs, c->Xim, c->stream);             // Xim[a][i] = z_i[a]
+        launch_scale_rows_f(N, c->Xim, d_occ, c->Xim, c->stream);  // * f_i
+        gemm_f64(N, N, N, c->Xim, N, c->Hs, N, c->rho_re[0], N, c->stream);
+        cudaMemsetAsync(c->rho_im[0], 0, sizeof(double) * N * N, c->stream);
+        launch_mulliken_partials(N, c->rho_re[0], c->S, c->partial, c->stream);
+        launch_charges(*c, c->partial, c->q, c->dq, c->stream);
+        cudaMemcpyAsync(dq_out.data(), c->dq, sizeof(double) * nat, cudaMemcpyDeviceToHost,
+                        c->stream);
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            set_err("ground state: %s", cudaGetErrorString(cudaGetLastError()));
+            rc = TDB_ERR_CUDA;
+            break;
+        }
+        res = 0.0;
+        for (int a = 0; a < nat; ++a) {
+            resid[a] = dq_out[a] - dq_in[a];
+            res = std::max(res, std::fabs(resid[a]));
+        }
+        if (!std::isfinite(res)) {
+            set_err("ground state produced NaN");
+            rc = TDB_ERR_NUMERIC;
+            break;
+        }
+        if (!c->prm.scc || res <= c->prm.scc_tol) {
+            if (!c->prm.scc) res = 0.0;
+            rc = TDB_OK;
+            break;
+        }
+        mixer.next(dq_in, resid);
+    }
+    cudaFree(work);
+    if (iters_out) *iters_out = std::min(it, c->prm.scc_max_iter);
+    if (residual_out) *residual_out = res;
+    c->field_on = saved_on;
+    TRY(upload_field(*c));
+    if (rc != TDB_OK) {
+        if (rc == TDB_ERR_SCC_NOCONV) set_err("SCC not converged: residual %.3e", res);
+        return rc;
+    }
+    c->spectral_width = eig[N - 1] - eig[0];
+    c->cur = 0;
+    c->euler_next = true;
+    c->have_gs = true;
+    c->work = 0.0;
+    // ground-state potential and operands of the reduced-precision forms:
+    // v_ref = v of the Hamiltonian whose eigenvectors built rho_0
+    CK(cudaMemcpyAsync(c->v_ref, c->v_orb, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->stream));
+    if (mixed(*c)) {
+        const size_t NN = (size_t)N * N;
+        CK(cudaMemcpyAsync(c->rho_ref, c->rho_re[0], sizeof(double) * NN,
+                           cudaMemcpyDeviceToDevice, c->stream));
+        gemm_f64_ham(N, c->Sinv, c->H0, c->S, c->v_ref, c->M, c->stream);  // M_gs
+        launch_f64_to_f32(NN, c->M, c->Mgs_f, c->stream);
+        launch_f64_to_f32(NN, c->rho_ref, c->rref_f, c->stream);
+        CKL();
+    }
+    TRY(refresh_derived(*c));
+    TRY(upload_clock(*c, 0, 0, 0.0));
+    CK(cudaStreamSynchronize(c->stream));
+    return TDB_OK;
+}
+
+tdb_status tdb_kick(tdb_ctx* c, double strength, const double dir[3]) {
+    TRY(check_ctx(c, true, false));
+    if (!dir || !std::isfinite(strength)) {
+        set_err("invalid kick");
+        return TDB_ERR_ARG;
+    }
+    const int N = c->N, cur = c->cur;
+    // eq:rhokick: T = e^{iV} rho S e^{-iV} S^-1,  rho(0+) = 1/2 (T + T^dagger)
+    gemm_f64(N, N, N, c->rho_re[cur], N, c->S, N, c->Xre, N, c->stream);
+    gemm_f64(N, N, N, c->rho_im[cur], N, c->S, N, c->Xim, N, c->stream);
+    launch_kick_phase(N, c->nper, c->d_R, strength, dir, c->Xre, c->Xim, c->M, c->Hs, c->stream);
+    gemm_f64(N, N, N, c->M, N, c->Sinv, N, c->Xre, N, c->stream);
+    gemm_f64(N, N, N, c->Hs, N, c->Sinv, N, c->Xim, N, c->stream);
+    launch_hermitian_half(N, c->Xre, c->Xim, c->rho_re[cur], c->rho_im[cur], c->stream);
+    CKL();
+    c->euler_next = true;
+    TRY(refresh_derived(*c));
+    CK(cudaStreamSynchronize(c->stream));
+    return TDB_OK;
+}
+
+tdb_status tdb_set_field(tdb_ctx* c, const tdb_field* f) {
+    TRY(check_ctx(c, false, false));
+    if (f) {
+        if (!std::isfinite(f->E0) || !std::isfinite(f->omega) || f->envelope < 0 ||
+            f->envelope > 2 || (f->envelope > 0 && !(f->fwhm > 0))) {
+            set_err("invalid field");
+            return TDB_ERR_ARG;
+        }
+        c->field = *f;
+        c->field_on = true;
+    } else {
+        c->field_on = false;
+    }
+    TRY(upload_field(*c));
+    CK(cudaStreamSynchronize(c->stream));
+    return TDB_OK;
+}
+
+tdb_status tdb_step(tdb_ctx* c, long n) {
+    TRY(check_ctx(c, true, false));
+    if (n < 0) {
+        set_err("negative step count");
+        return TDB_ERR_ARG;
+    }
+    if (std::fabs(c->prm.dt) * c->spectral_width >= 0.9) {
+        set_err("dt * spectral width = %.3f >= 0.9: leapfrog unstable",
+                std::fabs(c->prm.dt) * c->spectral_width);
+        return TDB_ERR_UNSTABLE;
+    }
+    long launches = 0;
+    for (long k = 0; k < n; ++k) {
+        if (c->euler_next) {
+            int nl = 0;
+            TRY(enqueue_step(*c, c->cur, true, &nl));
+            launches += nl;
+            c->euler_next = false;
+        } else {
+            TRY(ensure_graph(*c, c->cur));
+            CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
+            launches += c->graph_launches;
+        }
+        c->cur ^= 1;
+        c->n += 1;
+    }
+    c->last_launches = launches;
+    return TDB_OK;
+}
+
+tdb_status tdb_observables(tdb_ctx* c, tdb_obs* o, double* charges, double* forces) {
+    TRY(check_ctx(c, true, true));
+    if (!o) {
+        set_err("NULL obs");
+        return TDB_ERR_ARG;
+    }
+    if (forces) {
+        set_err("forces need moving-nuclei support, not in this build");
+        return TDB_ERR_UNSUPPORTED;
+    }
+    const int cur = c->cur;
+    launch_charges(*c, c->partial, c->q, c->dq, c->stream);
+    launch_potential(*c, c->gamma, c->dq, c->d_R, c->sc, c->v_orb, c->v_atom, c->gdq, c->hist,
+                     c->v_ref, nullptr, c->stream);
+    launch_obs_reduce(c->N, c->rho_re[cur], c->rho_im[cur], c->H0, c->S, c->obs_blocks, kObsBlocks,
+                      c->stream);
+    launch_obs_finish(kObsBlocks, c->obs_blocks, c->obs_out, c->stream);
+    launch_small_energies(*c, c->obs_out + 4, c->stream);
+    CKL();
+    double* red = reinterpret_cast<double*>(c->h_pinned + 256);
+    DevScalars* hs = reinterpret_cast<DevScalars*>(c->h_pinned + 512);
+    double* hq = reinterpret_cast<double*>(c->h_pinned + 4096);
+    static_assert(sizeof(DevScalars) <= 4096 - 512, "staging layout");
+    CK(cudaMemcpyAsync(red, c->obs_out, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(hs, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
+    if (charges)
+        CK(cudaMemcpyAsync(hq, c->q, sizeof(double) * c->nat, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (charges) std::memcpy(charges, hq, sizeof(double) * c->nat);
+    const DevScalars h = *hs;
+    std::memset(o, 0, sizeof *o);
+    o->step = (long)h.step;
+    o->t = h.t_base + (double)(h.step - h.n_base) * h.dt;
+    for (int k = 0; k < 3; ++k) o->dipole[k] = h.mu[k];
+    o->E_band = red[0];
+    o->trace_re = red[1];
+    o->trace_im = red[2];
+    o->herm_err = red[3];
+    o->E_coul = c->prm.scc ? red[4] : 0.0;
+    o->E_rep = red[5];
+    o->E_kin = red[6];
+    o->E_ext = h.e_ext;
+    o->work = c->work;
+    o->E_total = o->E_band + o->E_coul + o->E_rep + o->E_kin + o->E_ext;
+    return TDB_OK;
+}
+
+tdb_status tdb_dipole_history(tdb_ctx* c, double* out, long cap, long* n_out) {
+    TRY(check_ctx(c, true, true));
+    if (!out || cap < 1 || !n_out) {
+        set_err("invalid history request");
+        return TDB_ERR_ARG;
+    }
+    const long long hc = c->prm.history_cap;
+    const long long avail = std::min<long long>(std::max<long long>(c->n, 0), hc);
+    const long long m = std::min<long long>(avail, cap);
+    std::vector<double> ring(3 * hc);
+    CK(cudaMemcpyAsync(ring.data(), c->hist, sizeof(double) * 3 * hc, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    // steps n-m .. n-1 (n counted from the last ground state / set_state)
+    const long long dir = c->prm.dt > 0 ? 1 : 1;
+    (void)dir;
+    for (long long j = 0; j < m; ++j) {
+        const long long k = c->n - m + j;
+        long long slot = k % hc;
+        if (slot < 0) slot += hc;
+        for (int d = 0; d < 3; ++d) out[3 * j + d] = ring[3 * slot + d];
+    }
+    *n_out = (long)m;
+    return TDB_OK;
+}
+
+tdb_status tdb_get_rho(tdb_ctx* c, double* re, double* im, double* prev_re, double* prev_im) {
+    TRY(check_ctx(c, true, true));
+    const size_t b = sizeof(double) * c->N * c->N;
+    if (re) CK(cudaMemcpyAsync(re, c->rho_re[c->cur], b, cudaMemcpyDeviceToHost, c->stream));
+    if (im) CK(cudaMemcpyAsync(im, c->rho_im[c->cur], b, cudaMemcpyDeviceToHost, c->stream));
+    if (prev_re)
+        CK(cudaMemcpyAsync(prev_re, c->rho_re[c->cur ^ 1], b, cudaMemcpyDeviceToHost, c->stream));
+    if (prev_im)
+        CK(cudaMemcpyAsync(prev_im, c->rho_im[c->cur ^ 1], b, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return TDB_OK;
+}
+
+size_t tdb_state_bytes(const tdb_ctx* c) {
+    if (!c) return 0;
+    return sizeof(StateHeader) + 4 * sizeof(double) * (size_t)c->N * c->N +
+           6 * sizeof(double) * c->nat;
+}
+
+tdb_status tdb_get_state(tdb_ctx* c, void* buf, size_t bytes) {
+    TRY(check_ctx(c, true, true));
+    if (!buf || bytes < tdb_state_bytes(c)) {
+        set_err("state buffer too small");
+        return TDB_ERR_ARG;
+    }
+    DevScalars h{};
+    CK(cudaMemcpyAsync(&h, c->sc, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    StateHeader hd{kStateMagic, c->N, c->nat, h.step, h.n_base, h.t_base, c->work, c->prm.dt,
+                   c->euler_next ? 1 : 0, c->prm.precision};
+    char* p = static_cast<char*>(buf);
+    std::memcpy(p, &hd, sizeof hd);
+    p += sizeof hd;
+    const size_t b = sizeof(double) * c->N * c->N;
+    const int cur = c->cur, prv = cur ^ 1;
+    double* dst[4] = {reinterpret_cast<double*>(p), reinterpret_cast<double*>(p + b),
+                      reinterpret_cast<double*>(p + 2 * b), reinterpret_cast<double*>(p + 3 * b)};
+    CK(cudaMemcpyAsync(dst[0], c->rho_re[prv], b, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(dst[1], c->rho_im[prv], b, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(dst[2], c->rho_re[cur], b, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(dst[3], c->rho_im[cur], b, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    p += 4 * b;
+    std::memcpy(p, c->R.data(), sizeof(double) * 3 * c->nat);
+    std::memcpy(p + sizeof(double) * 3 * c->nat, c->V.data(), sizeof(double) * 3 * c->nat);
+    return TDB_OK;
+}
+
+tdb_status tdb_set_state(tdb_ctx* c, const void* buf, size_t bytes) {
+    TRY(check_ctx(c, false, false));
+    if (!buf || bytes < tdb_state_bytes(c)) {
+        set_err("state buffer too small");
+        return TDB_ERR_ARG;
+    }
+    StateHeader hd;
+    const char* p = static_cast<const char*>(buf);
+    std::memcpy(&hd, p, sizeof hd);
+    if (hd.magic != kStateMagic || hd.N != c->N || hd.nat != c->nat) {
+        set_err("state blob does not match this context");
+        return TDB_ERR_ARG;
+    }
+    if (!c->have_gs && mixed(*c)) {
+        set_err("reduced-precision forms need tdb_ground_state before tdb_set_state");
+        return TDB_ERR_STATE;
+    }
+    p += sizeof hd;
+    const size_t b = sizeof(double) * c->N * c->N;
+    const int cur = c->cur, prv = cur ^ 1;
+    CK(cudaMemcpyAsync(c->rho_re[prv], p, b, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->rho_im[prv], p + b, b, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->rho_re[cur], p + 2 * b, b, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->rho_im[cur], p + 3 * b, b, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->euler_next = hd.euler_next != 0;
+    c->work = hd.work;
+    c->have_gs = true;
+    TRY(refresh_derived(*c));
+    TRY(upload_clock(*c, hd.n, hd.n_base, hd.t_base));
+    return TDB_OK;
+}
+
+tdb_status tdb_check(tdb_ctx* c, double tol_trace) {
+    TRY(check_ctx(c, true, false));
+    tdb_obs o;
+    TRY(tdb_observables(c, &o, nullptr, nullptr));
+    const double rel = std::fabs(o.trace_re - c->n_electrons) / c->n_electrons;
+    if (!std::isfinite(o.trace_re) || !std::isfinite(o.E_band) || !std::isfinite(o.dipole[0]) ||
+        !std::isfinite(o.herm_err) || rel > tol_trace) {
+        set_err("invariant violated: |Tr(rho S) - Ne|/Ne = %.3e (tol %.3e)", rel, tol_trace);
+        c->sticky = true;
+        return TDB_ERR_NUMERIC;
+    }
+    return TDB_OK;
+}
+
+long tdb_last_launch_count(const tdb_ctx* c) { return c ? c->last_launches : 0; }
+
+tdb_status tdb_step_profiled(tdb_ctx* c, double* ms, const char** names, int cap, int* n_out) {
+    TRY(check_ctx(c, true, false));
+    if (!ms || !n_out || cap < 1) {
+        set_err("invalid profiling buffers");
+        return TDB_ERR_ARG;
+    }
+    if (std::fabs(c->prm.dt) * c->spectral_width >= 0.9) {
+        set_err("dt * spectral width >= 0.9: leapfrog unstable");
+        return TDB_ERR_UNSTABLE;
+    }
+    StepTimer tm;
+    int nl = 0;
+    TRY(enqueue_step(*c, c->cur, c->euler_next, &nl, &tm));
+    CK(cudaStreamSynchronize(c->stream));
+    const int k = std::min<int>(cap, (int)tm.ev.size() - 1);
+    for (int i = 0; i < k; ++i) {
+        float f = 0.f;
+        CK(cudaEventElapsedTime(&f, tm.ev[i], tm.ev[i + 1]));
+        ms[i] = f;
+        if (names) names[i] = tm.names[i];
+    }
+    *n_out = k;
+    c->euler_next = false;
+    c->cur ^= 1;
+    c->n += 1;
+    c->last_launches = nl;
+    return TDB_OK;
+}
+
+void tdb_destroy(tdb_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto& g : c->graph)
+        if (g) cudaGraphExecDestroy(g);
+    if (c->solver) cusolverDnDestroy(c->solver);
+    if (c->own_ws && c->ws) cudaFree(c->ws);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    delete c;
+}
+
+const char* tdb_status_string(tdb_status s) {
+    switch (s) {
+        case TDB_OK: return "ok";
+        case TDB_ERR_ARG: return "invalid argument";
+        case TDB_ERR_STATE: return "call out of order";
+        case TDB_ERR_CUDA: return "CUDA error";
+        case TDB_ERR_NOT_SPD: return "overlap not positive definite";
+        case TDB_ERR_SCC_NOCONV: return "SCC not converged";
+        case TDB_ERR_UNSTABLE: return "time step unstable";
+        case TDB_ERR_NUMERIC: return "numerical invariant violated";
+        case TDB_ERR_TIMEOUT: return "device wait timed out";
+        case TDB_ERR_NOMEM: return "out of device memory";
+        case TDB_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char* tdb_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,147 @@
+// Internal declarations of the tdb library (context layout and kernel launchers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cusolverDn.h>
+
+#include <string>
+#include <vector>
+
+#include "tdb.h"
+
+namespace tdb {
+
+constexpr int kTile = 32;          // tile edge of the O(N^2) kernels (update, Mulliken partials)
+
+// Laser field parameters as the kernels read them (eq:pumpf).
+struct FieldDev {
+    double E0, omega, phase, t_center, fwhm;
+    double dir[3];
+    int envelope;
+    int on;
+};
+
+// Device-resident scalars of a trajectory.  Graph-captured kernels read the
+// step counter from here, so a replayed graph sees the current step.
+struct DevScalars {
+    long long step;      // n of the current rho_n
+    long long n_base;    // t = t_base + (n - n_base) * dt
+    double t_base;
+    double dt;
+    FieldDev field;
+    double E[3];         // field at t_n (written by the potential kernel)
+    double mu[3];        // dipole of rho_n
+    double e_coul;       // 1/2 dq . gamma dq of rho_n
+    double e_ext;        // dq . (R E(t_n))
+    long long hist_cap;
+};
+
+// Parameters of the synthetic two-centre model.
+struct ModelParams {
+    double t0, lam_H, s0, lam_S;
+    double eta[4];
+    double rep_A, rep_b;
+};
+
+// A propagation context.  All device pointers point into one workspace.
+struct Ctx {
+    int nat = 0, nper = 0, N = 0, nspec = 0, nct = 0;
+    tdb_params prm{};
+    ModelParams mp{};
+    double n_electrons = 0;
+    std::vector<int> species;
+    std::vector<double> R, V, eps_s, eps_p, U, mass;
+
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    bool own_ws = false;
+
+    // device arrays (FP64)
+    double *d_R = nullptr, *d_V = nullptr;           // [nat][3]
+    double *d_onsite = nullptr;                     // [N] H0 diagonal
+    double *d_U = nullptr, *d_mass = nullptr;        // per atom
+    double *d_q0 = nullptr;                          // per atom reference population
+    double *S = nullptr, *Sinv = nullptr, *H0 = nullptr, *gamma = nullptr;
+    double *rho_re[2] = {nullptr, nullptr}, *rho_im[2] = {nullptr, nullptr};
+    double *Xre = nullptr, *Xim = nullptr, *M = nullptr, *Hs = nullptr;
+    double *partial = nullptr;                       // [nct][N] Mulliken row partial sums
+    double *q = nullptr, *dq = nullptr, *v_orb = nullptr, *v_atom = nullptr, *gdq = nullptr;
+    double *v_ref = nullptr;                         // [N] ground-state potential per orbital
+    double *hist = nullptr;                          // [cap][3]
+    double *obs_blocks = nullptr, *obs_out = nullptr;
+    DevScalars* sc = nullptr;
+
+    // reduced-precision operands (TDB_FP32 / TDB_BF16X3)
+    double *rho_ref = nullptr;                       // ground-state rho (real)
+    float *dv_f = nullptr;                           // [N] v - v_ref per orbital
+    float *S_f = nullptr, *Sinv_f = nullptr, *Mgs_f = nullptr, *rref_f = nullptr;
+    float *dM_f = nullptr, *M_f = nullptr;           // delta M, M = M_gs + delta M
+    float *dre_f = nullptr, *dim_f = nullptr;        // rho - rho_ref (Re, Im)
+    float *Xre_f = nullptr, *Xim_f = nullptr;
+
+    // host-side trajectory state
+    int cur = 0;                 // index of rho_n in rho_re/rho_im
+    bool have_gs = false, euler_next = true, sticky = false;
+    long long n = 0;             // host mirror of the step counter
+    long last_launches = 0;
+    double spectral_width = 0;   // of S^-1 H at the ground state
+    double work = 0;
+    tdb_field field{};
+    bool field_on = false;
+
+    // pinned host staging for the per-step host<->device traffic (field, observables)
+    char* h_pinned = nullptr;
+    size_t h_pinned_bytes = 0;
+
+    cusolverDnHandle_t solver = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int graph_launches = 0;      // kernels per captured step
+};
+
+// ---- kernels (launchers) ----
+void launch_build_model(const Ctx& c, const double* R, double* S, double* H0, cudaStream_t st);
+void launch_build_gamma(const Ctx& c, const double* R, double* gamma, cudaStream_t st);
+void launch_symmetrize_upper_to_lower(int N, double* A, cudaStream_t st);
+void launch_transpose(int N, const double* in, double* out, cudaStream_t st);
+void launch_mulliken_partials(int N, const double* rho_re, const double* S, double* partial,
+                              cudaStream_t st);
+void launch_charges(const Ctx& c, const double* partial, double* q, double* dq, cudaStream_t st);
+void launch_potential(const Ctx& c, const double* gamma, const double* dq, const double* R,
+                      DevScalars* sc, double* v_orb, double* v_atom, double* gdq, double* hist,
+                      const double* v_ref, float* dv_orb, cudaStream_t st);
+void launch_build_hamiltonian(int N, const double* H0, const double* S, const double* v_orb,
+                              double* H, cudaStream_t st);
+void launch_update(const Ctx& c, const double* Xre, const double* Xim, const double* base_re,
+                   const double* base_im, double* out_re, double* out_im, double factor,
+                   const double* S, double* partial, DevScalars* sc, cudaStream_t st);
+void launch_update_f32(const Ctx& c, const float* Xre, const float* Xim, const double* base_re,
+                       const double* base_im, double* out_re, double* out_im, double factor,
+                       const double* S, double* partial, DevScalars* sc, const double* rho_ref,
+                       float* op_re, float* op_im, __nv_bfloat16* opb_re_hi,
+                       __nv_bfloat16* opb_re_lo, __nv_bfloat16* opb_im_hi,
+                       __nv_bfloat16* opb_im_lo, cudaStream_t st);
+void launch_kick_phase(int N, int n_per, const double* R, double strength, const double* dir,
+                       const double* Pre, const double* Pim, double* Cre, double* Cim,
+                       cudaStream_t st);
+void launch_hermitian_half(int N, const double* Tre, const double* Tim, double* out_re,
+                           double* out_im, cudaStream_t st);
+void launch_obs_reduce(int N, const double* rho_re, const double* rho_im, const double* H0,
+                       const double* S, double* block_out, int n_blocks, cudaStream_t st);
+void launch_obs_finish(int n_blocks, const double* block_out, double* out4, cudaStream_t st);
+void launch_scale_rows_f(int N, const double* in, const double* f, double* out, cudaStream_t st);
+
+// GEMM: C[M x Ncol] = A[M x K] * B[K x Ncol], row-major, FP64 SIMT.
+enum class BKind { Dense = 0, Hamiltonian = 1 };
+void gemm_f64(int M, int Ncol, int K, const double* A, int lda, const double* B, int ldb,
+              double* C, int ldc, cudaStream_t st);
+// C = A * H with H_kj = H0_kj + 1/2 S_kj (v_k + v_j) formed while loading B (eq:hscc).
+void gemm_f64_ham(int N, const double* A, const double* H0, const double* S, const double* v_orb,
+                  double* C, cudaStream_t st);
+// FP32 SIMT: C = A * B (+ Cadd if non-null).
+void gemm_f32(int M, int Ncol, int K, const float* A, int lda, const float* B, int ldb, float* C,
+              int ldc, cudaStream_t st);
+
+}  // namespace tdb

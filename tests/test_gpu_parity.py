@@ -1,0 +1,209 @@
+"""Parity of the CUDA propagator (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances.  The FP64 form differs from the oracle only in summation order
+(~1e-16 relative per operation), so after hundreds of steps of a bounded
+oscillation the dipole, the charges and rho agree to ~1e-12; the tests allow
+1e-10 (rho, charges) and 1e-10 a.u. (dipole), four orders under the 1e-6 a.u.
+dipole target.  The reduced-precision forms act on rho - rho_gs with FP32
+products: their error is ~1e-7 relative to |rho - rho_gs| per step, and the
+tests hold them to the 1e-6 a.u. dipole target.
+"""
+import numpy as np
+import pytest
+
+from oracle import tdb_oracle as O
+from paper_1912_03174_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import __graft_entry__ as g
+    g.build()
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1912_03174_gb300 import binding
+    return binding
+
+
+def _gpu_run(B, sysm, run, n, precision="fp64"):
+    with B.Propagator(sysm, run, precision) as p:
+        it, res = p.setup()
+        rho0 = B.tdb_get_rho(p.ctx)
+        p.step(n)
+        hist = B.tdb_dipole_history(p.ctx, n)
+        obs = p.observables()
+        rho, prev = B.tdb_get_rho(p.ctx, prev=True)
+    return dict(it=it, res=res, rho0=rho0, hist=hist, obs=obs, rho=rho, prev=prev)
+
+
+def _oracle(sysm, run, n):
+    rho, gs, S, Sinv = O.setup(sysm, run)
+    tr = O.propagate(sysm, run, rho, n)
+    return rho, gs, tr
+
+
+def _compare(g, rho0, tr, n, tol_rho=1e-10, tol_mu=1e-10):
+    assert np.max(np.abs(g["rho0"] - rho0)) < tol_rho
+    mu = np.vstack([g["hist"], g["obs"]["dipole"][None, :]])
+    assert mu.shape == tr.dipole.shape
+    err_mu = np.max(np.abs(mu - tr.dipole))
+    assert err_mu < tol_mu, err_mu
+    assert np.max(np.abs(g["obs"]["charges"] - tr.charges[-1])) < tol_rho * 10
+    assert np.max(np.abs(g["rho"] - tr.rho)) < tol_rho
+    assert np.max(np.abs(g["prev"] - tr.rho_prev)) < tol_rho
+    return err_mu
+
+
+def test_c1_chain_full_run_matches_oracle(B):
+    sysm, run = I.chain_c1()
+    g = _gpu_run(B, sysm, run, run.n_steps)
+    rho0, gs, tr = _oracle(sysm, run, run.n_steps)
+    _compare(g, rho0, tr, run.n_steps)
+    # Tr(rho S) exact and rho exactly Hermitian on the device
+    assert abs(g["obs"]["trace_re"] - sysm.n_electrons) / sysm.n_electrons < 1e-12
+    assert g["obs"]["herm_err"] == 0.0
+
+
+@pytest.mark.parametrize("n_atoms,n_species,seed", [(10, 1, 3), (22, 2, 5), (33, 1, 8)])
+def test_scc_flakes_match_oracle(B, n_atoms, n_species, seed):
+    # N = 40, 88, 132: several 32-tiles and 64-GEMM tiles plus ragged tails
+    sysm = I.small_flake(n_atoms, seed=seed, n_species=n_species)
+    run = I.Run(dt=0.2, n_steps=0, scc=True, kick=1e-2, kT=I.SCC_KT)
+    n = 300
+    g = _gpu_run(B, sysm, run, n)
+    rho0, gs, tr = _oracle(sysm, run, n)
+    _compare(g, rho0, tr, n)
+    assert g["it"] >= 1 and g["res"] <= run.scc_tol
+
+
+def test_laser_field_matches_oracle(B):
+    sysm = I.small_flake(16, seed=12, n_species=2)
+    fld = I.Field(E0=0.02, omega=0.3, phase=0.3, t_center=20.0, fwhm=15.0, envelope=1,
+                  dir=np.array([0.6, 0.8, 0.0]))
+    run = I.Run(dt=0.2, n_steps=0, scc=True, kick=0.0, field=fld, kT=I.SCC_KT)
+    n = 400
+    g = _gpu_run(B, sysm, run, n)
+    rho0, gs, tr = _oracle(sysm, run, n)
+    _compare(g, rho0, tr, n)
+    assert abs(g["obs"]["E_ext"]) > 0
+
+
+def test_orbs_per_atom_one_and_two_level_system(B):
+    sysm = I.two_level(2.0, 0.25)
+    fld = I.Field(E0=1e-2, omega=0.5, phase=np.pi / 2, envelope=0)
+    run = I.Run(dt=0.2, n_steps=0, scc=False, field=fld)
+    g = _gpu_run(B, sysm, run, 500)
+    rho0, gs, tr = _oracle(sysm, run, 500)
+    _compare(g, rho0, tr, 500)
+
+
+def test_observables_energy_terms_match_oracle(B):
+    sysm = I.small_flake(12, seed=4, n_species=2)
+    run = I.Run(dt=0.2, n_steps=0, scc=True, kick=5e-2, kT=I.SCC_KT)
+    n = 100
+    g = _gpu_run(B, sysm, run, n)
+    rho0, gs, tr = _oracle(sysm, run, n)
+    assert abs(g["obs"]["E_total"] - tr.energy[-1]) < 1e-10
+    assert abs(g["obs"]["trace_re"] - sysm.n_electrons) < 1e-11
+    assert abs(g["obs"]["trace_im"]) < 1e-12
+    assert g["obs"]["step"] == n and abs(g["obs"]["t"] - n * run.dt) < 1e-12
+
+
+def test_checkpoint_resume_is_bitwise(B):
+    sysm = I.small_flake(12, seed=6)
+    run = I.Run(dt=0.2, n_steps=0, scc=True, kick=1e-2, kT=I.SCC_KT)
+    with B.Propagator(sysm, run) as a, B.Propagator(sysm, run) as b:
+        a.setup()
+        b.setup()
+        a.step(37)
+        blob = B.tdb_get_state(a.ctx)
+        B.tdb_set_state(b.ctx, blob)
+        a.step(50)
+        b.step(50)
+        ra = B.tdb_get_rho(a.ctx)
+        rb = B.tdb_get_rho(b.ctx)
+        assert np.array_equal(ra, rb)
+        oa, ob = a.observables(), b.observables()
+        assert np.array_equal(oa["dipole"], ob["dipole"]) and oa["step"] == ob["step"] == 87
+
+
+def test_replicas_are_bitwise_identical(B):
+    sysm = I.small_flake(20, seed=9)
+    run = I.Run(dt=0.2, n_steps=0, scc=True, kick=1e-2, kT=I.SCC_KT)
+    out = []
+    for _ in range(2):
+        with B.Propagator(sysm, run) as p:
+            p.setup()
+            p.step(120)
+            out.append(B.tdb_get_rho(p.ctx))
+    assert np.array_equal(out[0], out[1])
+
+
+def test_error_paths(B):
+    sysm, run = I.chain_c1()
+    with B.Propagator(sysm, run) as p:
+        with pytest.raises(B.TdbError) as e:
+            p.step(1)                       # before the ground state
+        assert e.value.status == 2
+        p.setup()
+        with pytest.raises(B.TdbError) as e:
+            B.tdb_step(p.ctx, -1)
+        assert e.value.status == 1
+    bad = I.Run(dt=5.0, n_steps=0, scc=False)   # dt * spectral width >> 0.9
+    with B.Propagator(sysm, bad) as p:
+        p.setup()
+        with pytest.raises(B.TdbError) as e:
+            p.step(1)
+        assert e.value.status == 6
+    s2 = I.small_flake(4, seed=1)
+    s2.species = np.array([0, 0, 0, 5], np.int32)
+    with pytest.raises(B.TdbError) as e:
+        B.tdb_create(s2, B.make_params(run))
+    assert e.value.status == 1
+
+
+def test_invariant_monitor_flags_a_corrupted_state(B):
+    # a state blob with a scaled density (host-made fault, no device fault)
+    sysm = I.small_flake(10, seed=2)
+    run = I.Run(dt=0.2, n_steps=0, scc=True, kick=1e-2, kT=I.SCC_KT)
+    with B.Propagator(sysm, run) as p:
+        p.setup()
+        p.step(5)
+        B.tdb_check(p.ctx, 1e-10)
+        blob = bytearray(B.tdb_get_state(p.ctx))
+        hdr = len(blob) - 4 * 8 * sysm.n_orb ** 2 - 6 * 8 * sysm.n_atoms
+        arr = np.frombuffer(bytes(blob[hdr:hdr + 4 * 8 * sysm.n_orb ** 2]), dtype=np.float64).copy()
+        arr *= 1.01
+        blob[hdr:hdr + arr.nbytes] = arr.tobytes()
+        B.tdb_set_state(p.ctx, bytes(blob))
+        with pytest.raises(B.TdbError) as e:
+            B.tdb_check(p.ctx, 1e-10)
+        assert e.value.status == 7
+        with pytest.raises(B.TdbError):
+            p.step(1)                       # sticky after a numeric error
+        p.observables()                     # still readable
+
+
+def test_c2_flake_full_size_prefix_fp64(B):
+    # the N = 1024 SCC flake at its full size: a 10-step prefix against the oracle
+    sysm, run = I.flake_c2()
+    n = 10
+    g = _gpu_run(B, sysm, run, n)
+    rho0, gs, tr = _oracle(sysm, run, n)
+    _compare(g, rho0, tr, n, tol_rho=1e-10, tol_mu=1e-10)
+
+
+@pytest.mark.parametrize("n_atoms", [10, 33])
+def test_fp32_form_matches_oracle(B, n_atoms):
+    sysm = I.small_flake(n_atoms, seed=8)
+    run = I.Run(dt=0.2, n_steps=0, scc=True, kick=1e-3, kT=I.SCC_KT)
+    n = 500
+    g = _gpu_run(B, sysm, run, n, "fp32")
+    rho0, gs, tr = _oracle(sysm, run, n)
+    mu = np.vstack([g["hist"], g["obs"]["dipole"][None, :]])
+    assert np.max(np.abs(mu - tr.dipole)) < 1e-6
+    assert np.max(np.abs(g["rho"] - tr.rho)) < 1e-6
+    assert abs(g["obs"]["trace_re"] - sysm.n_electrons) / sysm.n_electrons < 1e-8
+    assert g["obs"]["herm_err"] == 0.0
