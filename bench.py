@@ -39,12 +39,21 @@ KERNEL_FLOPS = {
     "gemm_dM_f32": lambda N: 2 * N ** 3,
     "gemm_Xre_f32": lambda N: 4 * N ** 3,
     "gemm_Xim_f32": lambda N: 2 * N ** 3,
+    # tensor-core split GEMMs: algorithmic flops (the three split products execute 3x this)
+    "tc_gemm_dM": lambda N: 2 * N ** 3,
+    "tc_gemm_X": lambda N: 6 * N ** 3,
 }
 # algorithmic bytes per launch of the O(N^2) kernels
 KERNEL_BYTES = {
     # reads X (re, im; both halves once), rho_{n-1}, S; writes rho_{n+1} (+ operands)
     "update_f64": lambda N: N * N * 8 * (2 + 2 + 1 + 2),
     "update_f32": lambda N: N * N * (4 * 2 + 8 * 2 + 8 + 8 * 2 + 4 * 2),
+    # reads X (2 x f32), rho_{n-1} (2 x f64), S, rho_ref; writes rho_{n+1} (2 x f64), 4 x 16-bit pieces
+    "update_tc": lambda N: N * N * (4 * 2 + 8 * 2 + 8 + 8 + 8 * 2 + 2 * 4),
+    # reads S (f64), writes 2 x 16-bit pieces
+    "split_dH": lambda N: N * N * (8 + 2 * 2),
+    # reads rho (2 x f64) and rho_ref, writes 6 x 16-bit pieces
+    "split_rho": lambda N: N * N * (8 * 3 + 6 * 2),
 }
 
 
@@ -209,7 +218,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--forms", default="fp64,fp32")
+    ap.add_argument("--forms", default="fp64,fp32,bf16x3,fp16x3,fp16x6")
     ap.add_argument("--atoms", type=int, default=256)
     ap.add_argument("--cpu-steps", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -268,7 +277,14 @@ def main():
     peaks, src = _peaks()
     N = sysm.n_orb
     sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
-    if name in KERNEL_FLOPS:
+    if name.startswith("tc_gemm"):
+        ach = KERNEL_FLOPS[name](N) / (t_ms * 1e-3) / 1e12
+        peak = peaks["bf16_tflops"]
+        roof = {"kernel": name, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_source": f"{src} dense bf16 burst (fp16 runs at the same rate)",
+                "executed_tflops": 3 * ach}
+    elif name in KERNEL_FLOPS:
         kind = "f64" if name.endswith("f64") else "f32"
         ach = KERNEL_FLOPS[name](N) / (t_ms * 1e-3) / 1e12
         peak = alu_peak_tflops(kind, peaks.get("sm_max_mhz", 2070.0))
@@ -277,20 +293,26 @@ def main():
                 "peak_source": f"derived from unit counts at {peaks.get('sm_max_mhz', 2070.0):.0f} MHz"
                 if kind == "f32" else "GB300 nominal FP64 1.25 TFLOP/s"}
     else:
-        key = "update_f64" if head == "fp64" else "update_f32"
+        key = {"fp64": "update_f64", "fp32": "update_f32"}.get(head, "update_tc")
+        key = name if name in KERNEL_BYTES else key
         ach = KERNEL_BYTES[key](N) / (t_ms * 1e-3) / 1e9
         roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": src}
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "bf16x3"}[head],
+        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "bf16x3",
+                                       "fp16x3": "fp16x3", "fp16x6": "fp16x6"}[head],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": N, "precision": head, "parallelism": "replicas",
                    "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)",
                    "fp64_steps_per_s": (1000.0 / ms64) if ms64 else None,
                    "speedup_vs_fp64": (ms64 / float(np.mean(r['ms']))) if ms64 else None,
                    "max_dipole_err_vs_fp64_au": err,
+                   "forms": {f: {"steps_per_s": 1000.0 / float(np.mean(res[f]["ms"])),
+                                 "max_dipole_err_vs_fp64_au": (float(np.max(np.abs(res[f]["hist"] - res["fp64"]["hist"])))
+                                                               if "fp64" in res else None)}
+                             for f in forms},
                    "kernel_ms": {f: res[f]["prof"] for f in forms}},
         "roofline": roof,
         "gpu_launches": int(r["launches"]),

@@ -60,8 +60,15 @@ typedef enum {
 typedef enum {
     TDB_FP64 = 0,     /* FP64 products (SIMT DFMA) */
     TDB_FP32 = 1,     /* FP32 products (SIMT FFMA) on the deviation rho - rho_gs */
-    TDB_BF16X3 = 2    /* tcgen05 tensor cores: BF16 hi/lo split, 3 products, FP32 accumulate,
-                         on the deviation rho - rho_gs */
+    TDB_BF16X3 = 2,   /* tcgen05 tensor cores, BF16 hi/lo pieces (~16 bits), 3 products,
+                         FP32 accumulate, on the deviation rho - rho_gs */
+    TDB_FP16X3 = 3,   /* tcgen05 tensor cores, power-of-two scaled FP16 hi/lo pieces
+                         (~22 bits), 3 products, FP32 accumulate, on rho - rho_gs.
+                         Requires |v - v_gs| < 16 Ha for every atom potential. */
+    TDB_FP16X6 = 4    /* tcgen05 tensor cores, each operand = 7-bit integer head + two FP16
+                         tails (~29 bits) under per-step power-of-two scales; the head
+                         products accumulate exactly (integer sums below 2^24), the five
+                         tail products in a second FP32 accumulator; on rho - rho_gs */
 } tdb_precision;
 
 /* The system (geometry and synthetic two-centre model).  Radial integrals:
@@ -187,6 +194,19 @@ long tdb_last_launch_count(const tdb_ctx* ctx);
  * ms[i] = device time of kernel i (milliseconds), names[i] = a static string
  * naming it (names may be NULL); *n_out = kernels timed (<= cap). */
 tdb_status tdb_step_profiled(tdb_ctx* ctx, double* ms, const char** names, int cap, int* n_out);
+
+/* C = A B through the tensor-core split-precision GEMM on its own, for
+ * validation and measurement (no context needed; allocates and frees its own
+ * device buffers).  A: M x K, B: K x N, C: M x N, row-major host doubles.
+ * fmt 0: FP16 hi/lo pieces with power-of-two scaling (~22 bits), products
+ *        A_hi B_hi + A_hi B_lo + A_lo B_hi in one FP32 accumulator (tcgen05, TMEM);
+ * fmt 1: the same with BF16 pieces (~16 bits);
+ * fmt 2: 7-bit integer head + two FP16 tails (~29 bits); head products summed
+ *        exactly in one accumulator (K <= 1024), five tail products in another.
+ * ms (may be NULL): kernel time.
+ * TDB_ERR_TIMEOUT if a bounded device wait expired. */
+tdb_status tdb_split_gemm(int M, int N, int K, const double* A, const double* B, int fmt, double* C,
+                          double* ms);
 
 void tdb_destroy(tdb_ctx* ctx);
 const char* tdb_status_string(tdb_status s);

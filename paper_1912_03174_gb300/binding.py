@@ -15,8 +15,9 @@ import numpy as np
 
 from . import build as _build
 
-TDB_FP64, TDB_FP32, TDB_BF16X3 = 0, 1, 2
-PRECISIONS = {"fp64": TDB_FP64, "fp32": TDB_FP32, "bf16x3": TDB_BF16X3}
+TDB_FP64, TDB_FP32, TDB_BF16X3, TDB_FP16X3, TDB_FP16X6 = 0, 1, 2, 3, 4
+PRECISIONS = {"fp64": TDB_FP64, "fp32": TDB_FP32, "bf16x3": TDB_BF16X3, "fp16x3": TDB_FP16X3,
+              "fp16x6": TDB_FP16X6}
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -76,6 +77,7 @@ SIGNATURES = {
     "tdb_last_launch_count": (ctypes.c_long, [ctypes.c_void_p]),
     "tdb_step_profiled": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_char_p), ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int)]),
+    "tdb_split_gemm": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_int, _dp, _dp]),
     "tdb_destroy": (None, [ctypes.c_void_p]),
     "tdb_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "tdb_last_error": (ctypes.c_char_p, []),
@@ -293,6 +295,19 @@ def tdb_step_profiled(ctx: Context, cap: int = 32):
     n = ctypes.c_int()
     _check("tdb_step_profiled", load().tdb_step_profiled(ctx.handle, _ptr(ms), names, cap, ctypes.byref(n)))
     return [(names[i].decode(), float(ms[i])) for i in range(n.value)]
+
+
+def tdb_split_gemm(A, B, fmt=0):
+    """C = A @ B on the tensor-core split GEMM; returns (C, kernel ms)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2
+    C = np.zeros((M, N))
+    ms = ctypes.c_double()
+    _check("tdb_split_gemm", load().tdb_split_gemm(M, N, K, _ptr(A), _ptr(B), int(fmt), _ptr(C), ctypes.byref(ms)))
+    return C, ms.value
 
 
 def tdb_destroy(ctx: Context):

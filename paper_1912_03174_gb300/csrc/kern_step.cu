@@ -3,6 +3,8 @@
 // helpers and observable reductions.  All arithmetic is FP64.
 #include <cmath>
 
+#include <cuda_fp16.h>
+
 #include "tdb_internal.h"
 
 namespace tdb {
@@ -31,6 +33,26 @@ __device__ void field_at(const FieldDev& f, double t, double E[3]) {
     E[0] = a * f.dir[0];
     E[1] = a * f.dir[1];
     E[2] = a * f.dir[2];
+}
+
+__device__ __forceinline__ uint16_t to16(float x, int bf16) {
+    if (bf16) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+    return __half_as_ushort(__float2half_rn(x));
+}
+__device__ __forceinline__ float from16(uint16_t x, int bf16) {
+    if (bf16) return __bfloat162float(__ushort_as_bfloat16(x));
+    return __half2float(__ushort_as_half(x));
+}
+
+// head (integer, |h| <= 127) + two FP16 tails of a scaled value
+__device__ __forceinline__ void split_head3(double x, uint16_t (&q)[3]) {
+    double h = rint(x);
+    h = fmin(fmax(h, -127.0), 127.0);
+    const double r = x - h;
+    const __half rh = __double2half(r);
+    q[0] = __half_as_ushort(__double2half(h));
+    q[1] = __half_as_ushort(rh);
+    q[2] = __half_as_ushort(__double2half(r - (double)__half2float(rh)));
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -165,8 +187,12 @@ __global__ void k_mulliken_partials(int N, const double* __restrict__ rre,
 
 __global__ void k_charges(int nat, int nper, int nct, int N, const double* __restrict__ partial,
                           const double* __restrict__ q0, double* __restrict__ q,
-                          double* __restrict__ dq) {
+                          double* __restrict__ dq, double* reset0, double* reset1) {
     const int A = blockIdx.x * blockDim.x + threadIdx.x;
+    if (A == 0) {
+        if (reset0) *reset0 = 0.0;
+        if (reset1) *reset1 = 0.0;
+    }
     if (A >= nat) return;
     double s = 0.0;
     for (int i = 0; i < nper; ++i)
@@ -183,7 +209,7 @@ __global__ void k_potential(int nat, int nper, int scc, const double* __restrict
                             DevScalars* __restrict__ sc, double* __restrict__ v_orb,
                             double* __restrict__ v_atom, double* __restrict__ gdq,
                             double* __restrict__ hist, const double* __restrict__ v_ref,
-                            float* __restrict__ dv_f) {
+                            float* __restrict__ dv_f, double* __restrict__ max_dv) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarp = blockDim.x >> 5;
     const long long n = sc->step;
@@ -204,6 +230,9 @@ __global__ void k_potential(int nat, int nper, int scc, const double* __restrict
         if (lane == 0) {
             v_atom[A] = vA;
             gdq[A] = s;
+            if (max_dv)
+                atomicMax(reinterpret_cast<unsigned long long*>(max_dv),
+                          (unsigned long long)__double_as_longlong(fabs(vA - v_ref[A * nper])));
         }
     }
     if (blockIdx.x == 0) {
@@ -272,12 +301,11 @@ __global__ void k_update(int N, int nct, const T* __restrict__ Xre, const T* __r
                          const double* __restrict__ bre, const double* __restrict__ bim,
                          double* __restrict__ ore, double* __restrict__ oim, double factor,
                          const double* __restrict__ S, double* __restrict__ partial,
-                         DevScalars* __restrict__ sc, const double* __restrict__ rho_ref,
-                         float* __restrict__ op_re, float* __restrict__ op_im,
-                         __nv_bfloat16* __restrict__ hre, __nv_bfloat16* __restrict__ lre,
-                         __nv_bfloat16* __restrict__ him, __nv_bfloat16* __restrict__ lim) {
+                         DevScalars* __restrict__ sc, UpdateOperands ops) {
     const int bi = blockIdx.y, bj = blockIdx.x;
     if (bi > bj) return;
+    const double op_scale = ops.scale;
+    double dmax = 0.0;   // max |rho_{n+1} - rho_ref| of this block (FP16X6 scale tracking)
     __shared__ T xr_ij[kTile][kTile + 1], xi_ij[kTile][kTile + 1];
     __shared__ T xr_ji[kTile][kTile + 1], xi_ji[kTile][kTile + 1];
     const int tx = threadIdx.x;
@@ -286,6 +314,7 @@ __global__ void k_update(int N, int nct, const T* __restrict__ Xre, const T* __r
         T a = 0, b = 0;
         if (r < N && c < N) {
             a = Xre[(size_t)r * N + c];
+            if (ops.Xre2) a += ops.Xre2[(size_t)r * N + c];
             b = Xim[(size_t)r * N + c];
         }
         xr_ij[y][tx] = a;
@@ -296,6 +325,7 @@ __global__ void k_update(int N, int nct, const T* __restrict__ Xre, const T* __r
         b = 0;
         if (r < N && c < N) {
             a = Xre[(size_t)r * N + c];
+            if (ops.Xre2) a += ops.Xre2[(size_t)r * N + c];
             b = Xim[(size_t)r * N + c];
         }
         xr_ji[y][tx] = a;
@@ -328,28 +358,40 @@ __global__ void k_update(int N, int nct, const T* __restrict__ Xre, const T* __r
                 ore[i] = nre;
                 oim[i] = nim;
                 pv = nre * S[i];
-                if (rho_ref) {
-                    const double d_re = nre - rho_ref[i];
-                    if (op_re) {
-                        op_re[i] = (float)d_re;
-                        op_im[i] = (float)nim;
+                if (ops.rho_ref) {
+                    const double d_re = nre - ops.rho_ref[i];
+                    if (ops.f_re) {
+                        ops.f_re[i] = (float)d_re;
+                        ops.f_im[i] = (float)nim;
                     }
-                    if (hre) {
-                        // rho operands are stored K-major for the tensor-core products:
-                        // Re is symmetric, the transposed Im is -Im.
-                        const __nv_bfloat16 h1 = __double2bfloat16(d_re);
-                        hre[i] = h1;
-                        lre[i] = __double2bfloat16(d_re - (double)__bfloat162float(h1));
-                        const double ni = -nim;
-                        const __nv_bfloat16 h2 = __double2bfloat16(ni);
-                        him[i] = h2;
-                        lim[i] = __double2bfloat16(ni - (double)__bfloat162float(h2));
+                    if (ops.dyn) dmax = fmax(dmax, fmax(fabs(d_re), fabs(nim)));
+                    if (ops.re[0]) {
+                        // operands of the tensor-core products are K-major: Re rho is
+                        // symmetric, and the transpose of Im rho is -Im rho
+                        const size_t jr = (size_t)r * ops.ld_re + c;
+                        const size_t ji = (size_t)r * ops.ld_im + c;
+                        {
+                            const float x = (float)(d_re * op_scale);
+                            const uint16_t h1 = to16(x, ops.bf16);
+                            ops.re[0][jr] = h1;
+                            ops.re[1][jr] = to16(x - from16(h1, ops.bf16), ops.bf16);
+                            const float y = (float)(-nim * op_scale);
+                            const uint16_t h2 = to16(y, ops.bf16);
+                            ops.im[0][ji] = h2;
+                            ops.im[1][ji] = to16(y - from16(h2, ops.bf16), ops.bf16);
+                        }
                     }
                 }
             }
             pv = warp_sum(pv);
             if (tx == 0 && r < N) partial[(size_t)tj * N + r] = pv;
         }
+    }
+    if (ops.dyn) {
+        for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        if (tx == 0)
+            atomicMax(reinterpret_cast<unsigned long long*>(&ops.dyn->max_drho[ops.cur ^ 1]),
+                      (unsigned long long)__double_as_longlong(dmax));
     }
     if (bi == 0 && bj == 0 && threadIdx.x == 0 && threadIdx.y == 0) sc->step += 1;
 }
@@ -489,18 +531,19 @@ void launch_mulliken_partials(int N, const double* rho_re, const double* S, doub
     k_mulliken_partials<<<dim3(nct, nct), b, 0, st>>>(N, rho_re, S, partial);
 }
 
-void launch_charges(const Ctx& c, const double* partial, double* q, double* dq, cudaStream_t st) {
+void launch_charges(const Ctx& c, const double* partial, double* q, double* dq, cudaStream_t st,
+                    double* reset0, double* reset1) {
     k_charges<<<(c.nat + 127) / 128, 128, 0, st>>>(c.nat, c.nper, c.nct, c.N, partial, c.d_q0, q,
-                                                   dq);
+                                                   dq, reset0, reset1);
 }
 
 void launch_potential(const Ctx& c, const double* gamma, const double* dq, const double* R,
                       DevScalars* sc, double* v_orb, double* v_atom, double* gdq, double* hist,
-                      const double* v_ref, float* dv_orb, cudaStream_t st) {
+                      const double* v_ref, float* dv_orb, cudaStream_t st, double* max_dv) {
     const int warps = 8;
     const int blocks = (c.nat + warps - 1) / warps;
     k_potential<<<blocks, warps * 32, 0, st>>>(c.nat, c.nper, c.prm.scc, gamma, dq, R, sc, v_orb,
-                                               v_atom, gdq, hist, v_ref, dv_orb);
+                                               v_atom, gdq, hist, v_ref, dv_orb, max_dv);
 }
 
 void launch_build_hamiltonian(int N, const double* H0, const double* S, const double* v_orb,
@@ -513,21 +556,18 @@ void launch_update(const Ctx& c, const double* Xre, const double* Xim, const dou
                    const double* base_im, double* out_re, double* out_im, double factor,
                    const double* S, double* partial, DevScalars* sc, cudaStream_t st) {
     dim3 b(kTile, 8);
-    k_update<double><<<dim3(c.nct, c.nct), b, 0, st>>>(
-        c.N, c.nct, Xre, Xim, base_re, base_im, out_re, out_im, factor, S, partial, sc, nullptr,
-        nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    k_update<double><<<dim3(c.nct, c.nct), b, 0, st>>>(c.N, c.nct, Xre, Xim, base_re, base_im,
+                                                       out_re, out_im, factor, S, partial, sc,
+                                                       UpdateOperands{});
 }
 
 void launch_update_f32(const Ctx& c, const float* Xre, const float* Xim, const double* base_re,
                        const double* base_im, double* out_re, double* out_im, double factor,
-                       const double* S, double* partial, DevScalars* sc, const double* rho_ref,
-                       float* op_re, float* op_im, __nv_bfloat16* opb_re_hi,
-                       __nv_bfloat16* opb_re_lo, __nv_bfloat16* opb_im_hi,
-                       __nv_bfloat16* opb_im_lo, cudaStream_t st) {
+                       const double* S, double* partial, DevScalars* sc,
+                       const UpdateOperands& ops, cudaStream_t st) {
     dim3 b(kTile, 8);
-    k_update<float><<<dim3(c.nct, c.nct), b, 0, st>>>(
-        c.N, c.nct, Xre, Xim, base_re, base_im, out_re, out_im, factor, S, partial, sc, rho_ref,
-        op_re, op_im, opb_re_hi, opb_re_lo, opb_im_hi, opb_im_lo);
+    k_update<float><<<dim3(c.nct, c.nct), b, 0, st>>>(c.N, c.nct, Xre, Xim, base_re, base_im,
+                                                      out_re, out_im, factor, S, partial, sc, ops);
 }
 
 void launch_kick_phase(int N, int n_per, const double* R, double strength, const double* dir,
@@ -631,7 +671,60 @@ __global__ void k_small_energies(int nat, const double* __restrict__ dq,
     }
 }
 
+// out = max |x| (out must start at 0): non-negative doubles order like their bit patterns
+__global__ void k_absmax(size_t n, const double* __restrict__ x, const double* __restrict__ sub,
+                         double* __restrict__ out) {
+    double m = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(sub ? x[i] - sub[i] : x[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(reinterpret_cast<unsigned long long*>(out), (unsigned long long)__double_as_longlong(m));
+}
+
+// FP16X6 operands of rho: pieces of s (Re rho - rho_ref) at column Np + c of the
+// [rho_ref | Re] block (row stride 2 Np) and of -s Im rho (row stride Np), with
+// s = pscale(max |rho - rho_ref|) from the maximum tracked by the update.
+__global__ void k_split_rho(int N, int Np, const double* __restrict__ rre,
+                            const double* __restrict__ rim, const double* __restrict__ rref,
+                            tc::DynScales* __restrict__ dyn, int slot, UpdateOperands ops) {
+    const double s = tc::pscale(dyn->max_drho[slot]);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+        dyn->s_rho = (float)s;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    if (r >= N || c >= N) return;
+    const size_t i = (size_t)r * N + c;
+    uint16_t q[3];
+    split_head3((rre[i] - rref[i]) * s, q);
+    const size_t jr = (size_t)r * 2 * Np + Np + c;
+    ops.re[0][jr] = q[0];
+    ops.re[1][jr] = q[1];
+    ops.re[2][jr] = q[2];
+    split_head3(-rim[i] * s, q);
+    const size_t ji = (size_t)r * Np + c;
+    ops.im[0][ji] = q[0];
+    ops.im[1][ji] = q[1];
+    ops.im[2][ji] = q[2];
+}
+
 }  // namespace
+
+void launch_split_rho(const Ctx& c, int slot, const double* rre, const double* rim,
+                      cudaStream_t st) {
+    UpdateOperands o;
+    for (int k = 0; k < 3; ++k) {
+        o.re[k] = c.pc_bre[k];
+        o.im[k] = c.pc_bim[k];
+    }
+    dim3 b(32, 8);
+    k_split_rho<<<grid2(c.N, c.N, b), b, 0, st>>>(c.N, c.Np, rre, rim, c.rho_ref, c.dyn, slot, o);
+}
+
+void launch_absmax(size_t n, const double* x, double* out, cudaStream_t st, const double* sub) {
+    k_absmax<<<608, 256, 0, st>>>(n, x, sub, out);
+}
 
 void launch_f64_to_f32(size_t n, const double* in, float* out, cudaStream_t st) {
     k_f64_to_f32<<<1216, 256, 0, st>>>(n, in, out);

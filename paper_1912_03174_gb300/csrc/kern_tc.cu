@@ -1,0 +1,518 @@
+// Tensor-core (tcgen05) split-precision GEMM for sm_103a.
+//
+// Operands are carried as 16-bit pieces (see tdb_tc.h for the two schemes).
+// kHiLo evaluates A_hi B_hi + A_hi B_lo + A_lo B_hi into one FP32 TMEM
+// accumulator.  The tensor core's FP32 accumulation truncates, which biases
+// long sums by ~K 2^-25 relative; kHead3 removes that bias from the dominant
+// term: the integer heads' products are summed exactly (integers below 2^24)
+// in their own accumulator and only the small tail products (~2^-7 of the
+// result) share the second, inexact one.
+//
+// Data path: TMA (cp.async.bulk.tensor, 128-byte swizzle) -> shared-memory
+// ring (mbarrier full/empty pairs) -> tcgen05.mma issued by one thread ->
+// TMEM accumulators (128 lanes x 128 columns each) -> tcgen05.ld -> epilogue
+// in registers -> global.  Both operands are K-major: A is M x K row-major
+// and B is given as its transpose Bt (N x K row-major).
+//
+// Every mbarrier wait is bounded; on time-out the kernel records an error
+// code, lets the issued MMAs drain, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "tdb_tc.h"
+
+namespace tdb {
+namespace tc {
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int TILE_BYTES = BM * BK * 2;   // 16 KiB per operand piece
+constexpr long long kSpinLimit = 1ll << 22;
+
+template <int SCHEME>
+struct Cfg;
+template <>
+struct Cfg<kHiLo> {
+    static constexpr int PIECES = 2, STAGES = 3, ACCS = 1;
+};
+template <>
+struct Cfg<kHead3> {
+    static constexpr int PIECES = 3, STAGES = 2, ACCS = 2;
+};
+template <int S>
+__host__ __device__ constexpr int stage_bytes() {
+    return 2 * Cfg<S>::PIECES * TILE_BYTES;
+}
+template <int S>
+__host__ __device__ constexpr int smem_total() {
+    return Cfg<S>::STAGES * stage_bytes<S>() + 1024 + 256;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false (and an error code) if the phase never completes.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+    for (long long i = 0; i < kSpinLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    if (err) atomicCAS(err, 0, code);
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+    d |= static_cast<uint64_t>(1) << 16;            // leading byte offset (unused for SW128 K-major)
+    d |= static_cast<uint64_t>(1024 >> 4) << 32;    // stride byte offset
+    d |= static_cast<uint64_t>(1) << 46;            // descriptor version
+    d |= static_cast<uint64_t>(2) << 61;            // 128-byte swizzle
+    return d;
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint16_t to16(float x, int bf16) {
+    if (bf16) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+    return __half_as_ushort(__float2half_rn(x));
+}
+__device__ __forceinline__ float from16(uint16_t x, int bf16) {
+    if (bf16) return __bfloat162float(__ushort_as_bfloat16(x));
+    return __half2float(__ushort_as_half(x));
+}
+
+// Pieces of one scaled value (see tdb_tc.h).  Returns false if a tail overflows FP16.
+template <int SCHEME>
+__device__ __forceinline__ bool split_value(double x, int bf16, uint16_t (&q)[3]) {
+    if (SCHEME == kHiLo) {
+        const float xf = static_cast<float>(x);
+        q[0] = to16(xf, bf16);
+        q[1] = to16(xf - from16(q[0], bf16), bf16);
+        q[2] = 0;
+        return fabsf(xf) < 65000.f;
+    } else {
+        double h = rint(x);
+        h = fmin(fmax(h, -127.0), 127.0);
+        const double r = x - h;
+        const __half rh = __double2half(r);
+        const double r2 = r - static_cast<double>(__half2float(rh));
+        q[0] = __half_as_ushort(__double2half(h));
+        q[1] = __half_as_ushort(rh);
+        q[2] = __half_as_ushort(__double2half(r2));
+        return fabs(r) < 65000.0;
+    }
+}
+
+template <int SCHEME>
+__global__ void __launch_bounds__(128, 1)
+    k_split_gemm(const __grid_constant__ Maps maps, GemmParams p) {
+    constexpr int PIECES = Cfg<SCHEME>::PIECES, STAGES = Cfg<SCHEME>::STAGES;
+    constexpr int ACCS = Cfg<SCHEME>::ACCS, SB = stage_bytes<SCHEME>();
+    constexpr uint32_t TMEM_COLS = ACCS == 1 ? 128u : 256u;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* gbase = smem_raw + (base - raw);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + STAGES * SB);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES),
+                   done = smem_u32(bars + 2 * STAGES);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const GemmPart& P = p.part[blockIdx.z];
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int nkb = (P.K + BK - 1) / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        fence_before();
+    }
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer: A pieces then B pieces of one 64-wide K block per stage
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb % STAGES, round = kb / STAGES;
+            if (kb >= STAGES && !mbar_wait(empty0 + 8 * s, (round - 1) & 1, p.err, 1)) break;
+            const uint32_t st = base + s * SB;
+            const uint32_t fb = full0 + 8 * s;
+            mbar_expect_tx(fb, SB);
+#pragma unroll
+            for (int q = 0; q < PIECES; ++q) {
+                tma_load_2d(st + q * TILE_BYTES, &maps.a[q], P.k0_a + kb * BK, m0, fb);
+                tma_load_2d(st + (PIECES + q) * TILE_BYTES, &maps.b[P.b_set][q], P.k0_b + kb * BK,
+                            n0, fb);
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        const uint32_t acc0 = tmem, acc1 = tmem + (ACCS == 2 ? 128u : 0u);
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb % STAGES, round = kb / STAGES;
+            if (!mbar_wait(full0 + 8 * s, round & 1, p.err, 2)) break;
+            fence_after();
+            const uint32_t st = base + s * SB;
+#pragma unroll
+            for (int k = 0; k < BK / 16; ++k) {
+                uint64_t a[PIECES], b[PIECES];
+#pragma unroll
+                for (int q = 0; q < PIECES; ++q) {
+                    a[q] = sdesc(st + q * TILE_BYTES + k * 32);
+                    b[q] = sdesc(st + (PIECES + q) * TILE_BYTES + k * 32);
+                }
+                const uint32_t first = (kb | k) != 0;
+                if (SCHEME == kHiLo) {
+                    mma_f16(acc0, a[0], b[0], p.idesc, first);
+                    mma_f16(acc0, a[0], b[1], p.idesc, 1);
+                    mma_f16(acc0, a[1], b[0], p.idesc, 1);
+                } else {
+                    mma_f16(acc0, a[0], b[0], p.idesc, first);      // exact integer sums
+                    mma_f16(acc1, a[0], b[1], p.idesc, first);
+                    mma_f16(acc1, a[1], b[0], p.idesc, 1);
+                    mma_f16(acc1, a[1], b[1], p.idesc, 1);
+                    mma_f16(acc1, a[0], b[PIECES - 1], p.idesc, 1);
+                    mma_f16(acc1, a[PIECES - 1], b[0], p.idesc, 1);
+                }
+            }
+            mma_commit(empty0 + 8 * s);
+        }
+        mma_commit(done);
+    }
+    __syncwarp();
+
+    // epilogue: warp w owns accumulator rows 32w .. 32w + 31
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0, p.err, 3) ? 1 : 0) != 0;
+    fence_after();
+    if (ok) {
+        const float sa = P.sa_dev ? *P.sa_dev : P.sa, sb = P.sb_dev ? *P.sb_dev : P.sb;
+        const float inv = 1.0f / (sa * sb);
+        const int row = m0 + warp * 32 + lane;
+        const uint32_t lane_off = static_cast<uint32_t>(warp * 32) << 16;
+        for (int c = 0; c < BN / 32; ++c) {
+            uint32_t r[32];
+            tmem_ld32(tmem + lane_off + c * 32, r);
+            float v[32];
+            if (ACCS == 2) {
+                uint32_t r1[32];
+                tmem_ld32(tmem + 128u + lane_off + c * 32, r1);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    v[j] = (__uint_as_float(r[j]) + __uint_as_float(r1[j])) * inv;
+            } else {
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]) * inv;
+            }
+            const int col0 = n0 + c * 32;
+            if (row >= p.M) continue;
+            if (P.mode == 0) {
+                float* out = P.C + static_cast<size_t>(row) * P.ldc + col0;
+                if (col0 + 32 <= p.N && (P.ldc & 3) == 0) {
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4)
+                        *reinterpret_cast<float4*>(out + j) =
+                            make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (col0 + j < p.N) out[j] = v[j];
+                }
+            } else {
+                // delta M and M = M_gs + delta M, both re-split into A pieces; 16-byte
+                // vector loads of M_gs and stores of 8 pieces at a time
+                const float s_dm = p.s_dm_dev ? *p.s_dm_dev : 1.0f;
+                const float* mg = p.Mgs + static_cast<size_t>(row) * p.ld_mgs + col0;
+                const size_t ob = static_cast<size_t>(row) * p.ld_out + col0;
+                bool fine = true;
+                const bool vec = col0 + 32 <= p.N && (p.ld_mgs & 3) == 0 && (p.ld_out & 7) == 0 &&
+                                 (p.col_m & 7) == 0;
+                if (vec) {
+#pragma unroll
+                    for (int j0 = 0; j0 < 32; j0 += 8) {
+                        const float4 g0 = *reinterpret_cast<const float4*>(mg + j0);
+                        const float4 g1 = *reinterpret_cast<const float4*>(mg + j0 + 4);
+                        const float gm[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+                        uint16_t qd[3][8], qm[3][8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            uint16_t q[3];
+                            fine &= split_value<SCHEME>(static_cast<double>(v[j0 + j]) * s_dm, p.bf16, q);
+#pragma unroll
+                            for (int t = 0; t < 3; ++t) qd[t][j] = q[t];
+                            fine &= split_value<SCHEME>(static_cast<double>(gm[j] + v[j0 + j]) * p.s_m,
+                                                        p.bf16, q);
+#pragma unroll
+                            for (int t = 0; t < 3; ++t) qm[t][j] = q[t];
+                        }
+#pragma unroll
+                        for (int t = 0; t < PIECES; ++t) {
+                            uint4 a, b;
+                            a.x = qd[t][0] | (uint32_t(qd[t][1]) << 16);
+                            a.y = qd[t][2] | (uint32_t(qd[t][3]) << 16);
+                            a.z = qd[t][4] | (uint32_t(qd[t][5]) << 16);
+                            a.w = qd[t][6] | (uint32_t(qd[t][7]) << 16);
+                            b.x = qm[t][0] | (uint32_t(qm[t][1]) << 16);
+                            b.y = qm[t][2] | (uint32_t(qm[t][3]) << 16);
+                            b.z = qm[t][4] | (uint32_t(qm[t][5]) << 16);
+                            b.w = qm[t][6] | (uint32_t(qm[t][7]) << 16);
+                            *reinterpret_cast<uint4*>(p.out[t] + ob + j0) = a;
+                            *reinterpret_cast<uint4*>(p.out[t] + ob + p.col_m + j0) = b;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = col0 + j;
+                        if (col >= p.N) continue;
+                        uint16_t q[3];
+                        fine &= split_value<SCHEME>(static_cast<double>(v[j]) * s_dm, p.bf16, q);
+#pragma unroll
+                        for (int t = 0; t < PIECES; ++t) p.out[t][ob + j] = q[t];
+                        fine &= split_value<SCHEME>(static_cast<double>(mg[j] + v[j]) * p.s_m,
+                                                    p.bf16, q);
+#pragma unroll
+                        for (int t = 0; t < PIECES; ++t) p.out[t][ob + p.col_m + j] = q[t];
+                    }
+                }
+                if (!fine && p.err) atomicCAS(p.err, 0, 4);
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 2) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ---- splitting kernels (FP64 -> scaled 16-bit pieces) ----
+
+struct Pieces {
+    uint16_t* p[3];
+};
+
+template <int SCHEME>
+__global__ void k_split(int rows, int cols, const double* __restrict__ in,
+                        const double* __restrict__ sub, int ld_in, float scale,
+                        const float* __restrict__ scale_dev, int sign, int bf16, Pieces out,
+                        int ld_out, int* err) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    if (r >= rows || c >= cols) return;
+    const size_t i = static_cast<size_t>(r) * ld_in + c;
+    const double v = sub ? in[i] - sub[i] : in[i];
+    const double s = scale_dev ? *scale_dev : scale;
+    uint16_t q[3];
+    const bool ok = split_value<SCHEME>(sign * v * s, bf16, q);
+    const size_t o = static_cast<size_t>(r) * ld_out + c;
+#pragma unroll
+    for (int t = 0; t < Cfg<SCHEME>::PIECES; ++t) out.p[t][o] = q[t];
+    if (!ok && err) atomicCAS(err, 0, 4);
+}
+
+// delta H_kj = 1/2 S_kj (dv_k + dv_j), dv = v - v_ref
+template <int SCHEME>
+__global__ void k_split_dham(int N, const double* __restrict__ S, const double* __restrict__ v,
+                             const double* __restrict__ vref, float scale_const, int bf16,
+                             Pieces out, int ld_out, DynScales* __restrict__ dyn, int* err) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    double s = scale_const;
+    if (dyn) {
+        // |delta H| <= max |dv| (|S_kj| <= 1), |delta M| <= ||S^-1||_inf max |dv|
+        const double m = dyn->max_dv;
+        s = pscale(m);
+        if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+            dyn->s_dh = static_cast<float>(s);
+            dyn->s_dm = pscale(m * dyn->sinv_norm);
+        }
+    }
+    if (r >= N || c >= N) return;
+    const double dvr = v[r] - vref[r], dvc = v[c] - vref[c];
+    uint16_t q[3];
+    const bool ok =
+        split_value<SCHEME>(0.5 * S[static_cast<size_t>(r) * N + c] * (dvr + dvc) * s, bf16, q);
+    const size_t o = static_cast<size_t>(r) * ld_out + c;
+#pragma unroll
+    for (int t = 0; t < Cfg<SCHEME>::PIECES; ++t) out.p[t][o] = q[t];
+    if (!ok && err) atomicCAS(err, 0, 4);
+}
+
+}  // namespace
+
+size_t smem_bytes(int scheme) {
+    return scheme == kHiLo ? smem_total<kHiLo>() : smem_total<kHead3>();
+}
+
+bool make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int bf16) {
+    using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static EncodeFn encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = reinterpret_cast<EncodeFn>(fn);
+    }
+    const cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+    const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 2};
+    const cuuint32_t box[2] = {BK, BM};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r =
+        encode(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+               const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+uint32_t idesc_f16(int bf16) {
+    // D = F32 (bits 4-5), A/B format (7-9, 10-12: 0 F16, 1 BF16), both K-major,
+    // N >> 3 at bit 17, M >> 4 at bit 24
+    return (1u << 4) | (static_cast<uint32_t>(bf16) << 7) | (static_cast<uint32_t>(bf16) << 10) |
+           (static_cast<uint32_t>(BN >> 3) << 17) | (static_cast<uint32_t>(BM >> 4) << 24);
+}
+
+cudaError_t prepare() {
+    cudaError_t e = cudaFuncSetAttribute(k_split_gemm<kHiLo>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_total<kHiLo>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_split_gemm<kHead3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem_total<kHead3>());
+}
+
+cudaError_t launch(int scheme, const Maps& m, const GemmParams& p, int nparts, cudaStream_t st) {
+    dim3 grid((p.N + BN - 1) / BN, (p.M + BM - 1) / BM, nparts);
+    if (scheme == kHiLo)
+        k_split_gemm<kHiLo><<<grid, 128, smem_total<kHiLo>(), st>>>(m, p);
+    else
+        k_split_gemm<kHead3><<<grid, 128, smem_total<kHead3>(), st>>>(m, p);
+    return cudaGetLastError();
+}
+
+void launch_split(int scheme, int rows, int cols, const double* in, int ld_in, float scale, int sign,
+                  int bf16, uint16_t* const* pieces, int ld_out, cudaStream_t st, const double* sub,
+                  const float* scale_dev, int* err) {
+    dim3 b(32, 8);
+    dim3 g((cols + 31) / 32, (rows + 7) / 8);
+    Pieces o{{pieces[0], pieces[1], scheme == kHead3 ? pieces[2] : nullptr}};
+    if (scheme == kHiLo)
+        k_split<kHiLo><<<g, b, 0, st>>>(rows, cols, in, sub, ld_in, scale, scale_dev, sign, bf16, o,
+                                        ld_out, err);
+    else
+        k_split<kHead3><<<g, b, 0, st>>>(rows, cols, in, sub, ld_in, scale, scale_dev, sign, bf16,
+                                         o, ld_out, err);
+}
+
+void launch_split_dham(int scheme, int N, const double* S, const double* v, const double* vref,
+                       float scale, int bf16, uint16_t* const* pieces, int ld_out, DynScales* dyn,
+                       cudaStream_t st, int* err) {
+    dim3 b(32, 8);
+    dim3 g((N + 31) / 32, (N + 7) / 8);
+    Pieces o{{pieces[0], pieces[1], scheme == kHead3 ? pieces[2] : nullptr}};
+    if (scheme == kHiLo)
+        k_split_dham<kHiLo><<<g, b, 0, st>>>(N, S, v, vref, scale, bf16, o, ld_out, nullptr, err);
+    else
+        k_split_dham<kHead3><<<g, b, 0, st>>>(N, S, v, vref, scale, bf16, o, ld_out, dyn, err);
+}
+
+}  // namespace tc
+}  // namespace tdb

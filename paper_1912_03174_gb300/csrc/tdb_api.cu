@@ -21,6 +21,8 @@ void launch_sub_to_f32(size_t n, const double* a, const double* b, float* out, c
 void launch_add_f32_strided(int N, const float* a, const float* b, int ldb, float* out, int ldo,
                             cudaStream_t st);
 void launch_small_energies(const Ctx& c, double* out, cudaStream_t st);
+void launch_absmax(size_t n, const double* x, double* out, cudaStream_t st,
+                   const double* sub = nullptr);
 }  // namespace tdb
 
 using namespace tdb;
@@ -89,6 +91,18 @@ struct Carver {
 };
 
 bool mixed(const Ctx& c) { return c.prm.precision != TDB_FP64; }
+bool tensor(const Ctx& c) {
+    return c.prm.precision == TDB_BF16X3 || c.prm.precision == TDB_FP16X3 ||
+           c.prm.precision == TDB_FP16X6;
+}
+bool head3(const Ctx& c) { return c.prm.precision == TDB_FP16X6; }
+int piece_bf16(const Ctx& c) { return c.prm.precision == TDB_BF16X3 ? 1 : 0; }
+
+// 2^floor(log2(target / m)): the power-of-two scale that maps magnitude m near target
+float pow2_scale(double m, double target) {
+    if (!(m > 0)) return 1.0f;
+    return (float)std::ldexp(1.0, (int)std::floor(std::log2(target / m)));
+}
 
 size_t carve(Ctx& c, char* base) {
     Carver k{base};
@@ -124,18 +138,36 @@ size_t carve(Ctx& c, char* base) {
     c.sc = k.take<DevScalars>(1);
     if (mixed(c)) {
         c.rho_ref = k.take<double>(NN);
+        c.Mgs_f = k.take<float>(NN);
+        c.Xre_f = k.take<float>(NN);
+        c.Xim_f = k.take<float>(NN);
+    }
+    if (c.prm.precision == TDB_FP32) {
         c.dv_f = k.take<float>(N);
         c.S_f = k.take<float>(NN);
         c.Sinv_f = k.take<float>(NN);
-        c.Mgs_f = k.take<float>(NN);
         c.dM_f = k.take<float>(2 * NN);     // [delta M | M], row stride 2N
         c.M_f = c.dM_f ? c.dM_f + N : nullptr;
         c.rref_f = k.take<float>(2 * NN);   // [rho_ref ; Re(rho - rho_ref)] stacked, 2N x N
         c.dre_f = c.rref_f ? c.rref_f + NN : nullptr;
         c.dim_f = k.take<float>(NN);
-        c.Xre_f = k.take<float>(NN);
-        c.Xim_f = k.take<float>(NN);
     }
+    if (tensor(c)) {
+        const size_t Np = (N + 63) / 64 * 64;
+        c.Np = (int)Np;
+        c.scheme = head3(c) ? tc::kHead3 : tc::kHiLo;
+        c.npieces = head3(c) ? 3 : 2;
+        for (int q = 0; q < c.npieces; ++q) {
+            c.pc_sinv[q] = k.take<uint16_t>(N * Np);
+            c.pc_dh[q] = k.take<uint16_t>(N * Np);
+            c.pc_am[q] = k.take<uint16_t>(2 * N * Np);
+            c.pc_bre[q] = k.take<uint16_t>(2 * N * Np);
+            c.pc_bim[q] = k.take<uint16_t>(N * Np);
+        }
+        if (head3(c)) c.Xa_f = k.take<float>(NN);
+        c.dyn = k.take<tc::DynScales>(1);
+    }
+    c.d_err = k.take<int>(4);
     return k.off + 256;
 }
 
@@ -165,7 +197,7 @@ tdb_status validate(const tdb_system* s, const tdb_params* p) {
         }
     if (!(std::isfinite(p->dt)) || p->dt == 0.0 || p->window < 1 || p->history_cap < 1 ||
         p->scc_max_iter < 1 || !(p->scc_mix > 0 && p->scc_mix <= 1) || p->kT < 0 ||
-        p->precision < 0 || p->precision > 2) {
+        p->precision < 0 || p->precision > 4) {
         set_err("invalid params");
         return TDB_ERR_ARG;
     }
@@ -173,8 +205,9 @@ tdb_status validate(const tdb_system* s, const tdb_params* p) {
         set_err("moving nuclei are not implemented by this build");
         return TDB_ERR_UNSUPPORTED;
     }
-    if (p->precision == TDB_BF16X3) {
-        set_err("TDB_BF16X3 is not implemented by this build");
+    if (p->precision == TDB_FP16X6 && N > 1024) {
+        // the integer head products of a K = N sum are exact only while K * 127^2 < 2^24
+        set_err("TDB_FP16X6 supports N <= 1024 in this build");
         return TDB_ERR_UNSUPPORTED;
     }
     return TDB_OK;
@@ -365,11 +398,97 @@ tdb_status upload_clock(Ctx& c, long long step, long long n_base, double t_base)
 tdb_status refresh_derived(Ctx& c) {
     launch_mulliken_partials(c.N, c.rho_re[c.cur], c.S, c.partial, c.stream);
     CKL();
-    if (mixed(c)) {
+    if (c.prm.precision == TDB_FP32) {
         const size_t NN = (size_t)c.N * c.N;
         launch_sub_to_f32(NN, c.rho_re[c.cur], c.rho_ref, c.dre_f, c.stream);
         launch_sub_to_f32(NN, c.rho_im[c.cur], nullptr, c.dim_f, c.stream);
         CKL();
+    }
+    if (tensor(c)) {
+        const int N = c.N, b = piece_bf16(c);
+        if (head3(c)) {
+            // exact scale of the current deviation, then its pieces
+            CK(cudaMemsetAsync(&c.dyn->max_drho[c.cur], 0, sizeof(double), c.stream));
+            launch_absmax((size_t)N * N, c.rho_re[c.cur], &c.dyn->max_drho[c.cur], c.stream,
+                          c.rho_ref);
+            launch_absmax((size_t)N * N, c.rho_im[c.cur], &c.dyn->max_drho[c.cur], c.stream);
+            launch_split_rho(c, c.cur, c.rho_re[c.cur], c.rho_im[c.cur], c.stream);
+        } else {
+            uint16_t* re[3] = {c.pc_bre[0] + c.Np, c.pc_bre[1] + c.Np, nullptr};
+            tc::launch_split(c.scheme, N, N, c.rho_re[c.cur], N, c.s_rho, 1, b, re, 2 * c.Np,
+                             c.stream, c.rho_ref);
+            tc::launch_split(c.scheme, N, N, c.rho_im[c.cur], N, c.s_rho, -1, b, c.pc_bim, c.Np,
+                             c.stream);
+        }
+        CKL();
+    }
+    return TDB_OK;
+}
+
+// Tensor-core form setup after the ground state: scales, constant operands.
+tdb_status setup_tensor(Ctx& c) {
+    const int N = c.N, b = piece_bf16(c);
+    const size_t NN = (size_t)N * N;
+    double* dmax = c.obs_out + 8;
+    double mx[3];
+    const double* srcs[3] = {c.Sinv, c.M, c.rho_ref};
+    for (int i = 0; i < 3; ++i) {
+        CK(cudaMemsetAsync(dmax, 0, sizeof(double), c.stream));
+        launch_absmax(NN, srcs[i], dmax, c.stream);
+        CK(cudaMemcpyAsync(&mx[i], dmax, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        CK(cudaStreamSynchronize(c.stream));
+    }
+    tc::DynScales d{};
+    if (b) {
+        c.s_sinv = c.s_dh = c.s_m = c.s_rho = c.s_ref = 1.0f;
+    } else if (!head3(c)) {
+        c.s_sinv = pow2_scale(mx[0], 2048.0);
+        c.s_dh = 4096.0f;                              // |delta H| < 16 Ha
+        c.s_m = pow2_scale(std::max(mx[1], 1.0 / 16), 1024.0);
+        c.s_rho = c.s_ref = pow2_scale(std::max(mx[2], 0.5), 1024.0);
+    } else {
+        // integer heads: a matrix bound m maps to (32, 64], leaving 2x to the +-127 clamp
+        c.s_sinv = tc::pscale(mx[0]);
+        c.s_m = tc::pscale(mx[1] * 1.5);
+        c.s_ref = tc::pscale(mx[2]);
+        // ||S^-1||_inf bounds |delta M| / max |delta H|
+        std::vector<double> h(NN);
+        CK(cudaMemcpy(h.data(), c.Sinv, sizeof(double) * NN, cudaMemcpyDeviceToHost));
+        double nrm = 0;
+        for (int r = 0; r < N; ++r) {
+            double sum = 0;
+            for (int k = 0; k < N; ++k) sum += std::fabs(h[(size_t)r * N + k]);
+            nrm = std::max(nrm, sum);
+        }
+        d.sinv_norm = nrm;
+    }
+    d.s_dh = c.s_dh;
+    d.s_dm = c.s_m;     // hi/lo schemes: delta M shares the scale of M
+    d.s_rho = c.s_rho;
+    CK(cudaMemcpyAsync(c.dyn, &d, sizeof d, cudaMemcpyHostToDevice, c.stream));
+    tc::launch_split(c.scheme, N, N, c.Sinv, N, c.s_sinv, 1, b, c.pc_sinv, c.Np, c.stream, nullptr,
+                     nullptr, c.d_err);
+    tc::launch_split(c.scheme, N, N, c.rho_ref, N, c.s_ref, 1, b, c.pc_bre, 2 * c.Np, c.stream,
+                     nullptr, nullptr, c.d_err);
+    CKL();
+    CK(cudaStreamSynchronize(c.stream));
+    return TDB_OK;
+}
+
+tdb_status build_maps(Ctx& c) {
+    CK(tc::prepare());
+    const int N = c.N, Np = c.Np, b = piece_bf16(c);
+    bool ok = true;
+    for (int q = 0; q < c.npieces; ++q) {
+        ok = ok && tc::make_map(&c.maps_dm.a[q], c.pc_sinv[q], N, N, Np, b) &&
+             tc::make_map(&c.maps_dm.b[0][q], c.pc_dh[q], N, N, Np, b) &&
+             tc::make_map(&c.maps_x.a[q], c.pc_am[q], N, 2 * Np, 2 * Np, b) &&
+             tc::make_map(&c.maps_x.b[0][q], c.pc_bre[q], N, 2 * Np, 2 * Np, b) &&
+             tc::make_map(&c.maps_x.b[1][q], c.pc_bim[q], N, Np, Np, b);
+    }
+    if (!ok) {
+        set_err("cuTensorMapEncodeTiled failed");
+        return TDB_ERR_CUDA;
     }
     return TDB_OK;
 }
@@ -401,11 +520,14 @@ tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* t
     const double* bim = euler ? c.rho_im[cur] : c.rho_im[prv];
     int n = 0;
     MARK("charges");
-    launch_charges(c, c.partial, c.q, c.dq, c.stream);
+    if (head3(c))
+        launch_charges(c, c.partial, c.q, c.dq, c.stream, &c.dyn->max_dv, &c.dyn->max_drho[prv]);
+    else
+        launch_charges(c, c.partial, c.q, c.dq, c.stream);
     ++n;
     MARK("potential");
     launch_potential(c, c.gamma, c.dq, c.d_R, c.sc, c.v_orb, c.v_atom, c.gdq, c.hist, c.v_ref,
-                     mixed(c) ? c.dv_f : nullptr, c.stream);
+                     mixed(c) ? c.dv_f : nullptr, c.stream, head3(c) ? &c.dyn->max_dv : nullptr);
     ++n;
     if (c.prm.precision == TDB_FP64) {
         MARK("gemm_M_f64");
@@ -419,6 +541,80 @@ tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* t
         launch_update(c, c.Xre, c.Xim, bre, bim, c.rho_re[prv], c.rho_im[prv], factor, c.S,
                       c.partial, c.sc, c.stream);
         ++n;
+    } else if (tensor(c)) {
+        const int N = c.N, Np = c.Np, b = piece_bf16(c);
+        const bool h3 = head3(c);
+        MARK("split_dH");
+        tc::launch_split_dham(c.scheme, N, c.S, c.v_orb, c.v_ref, c.s_dh, b, c.pc_dh, Np,
+                              h3 ? c.dyn : nullptr, c.stream, c.d_err);
+        ++n;
+        // delta M = S^-1 delta H; the epilogue writes the pieces of [delta M | M_gs + delta M]
+        tc::GemmParams g{};
+        g.M = N;
+        g.N = N;
+        g.part[0] = {0, 0, N, 1, nullptr, 0, c.s_sinv, 0.f, nullptr, h3 ? &c.dyn->s_dh : nullptr, 0};
+        g.part[0].sb = c.s_dh;
+        g.idesc = tc::idesc_f16(b);
+        g.bf16 = b;
+        g.Mgs = c.Mgs_f;
+        g.ld_mgs = N;
+        for (int q = 0; q < 3; ++q) g.out[q] = c.pc_am[q];
+        g.ld_out = 2 * Np;
+        g.col_m = Np;
+        g.s_m = c.s_m;
+        g.s_dm_dev = &c.dyn->s_dm;
+        g.err = c.d_err;
+        MARK("tc_gemm_dM");
+        CK(tc::launch(c.scheme, c.maps_dm, g, 1, c.stream));
+        ++n;
+        tc::GemmParams x{};
+        x.M = N;
+        x.N = N;
+        x.idesc = g.idesc;
+        x.bf16 = b;
+        x.err = c.d_err;
+        int nparts;
+        if (h3) {
+            // X_a = dM rho_ref, X_re = M Re(rho - rho_ref), X_im = M Im(rho): each K = N
+            x.part[0] = {0, 0, N, 0, c.Xa_f, N, 0.f, c.s_ref, &c.dyn->s_dm, nullptr, 0};
+            x.part[1] = {Np, Np, N, 0, c.Xre_f, N, c.s_m, 0.f, nullptr, &c.dyn->s_rho, 0};
+            x.part[2] = {Np, 0, N, 0, c.Xim_f, N, c.s_m, 0.f, nullptr, &c.dyn->s_rho, 1};
+            nparts = 3;
+        } else {
+            // X_re = [dM | M] [rho_ref ; Re(rho - rho_ref)],  X_im = M Im(rho)
+            x.part[0] = {0, 0, Np + N, 0, c.Xre_f, N, c.s_m, c.s_rho, nullptr, nullptr, 0};
+            x.part[1] = {Np, 0, N, 0, c.Xim_f, N, c.s_m, c.s_rho, nullptr, nullptr, 1};
+            nparts = 2;
+        }
+        MARK("tc_gemm_X");
+        CK(tc::launch(c.scheme, c.maps_x, x, nparts, c.stream));
+        ++n;
+        UpdateOperands ops;
+        ops.rho_ref = c.rho_ref;
+        ops.scheme = c.scheme;
+        ops.bf16 = b;
+        ops.cur = cur;
+        if (h3) {
+            ops.dyn = c.dyn;          // tracks max |rho_{n+1} - rho_ref|; pieces come after
+            ops.Xre2 = c.Xa_f;
+        } else {
+            ops.re[0] = c.pc_bre[0] + Np;
+            ops.re[1] = c.pc_bre[1] + Np;
+            ops.im[0] = c.pc_bim[0];
+            ops.im[1] = c.pc_bim[1];
+            ops.ld_re = 2 * Np;
+            ops.ld_im = Np;
+            ops.scale = c.s_rho;
+        }
+        MARK("update");
+        launch_update_f32(c, c.Xre_f, c.Xim_f, bre, bim, c.rho_re[prv], c.rho_im[prv], factor,
+                          c.S, c.partial, c.sc, ops, c.stream);
+        ++n;
+        if (h3) {
+            MARK("split_rho");
+            launch_split_rho(c, prv, c.rho_re[prv], c.rho_im[prv], c.stream);
+            ++n;
+        }
     } else {
         const int N = c.N;
         // delta M = S^-1 delta H (left half of [dM | M]), M = M_gs + delta M (right half)
@@ -435,9 +631,12 @@ tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* t
         gemm_f32_add(N, N, N, c.M_f, 2 * N, c.dim_f, N, c.Xim_f, N, nullptr, c.stream);
         n += 2;
         MARK("update");
+        UpdateOperands ops;
+        ops.rho_ref = c.rho_ref;
+        ops.f_re = c.dre_f;
+        ops.f_im = c.dim_f;
         launch_update_f32(c, c.Xre_f, c.Xim_f, bre, bim, c.rho_re[prv], c.rho_im[prv], factor,
-                          c.S, c.partial, c.sc, c.rho_ref, c.dre_f, c.dim_f, nullptr, nullptr,
-                          nullptr, nullptr, c.stream);
+                          c.S, c.partial, c.sc, ops, c.stream);
         ++n;
     }
     MARK("end");
@@ -648,10 +847,14 @@ tdb_status tdb_create(const tdb_system* sys, const tdb_params* prm, void* worksp
     }
     tdb_status s = build_inverse(*c);
     if (s != TDB_OK) return fail(s);
-    if (mixed(*c)) {
+    if (c->prm.precision == TDB_FP32) {
         const size_t NN = (size_t)c->N * c->N;
         launch_f64_to_f32(NN, c->S, c->S_f, c->stream);
         launch_f64_to_f32(NN, c->Sinv, c->Sinv_f, c->stream);
+    }
+    if (tensor(*c)) {
+        s = build_maps(*c);
+        if (s != TDB_OK) return fail(s);
     }
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
         set_err("setup failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -768,8 +971,9 @@ tdb_status tdb_ground_state(tdb_ctx* c, int* iters_out, double* residual_out) {
                            cudaMemcpyDeviceToDevice, c->stream));
         gemm_f64_ham(N, c->Sinv, c->H0, c->S, c->v_ref, c->M, c->stream);  // M_gs
         launch_f64_to_f32(NN, c->M, c->Mgs_f, c->stream);
-        launch_f64_to_f32(NN, c->rho_ref, c->rref_f, c->stream);
+        if (c->prm.precision == TDB_FP32) launch_f64_to_f32(NN, c->rho_ref, c->rref_f, c->stream);
         CKL();
+        if (tensor(*c)) TRY(setup_tensor(*c));
     }
     TRY(refresh_derived(*c));
     TRY(upload_clock(*c, 0, 0, 0.0));
@@ -857,6 +1061,16 @@ tdb_status tdb_observables(tdb_ctx* c, tdb_obs* o, double* charges, double* forc
         return TDB_ERR_UNSUPPORTED;
     }
     const int cur = c->cur;
+    {
+        int* he = reinterpret_cast<int*>(c->h_pinned + 128);
+        CK(cudaMemcpyAsync(he, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        if (*he != 0 && !c->sticky) {
+            c->sticky = true;
+            set_err("a bounded device-side wait timed out (code %d)", *he);
+            return TDB_ERR_TIMEOUT;
+        }
+    }
     launch_charges(*c, c->partial, c->q, c->dq, c->stream);
     launch_potential(*c, c->gamma, c->dq, c->d_R, c->sc, c->v_orb, c->v_atom, c->gdq, c->hist,
                      c->v_ref, nullptr, c->stream);

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "tdb.h"
+#include "tdb_tc.h"
 
 namespace tdb {
 
@@ -82,6 +83,20 @@ struct Ctx {
     float *dre_f = nullptr, *dim_f = nullptr;        // rho - rho_ref (Re, Im)
     float *Xre_f = nullptr, *Xim_f = nullptr;
 
+    // tensor-core operands (TDB_BF16X3 / TDB_FP16X3 / TDB_FP16X6): 16-bit pieces
+    // (2 or 3 per operand), row stride padded to Np = round_up(N, 64)
+    int Np = 0, scheme = 0, npieces = 0;
+    uint16_t* pc_sinv[3] = {};   // N x Np     S^-1
+    uint16_t* pc_dh[3] = {};     // N x Np     delta H
+    uint16_t* pc_am[3] = {};     // N x 2Np    [delta M | M]
+    uint16_t* pc_bre[3] = {};    // N x 2Np    [rho_ref | Re(rho - rho_ref)]
+    uint16_t* pc_bim[3] = {};    // N x Np     -Im rho
+    float* Xa_f = nullptr;       // delta M rho_ref (FP16X6: its own output block)
+    tc::DynScales* dyn = nullptr;
+    int* d_err = nullptr;        // bounded-wait time-out / piece overflow flag
+    float s_sinv = 1, s_dh = 1, s_m = 1, s_rho = 1, s_ref = 1;   // power-of-two operand scales
+    tc::Maps maps_dm{}, maps_x{};
+
     // host-side trajectory state
     int cur = 0;                 // index of rho_n in rho_re/rho_im
     bool have_gs = false, euler_next = true, sticky = false;
@@ -108,21 +123,37 @@ void launch_symmetrize_upper_to_lower(int N, double* A, cudaStream_t st);
 void launch_transpose(int N, const double* in, double* out, cudaStream_t st);
 void launch_mulliken_partials(int N, const double* rho_re, const double* S, double* partial,
                               cudaStream_t st);
-void launch_charges(const Ctx& c, const double* partial, double* q, double* dq, cudaStream_t st);
+// reset0/reset1 (may be null): device doubles zeroed by the kernel
+void launch_charges(const Ctx& c, const double* partial, double* q, double* dq, cudaStream_t st,
+                    double* reset0 = nullptr, double* reset1 = nullptr);
+// max_dv (may be null): atomicMax of |v - v_ref| over atoms
 void launch_potential(const Ctx& c, const double* gamma, const double* dq, const double* R,
                       DevScalars* sc, double* v_orb, double* v_atom, double* gdq, double* hist,
-                      const double* v_ref, float* dv_orb, cudaStream_t st);
+                      const double* v_ref, float* dv_orb, cudaStream_t st,
+                      double* max_dv = nullptr);
 void launch_build_hamiltonian(int N, const double* H0, const double* S, const double* v_orb,
                               double* H, cudaStream_t st);
 void launch_update(const Ctx& c, const double* Xre, const double* Xim, const double* base_re,
                    const double* base_im, double* out_re, double* out_im, double factor,
                    const double* S, double* partial, DevScalars* sc, cudaStream_t st);
+// Operands written by the update for the next step's products.
+struct UpdateOperands {
+    const double* rho_ref = nullptr;   // deviations are taken from this (real) matrix
+    float *f_re = nullptr, *f_im = nullptr;                 // FP32: Re(rho - rho_ref), Im rho
+    int scheme = 0;                                         // tc::kHiLo / tc::kHead3 pieces
+    uint16_t* re[3] = {};                                   // pieces of s (Re rho - rho_ref)
+    uint16_t* im[3] = {};                                   // pieces of -s Im rho
+    int ld_re = 0, ld_im = 0;
+    float scale = 1.f;
+    int bf16 = 0;
+    tc::DynScales* dyn = nullptr;      // kHead3: s = pscale(max_drho[cur]); tracks the new max
+    int cur = 0;
+    const float* Xre2 = nullptr;       // added to X_re when set
+};
 void launch_update_f32(const Ctx& c, const float* Xre, const float* Xim, const double* base_re,
                        const double* base_im, double* out_re, double* out_im, double factor,
-                       const double* S, double* partial, DevScalars* sc, const double* rho_ref,
-                       float* op_re, float* op_im, __nv_bfloat16* opb_re_hi,
-                       __nv_bfloat16* opb_re_lo, __nv_bfloat16* opb_im_hi,
-                       __nv_bfloat16* opb_im_lo, cudaStream_t st);
+                       const double* S, double* partial, DevScalars* sc,
+                       const UpdateOperands& ops, cudaStream_t st);
 void launch_kick_phase(int N, int n_per, const double* R, double strength, const double* dir,
                        const double* Pre, const double* Pim, double* Cre, double* Cim,
                        cudaStream_t st);
@@ -132,6 +163,8 @@ void launch_obs_reduce(int N, const double* rho_re, const double* rho_im, const 
                        const double* S, double* block_out, int n_blocks, cudaStream_t st);
 void launch_obs_finish(int n_blocks, const double* block_out, double* out4, cudaStream_t st);
 void launch_scale_rows_f(int N, const double* in, const double* f, double* out, cudaStream_t st);
+// FP16X6: head pieces of rho - rho_ref (scale from c.dyn->max_drho[slot]) into the B operands
+void launch_split_rho(const Ctx& c, int slot, const double* rre, const double* rim, cudaStream_t st);
 
 // GEMM: C[M x Ncol] = A[M x K] * B[K x Ncol], row-major, FP64 SIMT.
 enum class BKind { Dense = 0, Hamiltonian = 1 };

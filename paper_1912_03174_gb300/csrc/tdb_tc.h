@@ -1,0 +1,98 @@
+// Host interface of the tensor-core split-precision GEMM (kern_tc.cu).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace tdb {
+namespace tc {
+
+// Piece schemes of an operand x (already multiplied by its power-of-two scale s):
+//  kHiLo  (2 pieces): hi = r16(x), lo = r16(x - hi); products hh + hl + lh, one accumulator.
+//  kHead3 (3 pieces): head = clamp(rint(x), -127, 127) (an integer), r = x - head,
+//          rh = fp16(r), rl = fp16(r - rh); the head*head products (integers) go to an
+//          accumulator whose sums stay exact below 2^24 (K <= 1024), the five products
+//          head*rh, rh*head, rh*rh, head*rl, rl*head to a second one.
+enum Scheme { kHiLo = 3, kHead3 = 6 };
+
+// One output block of the GEMM: C[M x N] = sum_k A[:, k0_a + k] Bt[:, k0_b + k], k < K,
+// times 1 / (scale_a scale_b); a scale is sa_dev[0] when sa_dev is set, else sa.
+struct GemmPart {
+    int k0_a, k0_b, K;
+    int mode;        // 0: FP32 output C; 1: delta-M epilogue (re-split into A pieces)
+    float* C;
+    int ldc;
+    float sa, sb;
+    const float* sa_dev;
+    const float* sb_dev;
+    int b_set;       // which B map set (0..2) this part reads
+};
+
+struct GemmParams {
+    int M, N;
+    GemmPart part[3];
+    uint32_t idesc;
+    int bf16;
+    // mode 1 (delta M): writes the pieces of s_dm dM at column j and of s_m (Mgs + dM) at
+    // column col_m + j of out[piece] (row stride ld_out)
+    const float* Mgs;
+    int ld_mgs;
+    uint16_t* out[3];
+    int ld_out, col_m;
+    float s_m;
+    const float* s_dm_dev;
+    int* err;          // device error flag: 1-3 bounded-wait time-outs, 4 piece overflow
+};
+
+// A: maps of the A pieces; b[set][piece]: maps of the Bt pieces.
+struct Maps {
+    CUtensorMap a[3];
+    CUtensorMap b[3][3];
+};
+
+// Tensor map of a rows x cols row-major 16-bit matrix (row stride ld elements):
+// box 64 (K) x 128 rows, 128-byte swizzle, zero fill out of bounds.
+bool make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int bf16);
+uint32_t idesc_f16(int bf16);
+size_t smem_bytes(int scheme);
+// Once per process and device before the first launch (and outside stream capture).
+cudaError_t prepare();
+cudaError_t launch(int scheme, const Maps& m, const GemmParams& p, int nparts, cudaStream_t st);
+
+// Pieces of sign * scale * (in - sub) (sub may be null) for a rows x cols block.
+// scale_dev (if set) overrides scale.
+void launch_split(int scheme, int rows, int cols, const double* in, int ld_in, float scale,
+                  int sign, int bf16, uint16_t* const* pieces, int ld_out, cudaStream_t st,
+                  const double* sub = nullptr, const float* scale_dev = nullptr, int* err = nullptr);
+// Pieces of delta H_kj = 1/2 S_kj (dv_k + dv_j), dv = v - v_ref.  With dyn (kHead3), the
+// scales come from the bound max|dv| (dyn->max_dv): s_dh = pscale(max|dv|) and
+// s_dm = pscale(||S^-1||_inf max|dv|) are stored in dyn->s_dh / dyn->s_dm.
+struct DynScales {
+    double max_dv;        // max |v - v_ref| of this step (atomicMax on the bit pattern)
+    double max_drho[2];   // max |rho - rho_ref| per density buffer
+    double sinv_norm;     // ||S^-1||_inf
+    float s_dh, s_dm, s_rho;
+    int pad;
+};
+void launch_split_dham(int scheme, int N, const double* S, const double* v, const double* vref,
+                       float scale, int bf16, uint16_t* const* pieces, int ld_out, DynScales* dyn,
+                       cudaStream_t st, int* err);
+
+// Power-of-two scale mapping a magnitude bound m into (63.5, 127]: the integer heads then
+// use their full 7-bit range and K <= 1040 head products (<= 127^2 each) sum exactly in FP32.
+// Every caller passes a rigorous bound (an exact maximum or a norm bound), so no value
+// exceeds the head range.
+__host__ __device__ inline float pscale(double m) {
+    if (!(m > 0)) return 1099511627776.0f;   // 2^40
+    int e;
+    frexp(127.0 / m, &e);                    // 127/m = f 2^e, f in [0.5, 1)
+    e -= 1;
+    if (e > 40) e = 40;
+    if (e < -40) e = -40;
+    return (float)ldexp(1.0, e);
+}
+
+}  // namespace tc
+}  // namespace tdb

@@ -195,15 +195,38 @@ def test_c2_flake_full_size_prefix_fp64(B):
     _compare(g, rho0, tr, n, tol_rho=1e-10, tol_mu=1e-10)
 
 
-@pytest.mark.parametrize("n_atoms", [10, 33])
-def test_fp32_form_matches_oracle(B, n_atoms):
+# reduced-precision forms: (form, dipole tolerance in a.u., rho tolerance)
+REDUCED = [("fp32", 1e-6, 1e-6), ("fp16x6", 1e-6, 1e-6), ("fp16x3", 1e-5, 1e-5),
+           ("bf16x3", 2e-5, 2e-5)]
+
+
+@pytest.mark.parametrize("form,tol_mu,tol_rho", REDUCED)
+@pytest.mark.parametrize("n_atoms", [10, 33, 64])
+def test_reduced_precision_forms_match_oracle(B, n_atoms, form, tol_mu, tol_rho):
+    # N = 40, 132, 256: one tile, ragged tails (132 is not a multiple of 64), several tiles
     sysm = I.small_flake(n_atoms, seed=8)
     run = I.Run(dt=0.2, n_steps=0, scc=True, kick=1e-3, kT=I.SCC_KT)
     n = 500
-    g = _gpu_run(B, sysm, run, n, "fp32")
+    g = _gpu_run(B, sysm, run, n, form)
     rho0, gs, tr = _oracle(sysm, run, n)
     mu = np.vstack([g["hist"], g["obs"]["dipole"][None, :]])
-    assert np.max(np.abs(mu - tr.dipole)) < 1e-6
-    assert np.max(np.abs(g["rho"] - tr.rho)) < 1e-6
+    err = np.max(np.abs(mu - tr.dipole))
+    assert err < tol_mu, err
+    assert np.max(np.abs(g["rho"] - tr.rho)) < tol_rho
     assert abs(g["obs"]["trace_re"] - sysm.n_electrons) / sysm.n_electrons < 1e-8
     assert g["obs"]["herm_err"] == 0.0
+
+
+def test_exact_head_form_beats_the_hi_lo_forms(B):
+    # the hi/lo forms are limited by the biased tensor-core accumulation; the
+    # exact-head form is not
+    sysm = I.small_flake(64, seed=8)
+    run = I.Run(dt=0.2, n_steps=0, scc=True, kick=1e-3, kT=I.SCC_KT)
+    n = 400
+    ref = _gpu_run(B, sysm, run, n, "fp64")
+    e = {}
+    for form in ("fp16x6", "fp16x3", "bf16x3"):
+        g = _gpu_run(B, sysm, run, n, form)
+        e[form] = np.max(np.abs(g["hist"] - ref["hist"]))
+    assert e["fp16x6"] < e["fp16x3"] / 4, e
+    assert e["fp16x6"] < e["bf16x3"] / 4, e

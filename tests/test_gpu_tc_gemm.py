@@ -1,0 +1,92 @@
+"""The tcgen05 split-precision GEMM against a numpy FP64 product.
+
+Error model: each operand is carried as hi + lo 16-bit pieces; the dropped
+lo*lo product and the piece rounding leave ~2^-22 (FP16 pieces, scaled) or
+~2^-16 (BF16 pieces) relative error per product, plus FP32 accumulation
+(~2^-24 sqrt(K)).  Errors are measured against |A| @ |B| elementwise.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1912_03174_gb300 import binding
+    return binding
+
+
+SHAPES = [(128, 128, 64), (40, 40, 40), (130, 200, 300), (256, 384, 1024), (1024, 1024, 1024)]
+
+
+@pytest.mark.parametrize("M,N,K", SHAPES)
+def test_fp16_pieces_match_fp64(B, M, N, K):
+    rng = np.random.default_rng(M * 7 + N * 3 + K)
+    A = rng.normal(size=(M, K)) * np.exp(rng.uniform(-6, 0, size=(M, K)))
+    Bm = rng.normal(size=(K, N)) * np.exp(rng.uniform(-6, 0, size=(K, N)))
+    C, ms = B.tdb_split_gemm(A, Bm, fmt=0)
+    ref = A @ Bm
+    scale = np.abs(A) @ np.abs(Bm)
+    rel = np.max(np.abs(C - ref) / scale)
+    # pieces (2^-20 with margin) + FP32 accumulation (2^-24 sqrt(K), x16 for the max over elements)
+    assert rel < 2.0 ** -20 + 16 * 2.0 ** -24 * np.sqrt(K), rel
+    assert ms > 0
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (130, 200, 300)])
+def test_bf16_pieces_match_fp64_to_16_bits(B, M, N, K):
+    rng = np.random.default_rng(5)
+    A = rng.normal(size=(M, K))
+    Bm = rng.normal(size=(K, N))
+    C, _ = B.tdb_split_gemm(A, Bm, fmt=1)
+    C16, _ = B.tdb_split_gemm(A, Bm, fmt=0)
+    ref = A @ Bm
+    scale = np.abs(A) @ np.abs(Bm)
+    e_bf = np.max(np.abs(C - ref) / scale)
+    e_fp = np.max(np.abs(C16 - ref) / scale)
+    assert e_bf < 1e-4, e_bf
+    # FP32 accumulation (~2^-24 sqrt(K)) bounds the FP16-piece error here, so the
+    # gap to the 16-bit BF16 pieces is a few x, not 2^6
+    assert e_fp < e_bf / 2, (e_fp, e_bf)
+
+
+def test_exact_small_integers(B):
+    # small integers are exact in every piece format: the result must be exact
+    rng = np.random.default_rng(1)
+    A = rng.integers(-8, 9, size=(192, 320)).astype(float)
+    Bm = rng.integers(-8, 9, size=(320, 136)).astype(float)
+    for fmt in (0, 1):
+        C, _ = B.tdb_split_gemm(A, Bm, fmt=fmt)
+        assert np.array_equal(C, A @ Bm)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (130, 200, 300), (256, 384, 1024)])
+def test_head_scheme_matches_fp64(B, M, N, K):
+    rng = np.random.default_rng(M + N + K)
+    A = rng.normal(size=(M, K)) * np.exp(rng.uniform(-6, 0, size=(M, K)))
+    Bm = rng.normal(size=(K, N)) * np.exp(rng.uniform(-6, 0, size=(K, N)))
+    C, _ = B.tdb_split_gemm(A, Bm, fmt=2)
+    ref = A @ Bm
+    scale = np.abs(A) @ np.abs(Bm)
+    rel = np.max(np.abs(C - ref) / scale)
+    assert rel < 2.0 ** -20 + 16 * 2.0 ** -24 * np.sqrt(K), rel
+
+
+def test_head_scheme_removes_the_accumulation_bias(B):
+    # all products positive: the FP32 tensor-core accumulation truncates, so the
+    # hi/lo scheme comes out systematically low by ~K 2^-25; the integer heads sum
+    # exactly, leaving only the tails' share (~2^-7 of it)
+    rng = np.random.default_rng(11)
+    K = 1024
+    A = rng.uniform(0, 1, (256, K))
+    Bm = rng.uniform(0, 1, (K, 256))
+    ref = A @ Bm
+    bias = {}
+    for fmt in (0, 2):
+        C, _ = B.tdb_split_gemm(A, Bm, fmt=fmt)
+        bias[fmt] = float(np.mean((C - ref) / ref))
+    assert bias[0] < -1e-6, bias              # measured ~ -7e-6 on GB300
+    assert abs(bias[2]) < abs(bias[0]) / 20, bias
