@@ -208,6 +208,26 @@ tdb_status tdb_step_profiled(tdb_ctx* ctx, double* ms, const char** names, int c
 tdb_status tdb_split_gemm(int M, int N, int K, const double* A, const double* B, int fmt, double* C,
                           double* ms);
 
+/* The same product as tdb_split_gemm, for callers that cannot allocate device
+ * memory (this entry point has no counterpart in the paper; it serves library
+ * users).  A process whose device memory is fully handed to its own pool, code
+ * running while another component owns the allocator, or code that must not
+ * trigger the implicit synchronisation of cudaMalloc/cudaFree cannot call
+ * tdb_split_gemm, which allocates its own buffers.  This call allocates nothing:
+ * A (M x K), B (K x N) and C (M x N) are caller-owned DEVICE arrays of row-major
+ * doubles, the work is enqueued on `stream` (a cudaStream_t, NULL = the legacy
+ * default stream) and the call returns without synchronising.  Intermediates
+ * live in one fixed 8 MiB device array that every GPU loading the library
+ * reserves until the process exits; it must hold the 16-bit pieces of A and of
+ * B^T (2 or 3 pieces of 2 bytes for each element, K padded to a multiple of 64)
+ * plus an FP32 copy of C, else TDB_ERR_NOMEM (for example 512 x 512 x 512
+ * fits, 1024 x 1024 x 1024 does not).  All calls share that array and it keeps
+ * the last call's contents: calls whose GPU work overlaps race, so serialise
+ * them.  The first call on each device looks up the array's address and must
+ * come before any stream capture.  fmt as in tdb_split_gemm. */
+tdb_status tdb_split_gemm_noalloc(int M, int N, int K, const double* A, const double* B, int fmt,
+                                  double* C, void* stream);
+
 void tdb_destroy(tdb_ctx* ctx);
 const char* tdb_status_string(tdb_status s);
 const char* tdb_last_error(void);

@@ -78,6 +78,8 @@ SIGNATURES = {
     "tdb_step_profiled": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_char_p), ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int)]),
     "tdb_split_gemm": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_int, _dp, _dp]),
+    "tdb_split_gemm_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "tdb_destroy": (None, [ctypes.c_void_p]),
     "tdb_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "tdb_last_error": (ctypes.c_char_p, []),
@@ -308,6 +310,13 @@ def tdb_split_gemm(A, B, fmt=0):
     ms = ctypes.c_double()
     _check("tdb_split_gemm", load().tdb_split_gemm(M, N, K, _ptr(A), _ptr(B), int(fmt), _ptr(C), ctypes.byref(ms)))
     return C, ms.value
+
+
+def tdb_split_gemm_noalloc(M, N, K, a_ptr, b_ptr, fmt, c_ptr, stream=None):
+    """C = A B with caller-owned device buffers (raw pointers); allocates nothing.
+    Returns without synchronising ``stream``."""
+    _check("tdb_split_gemm_noalloc", load().tdb_split_gemm_noalloc(
+        int(M), int(N), int(K), a_ptr, b_ptr, int(fmt), c_ptr, stream))
 
 
 def tdb_destroy(ctx: Context):

@@ -30,8 +30,15 @@ using namespace tdb;
 struct tdb_ctx : public Ctx {};
 
 namespace {
-
 thread_local std::string g_err;
+}
+
+namespace tdb {
+// message returned by tdb_last_error() on this thread
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace tdb
+
+namespace {
 
 void set_err(const char* fmt, ...) {
     char buf[512];
