@@ -44,15 +44,14 @@ __device__ __forceinline__ float from16(uint16_t x, int bf16) {
     return __half2float(__ushort_as_half(x));
 }
 
-// head (integer, |h| <= 127) + two FP16 tails of a scaled value
-__device__ __forceinline__ void split_head3(double x, uint16_t (&q)[3]) {
-    double h = rint(x);
-    h = fmin(fmax(h, -127.0), 127.0);
-    const double r = x - h;
-    const __half rh = __double2half(r);
-    q[0] = __half_as_ushort(__double2half(h));
+// head (integer, |h| <= 127) + two FP16 tails of a scaled FP32 value (exact split)
+__device__ __forceinline__ void split_head3(float x, uint16_t (&q)[3]) {
+    const float h = fminf(fmaxf(rintf(x), -127.f), 127.f);
+    const float r = x - h;
+    const __half rh = __float2half_rn(r);
+    q[0] = __half_as_ushort(__float2half_rn(h));
     q[1] = __half_as_ushort(rh);
-    q[2] = __half_as_ushort(__double2half(r - (double)__half2float(rh)));
+    q[2] = __half_as_ushort(__float2half_rn(r - __half2float(rh)));
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -169,9 +168,9 @@ __global__ void k_transpose(int N, const double* __restrict__ in, double* __rest
     }
 }
 
-// partial[ct][row] = sum over the 32 columns of tile ct of Re rho[row][col] * S[row][col]
+// partial[row][ct] = sum over the 32 columns of tile ct of Re rho[row][col] * S[row][col]
 // (eq:qmulik: q_A = sum_{nu in A} Re (rho S)_{nu nu}; S is symmetric).
-__global__ void k_mulliken_partials(int N, const double* __restrict__ rre,
+__global__ void k_mulliken_partials(int N, int nct, const double* __restrict__ rre,
                                     const double* __restrict__ S, double* __restrict__ partial) {
     const int ct = blockIdx.x;
     const int col = ct * kTile + threadIdx.x;
@@ -181,24 +180,30 @@ __global__ void k_mulliken_partials(int N, const double* __restrict__ rre,
         double v = 0.0;
         if (col < N) v = rre[(size_t)row * N + col] * S[(size_t)row * N + col];
         v = warp_sum(v);
-        if (threadIdx.x == 0) partial[(size_t)ct * N + row] = v;
+        if (threadIdx.x == 0) partial[(size_t)row * nct + ct] = v;
     }
 }
 
-__global__ void k_charges(int nat, int nper, int nct, int N, const double* __restrict__ partial,
+// q_A = sum of the Mulliken row partials of A's orbitals (contiguous in the
+// [row][ct] layout): one warp per atom.
+__global__ void k_charges(int nat, int nper, int nct, const double* __restrict__ partial,
                           const double* __restrict__ q0, double* __restrict__ q,
                           double* __restrict__ dq, double* reset0, double* reset1) {
-    const int A = blockIdx.x * blockDim.x + threadIdx.x;
-    if (A == 0) {
+    const int lane = threadIdx.x & 31;
+    const int A = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         if (reset0) *reset0 = 0.0;
         if (reset1) *reset1 = 0.0;
     }
     if (A >= nat) return;
+    const double* p = partial + (size_t)A * nper * nct;
     double s = 0.0;
-    for (int i = 0; i < nper; ++i)
-        for (int ct = 0; ct < nct; ++ct) s += partial[(size_t)ct * N + A * nper + i];
-    q[A] = s;
-    dq[A] = s - q0[A];
+    for (int i = lane; i < nper * nct; i += 32) s += p[i];
+    s = warp_sum(s);
+    if (lane == 0) {
+        q[A] = s;
+        dq[A] = s - q0[A];
+    }
 }
 
 // Warp per atom A: gdq_A = sum_B gamma_AB dq_B;  v_A = [scc] gdq_A + R_A . E(t_n)
@@ -293,29 +298,32 @@ __global__ void k_build_hamiltonian(int N, const double* __restrict__ H0,
 // Leapfrog / Euler update (eq:leapfrog with eq:eomrho, frozen nuclei):
 //   out = base + factor * rhodot,  rhodot = -i (X - X^dagger),  X = S^-1 H rho.
 // Re rhodot_ij = Im X_ij + Im X_ji;  Im rhodot_ij = -(Re X_ij - Re X_ji).
-// A block owns the tile pair (bi, bj), bi <= bj, so both halves come out of the
-// same operands and rho stays exactly Hermitian.  The Mulliken row partials of
-// the new rho are fused in.  T is the type of X.
+// A block (32 x 8 threads) owns the tile pair (bi, bj), bi <= bj, so both halves
+// come out of the same operands and rho stays exactly Hermitian.  The Mulliken
+// row partials of the new rho are fused in.  T is the type of X.
 template <typename T>
-__global__ void k_update(int N, int nct, const T* __restrict__ Xre, const T* __restrict__ Xim,
-                         const double* __restrict__ bre, const double* __restrict__ bim,
-                         double* __restrict__ ore, double* __restrict__ oim, double factor,
-                         const double* __restrict__ S, double* __restrict__ partial,
-                         DevScalars* __restrict__ sc, UpdateOperands ops) {
+__global__ void __launch_bounds__(256)
+    k_update(int N, int nct, const T* __restrict__ Xre, const T* __restrict__ Xim,
+             const double* __restrict__ bre, const double* __restrict__ bim,
+             double* __restrict__ ore, double* __restrict__ oim, double factor,
+             const double* __restrict__ S, double* __restrict__ partial,
+             DevScalars* __restrict__ sc, UpdateOperands ops) {
     const int bi = blockIdx.y, bj = blockIdx.x;
     if (bi > bj) return;
-    const double op_scale = ops.scale;
-    double dmax = 0.0;   // max |rho_{n+1} - rho_ref| of this block (FP16X6 scale tracking)
+    constexpr int RPT = kTile / 8;   // rows per thread
     __shared__ T xr_ij[kTile][kTile + 1], xi_ij[kTile][kTile + 1];
     __shared__ T xr_ji[kTile][kTile + 1], xi_ji[kTile][kTile + 1];
-    const int tx = threadIdx.x;
-    for (int y = threadIdx.y; y < kTile; y += blockDim.y) {
+    const int tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int y = ty + 8 * k;
         int r = bi * kTile + y, c = bj * kTile + tx;
         T a = 0, b = 0;
         if (r < N && c < N) {
-            a = Xre[(size_t)r * N + c];
-            if (ops.Xre2) a += ops.Xre2[(size_t)r * N + c];
-            b = Xim[(size_t)r * N + c];
+            const size_t i = (size_t)r * N + c;
+            a = Xre[i];
+            if (ops.Xre2) a += ops.Xre2[i];
+            b = Xim[i];
         }
         xr_ij[y][tx] = a;
         xi_ij[y][tx] = b;
@@ -324,74 +332,91 @@ __global__ void k_update(int N, int nct, const T* __restrict__ Xre, const T* __r
         a = 0;
         b = 0;
         if (r < N && c < N) {
-            a = Xre[(size_t)r * N + c];
-            if (ops.Xre2) a += ops.Xre2[(size_t)r * N + c];
-            b = Xim[(size_t)r * N + c];
+            const size_t i = (size_t)r * N + c;
+            a = Xre[i];
+            if (ops.Xre2) a += ops.Xre2[i];
+            b = Xim[i];
         }
         xr_ji[y][tx] = a;
         xi_ji[y][tx] = b;
     }
     __syncthreads();
+    float dmax = 0.f;   // max |rho_{n+1} - rho_ref| (FP16X6 scale tracking)
     for (int half = 0; half < (bi == bj ? 1 : 2); ++half) {
         const int ti = half ? bj : bi, tj = half ? bi : bj;
-        for (int y = threadIdx.y; y < kTile; y += blockDim.y) {
+        double b_re[RPT], b_im[RPT], s_v[RPT], r_v[RPT];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int r = ti * kTile + ty + 8 * k, c = tj * kTile + tx;
+            b_re[k] = b_im[k] = s_v[k] = r_v[k] = 0.0;
+            if (r < N && c < N) {
+                const size_t i = (size_t)r * N + c;
+                b_re[k] = bre[i];
+                b_im[k] = bim[i];
+                s_v[k] = S[i];
+                if (ops.rho_ref) r_v[k] = ops.rho_ref[i];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int y = ty + 8 * k;
             const int r = ti * kTile + y, c = tj * kTile + tx;
             double pv = 0.0;
             if (r < N && c < N) {
-                double x_ij_re, x_ij_im, x_ji_re, x_ji_im;
+                T x_ij_re, x_ij_im, x_ji_re, x_ji_im;
                 if (!half) {
-                    x_ij_re = (double)xr_ij[y][tx];
-                    x_ij_im = (double)xi_ij[y][tx];
-                    x_ji_re = (double)xr_ji[tx][y];
-                    x_ji_im = (double)xi_ji[tx][y];
+                    x_ij_re = xr_ij[y][tx];
+                    x_ij_im = xi_ij[y][tx];
+                    x_ji_re = xr_ji[tx][y];
+                    x_ji_im = xi_ji[tx][y];
                 } else {
-                    x_ij_re = (double)xr_ji[y][tx];
-                    x_ij_im = (double)xi_ji[y][tx];
-                    x_ji_re = (double)xr_ij[tx][y];
-                    x_ji_im = (double)xi_ij[tx][y];
+                    x_ij_re = xr_ji[y][tx];
+                    x_ij_im = xi_ji[y][tx];
+                    x_ji_re = xr_ij[tx][y];
+                    x_ji_im = xi_ij[tx][y];
                 }
-                const double dre = x_ij_im + x_ji_im;
-                const double dim = -(x_ij_re - x_ji_re);
+                // in the precision of X (exactly Hermitian either way: the (j,i) element
+                // repeats these operations on the swapped operands)
+                const double dre = (double)(x_ij_im + x_ji_im);
+                const double dim = (double)(-(x_ij_re - x_ji_re));
                 const size_t i = (size_t)r * N + c;
-                const double nre = bre[i] + factor * dre;
-                const double nim = bim[i] + factor * dim;
+                const double nre = b_re[k] + factor * dre;
+                const double nim = b_im[k] + factor * dim;
                 ore[i] = nre;
                 oim[i] = nim;
-                pv = nre * S[i];
+                pv = nre * s_v[k];
                 if (ops.rho_ref) {
-                    const double d_re = nre - ops.rho_ref[i];
+                    const double d_re = nre - r_v[k];
+                    if (ops.dyn) dmax = fmaxf(dmax, fmaxf(fabsf((float)d_re), fabsf((float)nim)));
                     if (ops.f_re) {
                         ops.f_re[i] = (float)d_re;
                         ops.f_im[i] = (float)nim;
                     }
-                    if (ops.dyn) dmax = fmax(dmax, fmax(fabs(d_re), fabs(nim)));
                     if (ops.re[0]) {
                         // operands of the tensor-core products are K-major: Re rho is
                         // symmetric, and the transpose of Im rho is -Im rho
                         const size_t jr = (size_t)r * ops.ld_re + c;
                         const size_t ji = (size_t)r * ops.ld_im + c;
-                        {
-                            const float x = (float)(d_re * op_scale);
-                            const uint16_t h1 = to16(x, ops.bf16);
-                            ops.re[0][jr] = h1;
-                            ops.re[1][jr] = to16(x - from16(h1, ops.bf16), ops.bf16);
-                            const float y = (float)(-nim * op_scale);
-                            const uint16_t h2 = to16(y, ops.bf16);
-                            ops.im[0][ji] = h2;
-                            ops.im[1][ji] = to16(y - from16(h2, ops.bf16), ops.bf16);
-                        }
+                        const float x = (float)(d_re * ops.scale);
+                        const uint16_t h1 = to16(x, ops.bf16);
+                        ops.re[0][jr] = h1;
+                        ops.re[1][jr] = to16(x - from16(h1, ops.bf16), ops.bf16);
+                        const float yv = (float)(-nim * ops.scale);
+                        const uint16_t h2 = to16(yv, ops.bf16);
+                        ops.im[0][ji] = h2;
+                        ops.im[1][ji] = to16(yv - from16(h2, ops.bf16), ops.bf16);
                     }
                 }
             }
             pv = warp_sum(pv);
-            if (tx == 0 && r < N) partial[(size_t)tj * N + r] = pv;
+            if (tx == 0 && r < N) partial[(size_t)r * nct + tj] = pv;
         }
     }
     if (ops.dyn) {
-        for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
         if (tx == 0)
             atomicMax(reinterpret_cast<unsigned long long*>(&ops.dyn->max_drho[ops.cur ^ 1]),
-                      (unsigned long long)__double_as_longlong(dmax));
+                      (unsigned long long)__double_as_longlong((double)dmax));
     }
     if (bi == 0 && bj == 0 && threadIdx.x == 0 && threadIdx.y == 0) sc->step += 1;
 }
@@ -528,13 +553,13 @@ void launch_mulliken_partials(int N, const double* rho_re, const double* S, doub
                               cudaStream_t st) {
     const int nct = (N + kTile - 1) / kTile;
     dim3 b(kTile, 8);
-    k_mulliken_partials<<<dim3(nct, nct), b, 0, st>>>(N, rho_re, S, partial);
+    k_mulliken_partials<<<dim3(nct, nct), b, 0, st>>>(N, nct, rho_re, S, partial);
 }
 
 void launch_charges(const Ctx& c, const double* partial, double* q, double* dq, cudaStream_t st,
                     double* reset0, double* reset1) {
-    k_charges<<<(c.nat + 127) / 128, 128, 0, st>>>(c.nat, c.nper, c.nct, c.N, partial, c.d_q0, q,
-                                                   dq, reset0, reset1);
+    k_charges<<<(c.nat + 7) / 8, 256, 0, st>>>(c.nat, c.nper, c.nct, partial, c.d_q0, q, dq,
+                                               reset0, reset1);
 }
 
 void launch_potential(const Ctx& c, const double* gamma, const double* dq, const double* R,
@@ -689,20 +714,24 @@ __global__ void k_absmax(size_t n, const double* __restrict__ x, const double* _
 __global__ void k_split_rho(int N, int Np, const double* __restrict__ rre,
                             const double* __restrict__ rim, const double* __restrict__ rref,
                             tc::DynScales* __restrict__ dyn, int slot, UpdateOperands ops) {
-    const double s = tc::pscale(dyn->max_drho[slot]);
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0)
-        dyn->s_rho = (float)s;
+    __shared__ float s_sh;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        s_sh = tc::pscale(dyn->max_drho[slot]);
+        if (blockIdx.x == 0 && blockIdx.y == 0) dyn->s_rho = s_sh;
+    }
+    __syncthreads();
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int r = blockIdx.y * blockDim.y + threadIdx.y;
     if (r >= N || c >= N) return;
     const size_t i = (size_t)r * N + c;
     uint16_t q[3];
-    split_head3((rre[i] - rref[i]) * s, q);
+    const float fs = s_sh;
+    split_head3((float)(rre[i] - rref[i]) * fs, q);
     const size_t jr = (size_t)r * 2 * Np + Np + c;
     ops.re[0][jr] = q[0];
     ops.re[1][jr] = q[1];
     ops.re[2][jr] = q[2];
-    split_head3(-rim[i] * s, q);
+    split_head3((float)(-rim[i]) * fs, q);
     const size_t ji = (size_t)r * Np + c;
     ops.im[0][ji] = q[0];
     ops.im[1][ji] = q[1];

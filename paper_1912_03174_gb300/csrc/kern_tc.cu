@@ -29,8 +29,8 @@ namespace tc {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64;
-constexpr int TILE_BYTES = BM * BK * 2;   // 16 KiB per operand piece
+constexpr int BM = 128, BK = 64;
+constexpr int TILE_BYTES = BM * BK * 2;   // 16 KiB per A piece (B pieces: BN * BK * 2)
 constexpr long long kSpinLimit = 1ll << 22;
 
 template <int SCHEME>
@@ -43,13 +43,13 @@ template <>
 struct Cfg<kHead3> {
     static constexpr int PIECES = 3, STAGES = 2, ACCS = 2;
 };
-template <int S>
+template <int S, int BN>
 __host__ __device__ constexpr int stage_bytes() {
-    return 2 * Cfg<S>::PIECES * TILE_BYTES;
+    return Cfg<S>::PIECES * (TILE_BYTES + BN * BK * 2);
 }
-template <int S>
+template <int S, int BN>
 __host__ __device__ constexpr int smem_total() {
-    return Cfg<S>::STAGES * stage_bytes<S>() + 1024 + 256;
+    return Cfg<S>::STAGES * stage_bytes<S, BN>() + 1024 + 256;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -156,34 +156,35 @@ __device__ __forceinline__ float from16(uint16_t x, int bf16) {
     return __half2float(__ushort_as_half(x));
 }
 
-// Pieces of one scaled value (see tdb_tc.h).  Returns false if a tail overflows FP16.
+// Pieces of one scaled FP32 value (see tdb_tc.h); FP32 arithmetic only (FP64 is slow
+// on this part).  For the head scheme the pieces reproduce the FP32 value exactly:
+// x - head is exact, and 11 + 11 tail bits cover the <= 17 bits left after the head.
+// Returns false if a tail overflows FP16.
 template <int SCHEME>
-__device__ __forceinline__ bool split_value(double x, int bf16, uint16_t (&q)[3]) {
+__device__ __forceinline__ bool split_value(float x, int bf16, uint16_t (&q)[3]) {
     if (SCHEME == kHiLo) {
-        const float xf = static_cast<float>(x);
-        q[0] = to16(xf, bf16);
-        q[1] = to16(xf - from16(q[0], bf16), bf16);
+        q[0] = to16(x, bf16);
+        q[1] = to16(x - from16(q[0], bf16), bf16);
         q[2] = 0;
-        return fabsf(xf) < 65000.f;
+        return fabsf(x) < 65000.f;
     } else {
-        double h = rint(x);
-        h = fmin(fmax(h, -127.0), 127.0);
-        const double r = x - h;
-        const __half rh = __double2half(r);
-        const double r2 = r - static_cast<double>(__half2float(rh));
-        q[0] = __half_as_ushort(__double2half(h));
+        const float h = fminf(fmaxf(rintf(x), -127.f), 127.f);
+        const float r = x - h;
+        const __half rh = __float2half_rn(r);
+        q[0] = __half_as_ushort(__float2half_rn(h));
         q[1] = __half_as_ushort(rh);
-        q[2] = __half_as_ushort(__double2half(r2));
-        return fabs(r) < 65000.0;
+        q[2] = __half_as_ushort(__float2half_rn(r - __half2float(rh)));
+        return fabsf(r) < 65000.f;
     }
 }
 
-template <int SCHEME>
+template <int SCHEME, int BN>
 __global__ void __launch_bounds__(128, 1)
     k_split_gemm(const __grid_constant__ Maps maps, GemmParams p) {
     constexpr int PIECES = Cfg<SCHEME>::PIECES, STAGES = Cfg<SCHEME>::STAGES;
-    constexpr int ACCS = Cfg<SCHEME>::ACCS, SB = stage_bytes<SCHEME>();
-    constexpr uint32_t TMEM_COLS = ACCS == 1 ? 128u : 256u;
+    constexpr int ACCS = Cfg<SCHEME>::ACCS, SB = stage_bytes<SCHEME, BN>();
+    constexpr int BTILE = BN * BK * 2;
+    constexpr uint32_t TMEM_COLS = static_cast<uint32_t>(ACCS * BN) < 32u ? 32u : static_cast<uint32_t>(ACCS * BN);
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -229,12 +230,12 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
             for (int q = 0; q < PIECES; ++q) {
                 tma_load_2d(st + q * TILE_BYTES, &maps.a[q], P.k0_a + kb * BK, m0, fb);
-                tma_load_2d(st + (PIECES + q) * TILE_BYTES, &maps.b[P.b_set][q], P.k0_b + kb * BK,
-                            n0, fb);
+                tma_load_2d(st + PIECES * TILE_BYTES + q * BTILE, &maps.b[P.b_set][q],
+                            P.k0_b + kb * BK, n0, fb);
             }
         }
     } else if (warp == 1 && lane == 0) {
-        const uint32_t acc0 = tmem, acc1 = tmem + (ACCS == 2 ? 128u : 0u);
+        const uint32_t acc0 = tmem, acc1 = tmem + (ACCS == 2 ? static_cast<uint32_t>(BN) : 0u);
         for (int kb = 0; kb < nkb; ++kb) {
             const int s = kb % STAGES, round = kb / STAGES;
             if (!mbar_wait(full0 + 8 * s, round & 1, p.err, 2)) break;
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
                 for (int q = 0; q < PIECES; ++q) {
                     a[q] = sdesc(st + q * TILE_BYTES + k * 32);
-                    b[q] = sdesc(st + (PIECES + q) * TILE_BYTES + k * 32);
+                    b[q] = sdesc(st + PIECES * TILE_BYTES + q * BTILE + k * 32);
                 }
                 const uint32_t first = (kb | k) != 0;
                 if (SCHEME == kHiLo) {
@@ -282,7 +283,7 @@ __global__ void __launch_bounds__(128, 1)
             float v[32];
             if (ACCS == 2) {
                 uint32_t r1[32];
-                tmem_ld32(tmem + 128u + lane_off + c * 32, r1);
+                tmem_ld32(tmem + static_cast<uint32_t>(BN) + lane_off + c * 32, r1);
                 tmem_wait_ld();
 #pragma unroll
                 for (int j = 0; j < 32; ++j)
@@ -325,11 +326,10 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
                             uint16_t q[3];
-                            fine &= split_value<SCHEME>(static_cast<double>(v[j0 + j]) * s_dm, p.bf16, q);
+                            fine &= split_value<SCHEME>(v[j0 + j] * s_dm, p.bf16, q);
 #pragma unroll
                             for (int t = 0; t < 3; ++t) qd[t][j] = q[t];
-                            fine &= split_value<SCHEME>(static_cast<double>(gm[j] + v[j0 + j]) * p.s_m,
-                                                        p.bf16, q);
+                            fine &= split_value<SCHEME>((gm[j] + v[j0 + j]) * p.s_m, p.bf16, q);
 #pragma unroll
                             for (int t = 0; t < 3; ++t) qm[t][j] = q[t];
                         }
@@ -354,11 +354,10 @@ __global__ void __launch_bounds__(128, 1)
                         const int col = col0 + j;
                         if (col >= p.N) continue;
                         uint16_t q[3];
-                        fine &= split_value<SCHEME>(static_cast<double>(v[j]) * s_dm, p.bf16, q);
+                        fine &= split_value<SCHEME>(v[j] * s_dm, p.bf16, q);
 #pragma unroll
                         for (int t = 0; t < PIECES; ++t) p.out[t][ob + j] = q[t];
-                        fine &= split_value<SCHEME>(static_cast<double>(mg[j] + v[j]) * p.s_m,
-                                                    p.bf16, q);
+                        fine &= split_value<SCHEME>((mg[j] + v[j]) * p.s_m, p.bf16, q);
 #pragma unroll
                         for (int t = 0; t < PIECES; ++t) p.out[t][ob + p.col_m + j] = q[t];
                     }
@@ -393,37 +392,42 @@ __global__ void k_split(int rows, int cols, const double* __restrict__ in,
     if (r >= rows || c >= cols) return;
     const size_t i = static_cast<size_t>(r) * ld_in + c;
     const double v = sub ? in[i] - sub[i] : in[i];
-    const double s = scale_dev ? *scale_dev : scale;
+    const float s = scale_dev ? *scale_dev : scale;
     uint16_t q[3];
-    const bool ok = split_value<SCHEME>(sign * v * s, bf16, q);
+    const bool ok = split_value<SCHEME>(static_cast<float>(sign * v) * s, bf16, q);
     const size_t o = static_cast<size_t>(r) * ld_out + c;
 #pragma unroll
     for (int t = 0; t < Cfg<SCHEME>::PIECES; ++t) out.p[t][o] = q[t];
     if (!ok && err) atomicCAS(err, 0, 4);
 }
 
-// delta H_kj = 1/2 S_kj (dv_k + dv_j), dv = v - v_ref
+// delta H_kj = 1/2 S_kj (dv_k + dv_j) from FP32 copies of S and dv = v - v_ref
 template <int SCHEME>
-__global__ void k_split_dham(int N, const double* __restrict__ S, const double* __restrict__ v,
-                             const double* __restrict__ vref, float scale_const, int bf16,
-                             Pieces out, int ld_out, DynScales* __restrict__ dyn, int* err) {
+__global__ void k_split_dham(int N, const float* __restrict__ S, const float* __restrict__ dv,
+                             float scale_const, int bf16, Pieces out, int ld_out,
+                             DynScales* __restrict__ dyn, int* err) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int r = blockIdx.y * blockDim.y + threadIdx.y;
-    double s = scale_const;
+    float s = scale_const;
     if (dyn) {
-        // |delta H| <= max |dv| (|S_kj| <= 1), |delta M| <= ||S^-1||_inf max |dv|
-        const double m = dyn->max_dv;
-        s = pscale(m);
-        if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
-            dyn->s_dh = static_cast<float>(s);
-            dyn->s_dm = pscale(m * dyn->sinv_norm);
+        // |delta H| <= max |dv| (|S_kj| <= 1), |delta M| <= ||S^-1||_inf max |dv|;
+        // one thread per block evaluates the scale (FP64 frexp/ldexp are slow here)
+        __shared__ float s_sh;
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            const double m = dyn->max_dv;
+            s_sh = pscale(m);
+            if (blockIdx.x == 0 && blockIdx.y == 0) {
+                dyn->s_dh = s_sh;
+                dyn->s_dm = pscale(m * dyn->sinv_norm);
+            }
         }
+        __syncthreads();
+        s = s_sh;
     }
     if (r >= N || c >= N) return;
-    const double dvr = v[r] - vref[r], dvc = v[c] - vref[c];
     uint16_t q[3];
-    const bool ok =
-        split_value<SCHEME>(0.5 * S[static_cast<size_t>(r) * N + c] * (dvr + dvc) * s, bf16, q);
+    const bool ok = split_value<SCHEME>(0.5f * S[static_cast<size_t>(r) * N + c] * (dv[r] + dv[c]) * s,
+                                        bf16, q);
     const size_t o = static_cast<size_t>(r) * ld_out + c;
 #pragma unroll
     for (int t = 0; t < Cfg<SCHEME>::PIECES; ++t) out.p[t][o] = q[t];
@@ -433,10 +437,11 @@ __global__ void k_split_dham(int N, const double* __restrict__ S, const double* 
 }  // namespace
 
 size_t smem_bytes(int scheme) {
-    return scheme == kHiLo ? smem_total<kHiLo>() : smem_total<kHead3>();
+    return scheme == kHiLo ? smem_total<kHiLo, 128>() : smem_total<kHead3, 128>();
 }
 
-bool make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int bf16) {
+bool make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int bf16,
+              int box_rows) {
     using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -453,7 +458,7 @@ bool make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int
     }
     const cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
     const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 2};
-    const cuuint32_t box[2] = {BK, BM};
+    const cuuint32_t box[2] = {BK, static_cast<cuuint32_t>(box_rows)};
     const cuuint32_t estr[2] = {1, 1};
     const CUresult r =
         encode(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
@@ -463,28 +468,44 @@ bool make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int
     return r == CUDA_SUCCESS;
 }
 
-uint32_t idesc_f16(int bf16) {
+uint32_t idesc_f16(int bf16, int bn) {
     // D = F32 (bits 4-5), A/B format (7-9, 10-12: 0 F16, 1 BF16), both K-major,
     // N >> 3 at bit 17, M >> 4 at bit 24
     return (1u << 4) | (static_cast<uint32_t>(bf16) << 7) | (static_cast<uint32_t>(bf16) << 10) |
-           (static_cast<uint32_t>(BN >> 3) << 17) | (static_cast<uint32_t>(BM >> 4) << 24);
+           (static_cast<uint32_t>(bn >> 3) << 17) | (static_cast<uint32_t>(BM >> 4) << 24);
 }
 
 cudaError_t prepare() {
-    cudaError_t e = cudaFuncSetAttribute(k_split_gemm<kHiLo>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         smem_total<kHiLo>());
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_split_gemm<kHead3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                smem_total<kHead3>());
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_split_gemm<kHiLo, 128>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem_total<kHiLo, 128>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_split_gemm<kHead3, 128>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem_total<kHead3, 128>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_split_gemm<kHiLo, 64>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem_total<kHiLo, 64>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_split_gemm<kHead3, 64>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem_total<kHead3, 64>());
+    return e;
 }
 
-cudaError_t launch(int scheme, const Maps& m, const GemmParams& p, int nparts, cudaStream_t st) {
-    dim3 grid((p.N + BN - 1) / BN, (p.M + BM - 1) / BM, nparts);
-    if (scheme == kHiLo)
-        k_split_gemm<kHiLo><<<grid, 128, smem_total<kHiLo>(), st>>>(m, p);
-    else
-        k_split_gemm<kHead3><<<grid, 128, smem_total<kHead3>(), st>>>(m, p);
+cudaError_t launch(int scheme, const Maps& m, const GemmParams& p, int nparts, cudaStream_t st,
+                   int bn) {
+    dim3 grid((p.N + bn - 1) / bn, (p.M + BM - 1) / BM, nparts);
+    if (bn == 64) {
+        if (scheme == kHiLo)
+            k_split_gemm<kHiLo, 64><<<grid, 128, smem_total<kHiLo, 64>(), st>>>(m, p);
+        else
+            k_split_gemm<kHead3, 64><<<grid, 128, smem_total<kHead3, 64>(), st>>>(m, p);
+    } else {
+        if (scheme == kHiLo)
+            k_split_gemm<kHiLo, 128><<<grid, 128, smem_total<kHiLo, 128>(), st>>>(m, p);
+        else
+            k_split_gemm<kHead3, 128><<<grid, 128, smem_total<kHead3, 128>(), st>>>(m, p);
+    }
     return cudaGetLastError();
 }
 
@@ -502,16 +523,16 @@ void launch_split(int scheme, int rows, int cols, const double* in, int ld_in, f
                                          o, ld_out, err);
 }
 
-void launch_split_dham(int scheme, int N, const double* S, const double* v, const double* vref,
-                       float scale, int bf16, uint16_t* const* pieces, int ld_out, DynScales* dyn,
-                       cudaStream_t st, int* err) {
+void launch_split_dham(int scheme, int N, const float* S, const float* dv, float scale, int bf16,
+                       uint16_t* const* pieces, int ld_out, DynScales* dyn, cudaStream_t st,
+                       int* err) {
     dim3 b(32, 8);
     dim3 g((N + 31) / 32, (N + 7) / 8);
     Pieces o{{pieces[0], pieces[1], scheme == kHead3 ? pieces[2] : nullptr}};
     if (scheme == kHiLo)
-        k_split_dham<kHiLo><<<g, b, 0, st>>>(N, S, v, vref, scale, bf16, o, ld_out, nullptr, err);
+        k_split_dham<kHiLo><<<g, b, 0, st>>>(N, S, dv, scale, bf16, o, ld_out, nullptr, err);
     else
-        k_split_dham<kHead3><<<g, b, 0, st>>>(N, S, v, vref, scale, bf16, o, ld_out, dyn, err);
+        k_split_dham<kHead3><<<g, b, 0, st>>>(N, S, dv, scale, bf16, o, ld_out, dyn, err);
 }
 
 }  // namespace tc

@@ -149,9 +149,11 @@ size_t carve(Ctx& c, char* base) {
         c.Xre_f = k.take<float>(NN);
         c.Xim_f = k.take<float>(NN);
     }
-    if (c.prm.precision == TDB_FP32) {
+    if (mixed(c)) {
         c.dv_f = k.take<float>(N);
         c.S_f = k.take<float>(NN);
+    }
+    if (c.prm.precision == TDB_FP32) {
         c.Sinv_f = k.take<float>(NN);
         c.dM_f = k.take<float>(2 * NN);     // [delta M | M], row stride 2N
         c.M_f = c.dM_f ? c.dM_f + N : nullptr;
@@ -488,7 +490,7 @@ tdb_status build_maps(Ctx& c) {
     bool ok = true;
     for (int q = 0; q < c.npieces; ++q) {
         ok = ok && tc::make_map(&c.maps_dm.a[q], c.pc_sinv[q], N, N, Np, b) &&
-             tc::make_map(&c.maps_dm.b[0][q], c.pc_dh[q], N, N, Np, b) &&
+             tc::make_map(&c.maps_dm.b[0][q], c.pc_dh[q], N, N, Np, b, 64) &&
              tc::make_map(&c.maps_x.a[q], c.pc_am[q], N, 2 * Np, 2 * Np, b) &&
              tc::make_map(&c.maps_x.b[0][q], c.pc_bre[q], N, 2 * Np, 2 * Np, b) &&
              tc::make_map(&c.maps_x.b[1][q], c.pc_bim[q], N, Np, Np, b);
@@ -552,7 +554,7 @@ tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* t
         const int N = c.N, Np = c.Np, b = piece_bf16(c);
         const bool h3 = head3(c);
         MARK("split_dH");
-        tc::launch_split_dham(c.scheme, N, c.S, c.v_orb, c.v_ref, c.s_dh, b, c.pc_dh, Np,
+        tc::launch_split_dham(c.scheme, N, c.S_f, c.dv_f, c.s_dh, b, c.pc_dh, Np,
                               h3 ? c.dyn : nullptr, c.stream, c.d_err);
         ++n;
         // delta M = S^-1 delta H; the epilogue writes the pieces of [delta M | M_gs + delta M]
@@ -561,7 +563,7 @@ tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* t
         g.N = N;
         g.part[0] = {0, 0, N, 1, nullptr, 0, c.s_sinv, 0.f, nullptr, h3 ? &c.dyn->s_dh : nullptr, 0};
         g.part[0].sb = c.s_dh;
-        g.idesc = tc::idesc_f16(b);
+        g.idesc = tc::idesc_f16(b, 64);
         g.bf16 = b;
         g.Mgs = c.Mgs_f;
         g.ld_mgs = N;
@@ -572,12 +574,12 @@ tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* t
         g.s_dm_dev = &c.dyn->s_dm;
         g.err = c.d_err;
         MARK("tc_gemm_dM");
-        CK(tc::launch(c.scheme, c.maps_dm, g, 1, c.stream));
+        CK(tc::launch(c.scheme, c.maps_dm, g, 1, c.stream, 64));
         ++n;
         tc::GemmParams x{};
         x.M = N;
         x.N = N;
-        x.idesc = g.idesc;
+        x.idesc = tc::idesc_f16(b, 128);
         x.bf16 = b;
         x.err = c.d_err;
         int nparts;
@@ -854,11 +856,9 @@ tdb_status tdb_create(const tdb_system* sys, const tdb_params* prm, void* worksp
     }
     tdb_status s = build_inverse(*c);
     if (s != TDB_OK) return fail(s);
-    if (c->prm.precision == TDB_FP32) {
-        const size_t NN = (size_t)c->N * c->N;
-        launch_f64_to_f32(NN, c->S, c->S_f, c->stream);
-        launch_f64_to_f32(NN, c->Sinv, c->Sinv_f, c->stream);
-    }
+    if (mixed(*c)) launch_f64_to_f32((size_t)c->N * c->N, c->S, c->S_f, c->stream);
+    if (c->prm.precision == TDB_FP32)
+        launch_f64_to_f32((size_t)c->N * c->N, c->Sinv, c->Sinv_f, c->stream);
     if (tensor(*c)) {
         s = build_maps(*c);
         if (s != TDB_OK) return fail(s);

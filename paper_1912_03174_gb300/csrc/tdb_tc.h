@@ -53,22 +53,26 @@ struct Maps {
 };
 
 // Tensor map of a rows x cols row-major 16-bit matrix (row stride ld elements):
-// box 64 (K) x 128 rows, 128-byte swizzle, zero fill out of bounds.
-bool make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int bf16);
-uint32_t idesc_f16(int bf16);
+// box 64 (K) x box_rows rows, 128-byte swizzle, zero fill out of bounds.  A operands
+// use 128-row boxes; B operands use boxes of the tile width bn of the launch.
+bool make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int bf16,
+              int box_rows = 128);
+uint32_t idesc_f16(int bf16, int bn = 128);
 size_t smem_bytes(int scheme);
 // Once per process and device before the first launch (and outside stream capture).
 cudaError_t prepare();
-cudaError_t launch(int scheme, const Maps& m, const GemmParams& p, int nparts, cudaStream_t st);
+// Output tiles of 128 x bn (bn = 64 or 128; the B maps must have bn-row boxes).
+cudaError_t launch(int scheme, const Maps& m, const GemmParams& p, int nparts, cudaStream_t st,
+                   int bn = 128);
 
 // Pieces of sign * scale * (in - sub) (sub may be null) for a rows x cols block.
 // scale_dev (if set) overrides scale.
 void launch_split(int scheme, int rows, int cols, const double* in, int ld_in, float scale,
                   int sign, int bf16, uint16_t* const* pieces, int ld_out, cudaStream_t st,
                   const double* sub = nullptr, const float* scale_dev = nullptr, int* err = nullptr);
-// Pieces of delta H_kj = 1/2 S_kj (dv_k + dv_j), dv = v - v_ref.  With dyn (kHead3), the
-// scales come from the bound max|dv| (dyn->max_dv): s_dh = pscale(max|dv|) and
-// s_dm = pscale(||S^-1||_inf max|dv|) are stored in dyn->s_dh / dyn->s_dm.
+// Pieces of delta H_kj = 1/2 S_kj (dv_k + dv_j) from FP32 S and dv = v - v_ref.  With dyn
+// (kHead3), the scales come from the bound max|dv| (dyn->max_dv): s_dh = pscale(max|dv|)
+// and s_dm = pscale(||S^-1||_inf max|dv|) are stored in dyn->s_dh / dyn->s_dm.
 struct DynScales {
     double max_dv;        // max |v - v_ref| of this step (atomicMax on the bit pattern)
     double max_drho[2];   // max |rho - rho_ref| per density buffer
@@ -76,9 +80,9 @@ struct DynScales {
     float s_dh, s_dm, s_rho;
     int pad;
 };
-void launch_split_dham(int scheme, int N, const double* S, const double* v, const double* vref,
-                       float scale, int bf16, uint16_t* const* pieces, int ld_out, DynScales* dyn,
-                       cudaStream_t st, int* err);
+void launch_split_dham(int scheme, int N, const float* S, const float* dv, float scale, int bf16,
+                       uint16_t* const* pieces, int ld_out, DynScales* dyn, cudaStream_t st,
+                       int* err);
 
 // Power-of-two scale mapping a magnitude bound m into (63.5, 127]: the integer heads then
 // use their full 7-bit range and K <= 1040 head products (<= 127^2 each) sum exactly in FP32.
