@@ -222,6 +222,7 @@ def main():
     ap.add_argument("--atoms", type=int, default=256)
     ap.add_argument("--cpu-steps", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -328,7 +329,8 @@ def main():
                                 "sample": f"ground state untimed, then {args.cpu_steps} oracle steps "
                                           f"of the same workload"}
     if rank == 0:
-        line["e2e"] = e2e_run(B, sysm, run, head, min(args.steps, 100), args.warmup)
+        if not args.no_e2e:
+            line["e2e"] = e2e_run(B, sysm, run, head, min(args.steps, 100), args.warmup)
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
