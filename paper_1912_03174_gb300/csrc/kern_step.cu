@@ -377,9 +377,15 @@ __global__ void __launch_bounds__(256)
                 }
                 // in the precision of X (exactly Hermitian either way: the (j,i) element
                 // repeats these operations on the swapped operands)
-                const double dre = (double)(x_ij_im + x_ji_im);
-                const double dim = (double)(-(x_ij_re - x_ji_re));
+                double dre = (double)(x_ij_im + x_ji_im);
+                double dim = (double)(-(x_ij_re - x_ji_re));
                 const size_t i = (size_t)r * N + c;
+                if (ops.zre) {
+                    // - (Z + Z^dagger), Z = S^-1 D rho (eq:eomrho, moving nuclei)
+                    const size_t j = (size_t)c * N + r;
+                    dre -= ops.zre[i] + ops.zre[j];
+                    dim -= ops.zim[i] - ops.zim[j];
+                }
                 const double nre = b_re[k] + factor * dre;
                 const double nim = b_im[k] + factor * dim;
                 ore[i] = nre;
@@ -579,11 +585,14 @@ void launch_build_hamiltonian(int N, const double* H0, const double* S, const do
 
 void launch_update(const Ctx& c, const double* Xre, const double* Xim, const double* base_re,
                    const double* base_im, double* out_re, double* out_im, double factor,
-                   const double* S, double* partial, DevScalars* sc, cudaStream_t st) {
+                   const double* S, double* partial, DevScalars* sc, cudaStream_t st,
+                   const double* zre, const double* zim) {
     dim3 b(kTile, 8);
+    UpdateOperands ops;
+    ops.zre = zre;
+    ops.zim = zim;
     k_update<double><<<dim3(c.nct, c.nct), b, 0, st>>>(c.N, c.nct, Xre, Xim, base_re, base_im,
-                                                       out_re, out_im, factor, S, partial, sc,
-                                                       UpdateOperands{});
+                                                       out_re, out_im, factor, S, partial, sc, ops);
 }
 
 void launch_update_f32(const Ctx& c, const float* Xre, const float* Xim, const double* base_re,
@@ -770,7 +779,7 @@ void launch_add_f32_strided(int N, const float* a, const float* b, int ldb, floa
 }
 
 void launch_small_energies(const Ctx& c, double* out, cudaStream_t st) {
-    k_small_energies<<<1, 256, 0, st>>>(c.nat, c.dq, c.gdq, c.d_R, c.d_V, c.d_mass, c.mp.rep_A,
+    k_small_energies<<<1, 256, 0, st>>>(c.nat, c.dq, c.gdq, c.d_R, c.d_Vn, c.d_mass, c.mp.rep_A,
                                         c.mp.rep_b, c.prm.move_nuclei, out);
 }
 

@@ -176,6 +176,16 @@ size_t carve(Ctx& c, char* base) {
         if (head3(c)) c.Xa_f = k.take<float>(NN);
         c.dyn = k.take<tc::DynScales>(1);
     }
+    if (c.prm.move_nuclei) {
+        c.d_Vn = k.take<double>(3 * nat);
+        c.d_F = k.take<double>(3 * nat);
+        c.D = k.take<double>(NN);
+        c.Zre = k.take<double>(NN);
+        c.Zim = k.take<double>(NN);
+        c.Wre = k.take<double>(NN);
+        c.pw_part = k.take<double>(kObsBlocks);
+        c.md = k.take<MdScalars>(1);
+    }
     c.d_err = k.take<int>(4);
     return k.off + 256;
 }
@@ -210,8 +220,8 @@ tdb_status validate(const tdb_system* s, const tdb_params* p) {
         set_err("invalid params");
         return TDB_ERR_ARG;
     }
-    if (p->move_nuclei) {
-        set_err("moving nuclei are not implemented by this build");
+    if (p->move_nuclei && p->precision != TDB_FP64) {
+        set_err("moving nuclei are implemented for the FP64 form only in this build");
         return TDB_ERR_UNSUPPORTED;
     }
     if (p->precision == TDB_FP16X6 && N > 1024) {
@@ -502,6 +512,71 @@ tdb_status build_maps(Ctx& c) {
     return TDB_OK;
 }
 
+// S^-1 at the current geometry without synchronising (moving nuclei): Cholesky
+// and inverse in the preallocated workspace; a non-positive-definite S shows up as
+// NaN through tdb_check.
+tdb_status enqueue_inverse(Ctx& c) {
+    const int N = c.N;
+    CK(cudaMemcpyAsync(c.Sinv, c.S, sizeof(double) * N * N, cudaMemcpyDeviceToDevice, c.stream));
+    CKS(cusolverDnDpotrf(c.solver, CUBLAS_FILL_MODE_LOWER, N, c.Sinv, N, c.inv_work, c.inv_lwork,
+                         c.inv_info));
+    CKS(cusolverDnDpotri(c.solver, CUBLAS_FILL_MODE_LOWER, N, c.Sinv, N, c.inv_work, c.inv_lwork,
+                         c.inv_info));
+    launch_symmetrize_upper_to_lower(N, c.Sinv, c.stream);
+    CKL();
+    return TDB_OK;
+}
+
+// S, H0, gamma and S^-1 at the current device geometry (moving nuclei).
+tdb_status md_model(Ctx& c) {
+    launch_build_model(c, c.d_R, c.S, c.H0, c.stream);
+    launch_build_gamma(c, c.d_R, c.gamma, c.stream);
+    CKL();
+    return enqueue_inverse(c);
+}
+
+// Everything of a moving-nuclei step up to the work rate, for rho_n in buffer cur
+// (Sec. 2.3 with the ordering: S_n, S^-1_n; q(rho_n), H_n; X_n; F_n; V_n; D_n; P_n).
+// commit = 1 inside a step (the work integral advances), 0 for observables.
+tdb_status md_forces(Ctx& c, int cur, bool first, int commit, int* n) {
+    TRY(md_model(c));
+    launch_mulliken_partials(c.N, c.rho_re[cur], c.S, c.partial, c.stream);
+    launch_charges(c, c.partial, c.q, c.dq, c.stream);
+    launch_potential(c, c.gamma, c.dq, c.d_R, c.sc, c.v_orb, c.v_atom, c.gdq, c.hist, c.v_ref,
+                     nullptr, c.stream);
+    gemm_f64_ham(c.N, c.Sinv, c.H0, c.S, c.v_orb, c.M, c.stream);            // M = S^-1 H
+    gemm_f64(c.N, c.N, c.N, c.M, c.N, c.rho_re[cur], c.N, c.Xre, c.N, c.stream);
+    gemm_f64(c.N, c.N, c.N, c.M, c.N, c.rho_im[cur], c.N, c.Xim, c.N, c.stream);
+    launch_wre(c.N, c.Xre, c.Wre, c.stream);
+    launch_forces(c, c.rho_re[cur], c.Wre, c.d_F, c.stream);
+    launch_vel_n(c, c.d_F, first ? 1 : 0, c.stream);
+    launch_build_nac(c, c.d_Vn, c.D, c.stream);
+    launch_power(c, c.Xre, c.D, c.pw_part, kObsBlocks, first ? 1 : 0, commit, c.stream);
+    CKL();
+    if (n) *n += 16;
+    return TDB_OK;
+}
+
+// One moving-nuclei step: forces as above, then Z = S^-1 D rho, the update with the
+// NAC term, and velocity Verlet for the nuclei.
+tdb_status enqueue_step_md(Ctx& c, int cur, bool euler, int* launches) {
+    const int prv = cur ^ 1;
+    int n = 0;
+    TRY(md_forces(c, cur, euler, 1, &n));
+    gemm_f64(c.N, c.N, c.N, c.Sinv, c.N, c.D, c.N, c.M, c.N, c.stream);       // Y = S^-1 D
+    gemm_f64(c.N, c.N, c.N, c.M, c.N, c.rho_re[cur], c.N, c.Zre, c.N, c.stream);
+    gemm_f64(c.N, c.N, c.N, c.M, c.N, c.rho_im[cur], c.N, c.Zim, c.N, c.stream);
+    const double factor = euler ? c.prm.dt : 2.0 * c.prm.dt;
+    const double* bre = euler ? c.rho_re[cur] : c.rho_re[prv];
+    const double* bim = euler ? c.rho_im[cur] : c.rho_im[prv];
+    launch_update(c, c.Xre, c.Xim, bre, bim, c.rho_re[prv], c.rho_im[prv], factor, c.S, c.partial,
+                  c.sc, c.stream, c.Zre, c.Zim);
+    launch_vv(c, c.d_F, c.stream);
+    CKL();
+    if (launches) *launches = n + 5;
+    return TDB_OK;
+}
+
 // Optional per-kernel timing of an enqueued step: an event before each launch.
 struct StepTimer {
     std::vector<cudaEvent_t> ev;
@@ -742,6 +817,7 @@ struct StateHeader {
     long long N, nat, n, n_base;
     double t_base, work, dt;
     int euler_next, precision;
+    double P_prev;   // moving nuclei: work rate of the previous step
 };
 
 }  // namespace
@@ -856,6 +932,27 @@ tdb_status tdb_create(const tdb_system* sys, const tdb_params* prm, void* worksp
     }
     tdb_status s = build_inverse(*c);
     if (s != TDB_OK) return fail(s);
+    if (c->prm.move_nuclei) {
+        int l1 = 0, l2 = 0;
+        if (cusolverDnDpotrf_bufferSize(c->solver, CUBLAS_FILL_MODE_LOWER, c->N, c->Sinv, c->N, &l1) !=
+                CUSOLVER_STATUS_SUCCESS ||
+            cusolverDnDpotri_bufferSize(c->solver, CUBLAS_FILL_MODE_LOWER, c->N, c->Sinv, c->N, &l2) !=
+                CUSOLVER_STATUS_SUCCESS) {
+            set_err("cusolver buffer size query failed");
+            return fail(TDB_ERR_CUDA);
+        }
+        c->inv_lwork = std::max(std::max(l1, l2), 1);
+        if (cudaMalloc(&c->inv_work, sizeof(double) * c->inv_lwork + 256) != cudaSuccess) {
+            cudaGetLastError();
+            set_err("cudaMalloc of the inverse workspace failed");
+            return fail(TDB_ERR_NOMEM);
+        }
+        c->inv_info = reinterpret_cast<int*>(reinterpret_cast<char*>(c->inv_work) +
+                                             sizeof(double) * c->inv_lwork);
+        if (cudaMemcpyAsync(c->d_Vn, c->d_V, sizeof(double) * 3 * c->nat, cudaMemcpyDeviceToDevice,
+                            c->stream) != cudaSuccess)
+            return fail(TDB_ERR_CUDA);
+    }
     if (mixed(*c)) launch_f64_to_f32((size_t)c->N * c->N, c->S, c->S_f, c->stream);
     if (c->prm.precision == TDB_FP32)
         launch_f64_to_f32((size_t)c->N * c->N, c->Sinv, c->Sinv_f, c->stream);
@@ -875,6 +972,11 @@ tdb_status tdb_ground_state(tdb_ctx* c, int* iters_out, double* residual_out) {
     TRY(check_ctx(c, false, false));
     const int N = c->N, nat = c->nat;
     double* d_eig = c->obs_out + 16;
+    if (c->prm.move_nuclei) {
+        TRY(md_model(*c));
+        CK(cudaMemsetAsync(c->md, 0, sizeof(MdScalars), c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
     double* d_occ = c->obs_out + 16 + N;
     // the ground state is field-free; the field applies from t = 0 on
     const bool saved_on = c->field_on;
@@ -964,6 +1066,12 @@ tdb_status tdb_ground_state(tdb_ctx* c, int* iters_out, double* residual_out) {
         if (rc == TDB_ERR_SCC_NOCONV) set_err("SCC not converged: residual %.3e", res);
         return rc;
     }
+    // rho_0 = Z f Z^T is symmetric only up to rounding; make it exactly symmetric
+    launch_hermitian_half(N, c->rho_re[0], c->rho_im[0], c->Xre, c->Xim, c->stream);
+    CK(cudaMemcpyAsync(c->rho_re[0], c->Xre, sizeof(double) * N * N, cudaMemcpyDeviceToDevice,
+                       c->stream));
+    CK(cudaMemcpyAsync(c->rho_im[0], c->Xim, sizeof(double) * N * N, cudaMemcpyDeviceToDevice,
+                       c->stream));
     c->spectral_width = eig[N - 1] - eig[0];
     c->cur = 0;
     c->euler_next = true;
@@ -995,6 +1103,7 @@ tdb_status tdb_kick(tdb_ctx* c, double strength, const double dir[3]) {
         return TDB_ERR_ARG;
     }
     const int N = c->N, cur = c->cur;
+    if (c->prm.move_nuclei) TRY(md_model(*c));
     // eq:rhokick: T = e^{iV} rho S e^{-iV} S^-1,  rho(0+) = 1/2 (T + T^dagger)
     gemm_f64(N, N, N, c->rho_re[cur], N, c->S, N, c->Xre, N, c->stream);
     gemm_f64(N, N, N, c->rho_im[cur], N, c->S, N, c->Xim, N, c->stream);
@@ -1039,6 +1148,18 @@ tdb_status tdb_step(tdb_ctx* c, long n) {
         return TDB_ERR_UNSTABLE;
     }
     long launches = 0;
+    if (c->prm.move_nuclei) {
+        for (long k = 0; k < n; ++k) {
+            int nl = 0;
+            TRY(enqueue_step_md(*c, c->cur, c->euler_next, &nl));
+            launches += nl;
+            c->euler_next = false;
+            c->cur ^= 1;
+            c->n += 1;
+        }
+        c->last_launches = launches;
+        return TDB_OK;
+    }
     for (long k = 0; k < n; ++k) {
         if (c->euler_next) {
             int nl = 0;
@@ -1063,8 +1184,8 @@ tdb_status tdb_observables(tdb_ctx* c, tdb_obs* o, double* charges, double* forc
         set_err("NULL obs");
         return TDB_ERR_ARG;
     }
-    if (forces) {
-        set_err("forces need moving-nuclei support, not in this build");
+    if (forces && !c->prm.move_nuclei) {
+        set_err("forces are evaluated for moving nuclei (move_nuclei = 1)");
         return TDB_ERR_UNSUPPORTED;
     }
     const int cur = c->cur;
@@ -1078,9 +1199,13 @@ tdb_status tdb_observables(tdb_ctx* c, tdb_obs* o, double* charges, double* forc
             return TDB_ERR_TIMEOUT;
         }
     }
-    launch_charges(*c, c->partial, c->q, c->dq, c->stream);
-    launch_potential(*c, c->gamma, c->dq, c->d_R, c->sc, c->v_orb, c->v_atom, c->gdq, c->hist,
-                     c->v_ref, nullptr, c->stream);
+    if (c->prm.move_nuclei) {
+        TRY(md_forces(*c, cur, c->euler_next, 0, nullptr));
+    } else {
+        launch_charges(*c, c->partial, c->q, c->dq, c->stream);
+        launch_potential(*c, c->gamma, c->dq, c->d_R, c->sc, c->v_orb, c->v_atom, c->gdq, c->hist,
+                         c->v_ref, nullptr, c->stream);
+    }
     launch_obs_reduce(c->N, c->rho_re[cur], c->rho_im[cur], c->H0, c->S, c->obs_blocks, kObsBlocks,
                       c->stream);
     launch_obs_finish(kObsBlocks, c->obs_blocks, c->obs_out, c->stream);
@@ -1094,6 +1219,13 @@ tdb_status tdb_observables(tdb_ctx* c, tdb_obs* o, double* charges, double* forc
     CK(cudaMemcpyAsync(hs, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
     if (charges)
         CK(cudaMemcpyAsync(hq, c->q, sizeof(double) * c->nat, cudaMemcpyDeviceToHost, c->stream));
+    MdScalars hm{};
+    if (c->prm.move_nuclei) {
+        CK(cudaMemcpyAsync(&hm, c->md, sizeof hm, cudaMemcpyDeviceToHost, c->stream));
+        if (forces)
+            CK(cudaMemcpyAsync(forces, c->d_F, sizeof(double) * 3 * c->nat, cudaMemcpyDeviceToHost,
+                               c->stream));
+    }
     CK(cudaStreamSynchronize(c->stream));
     if (charges) std::memcpy(charges, hq, sizeof(double) * c->nat);
     const DevScalars h = *hs;
@@ -1109,7 +1241,7 @@ tdb_status tdb_observables(tdb_ctx* c, tdb_obs* o, double* charges, double* forc
     o->E_rep = red[5];
     o->E_kin = red[6];
     o->E_ext = h.e_ext;
-    o->work = c->work;
+    o->work = c->prm.move_nuclei ? hm.work_now : c->work;
     o->E_total = o->E_band + o->E_coul + o->E_rep + o->E_kin + o->E_ext;
     return TDB_OK;
 }
@@ -1168,8 +1300,19 @@ tdb_status tdb_get_state(tdb_ctx* c, void* buf, size_t bytes) {
     DevScalars h{};
     CK(cudaMemcpyAsync(&h, c->sc, sizeof h, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    StateHeader hd{kStateMagic, c->N, c->nat, h.step, h.n_base, h.t_base, c->work, c->prm.dt,
-                   c->euler_next ? 1 : 0, c->prm.precision};
+    MdScalars hm{};
+    if (c->prm.move_nuclei) {
+        CK(cudaMemcpyAsync(&hm, c->md, sizeof hm, cudaMemcpyDeviceToHost, c->stream));
+        // positions R_n and velocities V_{n-1/2} (V_0 before the first step) live on the device
+        CK(cudaMemcpyAsync(c->R.data(), c->d_R, sizeof(double) * 3 * c->nat, cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaMemcpyAsync(c->V.data(), c->d_V, sizeof(double) * 3 * c->nat, cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    StateHeader hd{kStateMagic, c->N, c->nat, h.step, h.n_base, h.t_base,
+                   c->prm.move_nuclei ? hm.work : c->work, c->prm.dt, c->euler_next ? 1 : 0,
+                   c->prm.precision, hm.P_prev};
     char* p = static_cast<char*>(buf);
     std::memcpy(p, &hd, sizeof hd);
     p += sizeof hd;
@@ -1212,6 +1355,21 @@ tdb_status tdb_set_state(tdb_ctx* c, const void* buf, size_t bytes) {
     CK(cudaMemcpyAsync(c->rho_im[prv], p + b, b, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->rho_re[cur], p + 2 * b, b, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->rho_im[cur], p + 3 * b, b, cudaMemcpyHostToDevice, c->stream));
+    if (c->prm.move_nuclei) {
+        const char* q = p + 4 * b;
+        std::memcpy(c->R.data(), q, sizeof(double) * 3 * c->nat);
+        std::memcpy(c->V.data(), q + sizeof(double) * 3 * c->nat, sizeof(double) * 3 * c->nat);
+        CK(cudaMemcpyAsync(c->d_R, c->R.data(), sizeof(double) * 3 * c->nat, cudaMemcpyHostToDevice,
+                           c->stream));
+        CK(cudaMemcpyAsync(c->d_V, c->V.data(), sizeof(double) * 3 * c->nat, cudaMemcpyHostToDevice,
+                           c->stream));
+        CK(cudaMemcpyAsync(c->d_Vn, c->V.data(), sizeof(double) * 3 * c->nat, cudaMemcpyHostToDevice,
+                           c->stream));
+        MdScalars hm{hd.work, hd.P_prev, 0.0, hd.work};
+        CK(cudaMemcpyAsync(c->md, &hm, sizeof hm, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        TRY(md_model(*c));
+    }
     CK(cudaStreamSynchronize(c->stream));
     c->euler_next = hd.euler_next != 0;
     c->work = hd.work;
@@ -1273,6 +1431,7 @@ void tdb_destroy(tdb_ctx* c) {
         if (g) cudaGraphExecDestroy(g);
     if (c->solver) cusolverDnDestroy(c->solver);
     if (c->own_ws && c->ws) cudaFree(c->ws);
+    if (c->inv_work) cudaFree(c->inv_work);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     delete c;

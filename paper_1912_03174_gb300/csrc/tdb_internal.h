@@ -38,6 +38,14 @@ struct DevScalars {
     long long hist_cap;
 };
 
+// Moving-nuclei scalars: the work integral of P = Re Tr[S^-1 H rho (D - D^T)].
+struct MdScalars {
+    double work;      // int_0^{t_{n-1}} P dt (trapezoid), committed
+    double P_prev;    // P_{n-1}
+    double P_now;     // P of the last evaluated state
+    double work_now;  // work including P_now
+};
+
 // Parameters of the synthetic two-centre model.
 struct ModelParams {
     double t0, lam_H, s0, lam_S;
@@ -111,6 +119,16 @@ struct Ctx {
     char* h_pinned = nullptr;
     size_t h_pinned_bytes = 0;
 
+    // moving nuclei (Ehrenfest): per-step buffers
+    double *d_Vn = nullptr;                          // V_n (d_V holds V_{n-1/2}, or V_0)
+    double *d_F = nullptr;                           // [nat][3] forces F_n
+    double *D = nullptr, *Zre = nullptr, *Zim = nullptr, *Wre = nullptr;   // N x N
+    double *pw_part = nullptr;                       // work-rate block partials
+    MdScalars* md = nullptr;
+    double* inv_work = nullptr;                      // cuSOLVER workspace (potrf/potri)
+    int inv_lwork = 0;
+    int* inv_info = nullptr;
+
     cusolverDnHandle_t solver = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int graph_launches = 0;      // kernels per captured step
@@ -135,7 +153,8 @@ void launch_build_hamiltonian(int N, const double* H0, const double* S, const do
                               double* H, cudaStream_t st);
 void launch_update(const Ctx& c, const double* Xre, const double* Xim, const double* base_re,
                    const double* base_im, double* out_re, double* out_im, double factor,
-                   const double* S, double* partial, DevScalars* sc, cudaStream_t st);
+                   const double* S, double* partial, DevScalars* sc, cudaStream_t st,
+                   const double* zre = nullptr, const double* zim = nullptr);
 // Operands written by the update for the next step's products.
 struct UpdateOperands {
     const double* rho_ref = nullptr;   // deviations are taken from this (real) matrix
@@ -149,6 +168,8 @@ struct UpdateOperands {
     tc::DynScales* dyn = nullptr;      // kHead3: s = pscale(max_drho[cur]); tracks the new max
     int cur = 0;
     const float* Xre2 = nullptr;       // added to X_re when set
+    const double* zre = nullptr;       // NAC term Z = S^-1 D rho (moving nuclei, FP64 form)
+    const double* zim = nullptr;
 };
 void launch_update_f32(const Ctx& c, const float* Xre, const float* Xim, const double* base_re,
                        const double* base_im, double* out_re, double* out_im, double factor,
@@ -163,6 +184,14 @@ void launch_obs_reduce(int N, const double* rho_re, const double* rho_im, const 
                        const double* S, double* block_out, int n_blocks, cudaStream_t st);
 void launch_obs_finish(int n_blocks, const double* block_out, double* out4, cudaStream_t st);
 void launch_scale_rows_f(int N, const double* in, const double* f, double* out, cudaStream_t st);
+// moving nuclei (kern_md.cu)
+void launch_forces(const Ctx& c, const double* rre, const double* wre, double* F, cudaStream_t st);
+void launch_wre(int N, const double* xre, double* wre, cudaStream_t st);
+void launch_build_nac(const Ctx& c, const double* V, double* D, cudaStream_t st);
+void launch_power(const Ctx& c, const double* xre, const double* D, double* part, int nb, int first,
+                  int commit, cudaStream_t st);
+void launch_vel_n(const Ctx& c, const double* F, int first, cudaStream_t st);
+void launch_vv(const Ctx& c, const double* F, cudaStream_t st);
 // FP16X6: head pieces of rho - rho_ref (scale from c.dyn->max_drho[slot]) into the B operands
 void launch_split_rho(const Ctx& c, int slot, const double* rre, const double* rim, cudaStream_t st);
 

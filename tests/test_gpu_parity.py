@@ -230,3 +230,72 @@ def test_exact_head_form_beats_the_hi_lo_forms(B):
         e[form] = np.max(np.abs(g["hist"] - ref["hist"]))
     assert e["fp16x6"] < e["fp16x3"] / 4, e
     assert e["fp16x6"] < e["bf16x3"] / 4, e
+
+
+# ---------------------------------------------------------------------------
+# moving nuclei (Ehrenfest, eq:forces, eq:nac, velocity Verlet)
+# ---------------------------------------------------------------------------
+
+def _md_gpu(B, sysm, run, n):
+    with B.Propagator(sysm, run, "fp64") as p:
+        p.setup()
+        p.step(n)
+        hist = B.tdb_dipole_history(p.ctx, n)
+        obs = p.observables(forces=True)
+        rho, prev = B.tdb_get_rho(p.ctx, prev=True)
+        blob = B.tdb_get_state(p.ctx)
+    nat = sysm.n_atoms
+    tail = np.frombuffer(blob[len(blob) - 6 * 8 * nat:], dtype=np.float64)
+    return dict(hist=hist, obs=obs, rho=rho, prev=prev, R=tail[:3 * nat].reshape(nat, 3),
+                V=tail[3 * nat:].reshape(nat, 3))
+
+
+@pytest.mark.parametrize("n_atoms,seed,laser", [(6, 23, False), (12, 5, True), (33, 7, False)])
+def test_ehrenfest_matches_oracle(B, n_atoms, seed, laser):
+    sysm = I.small_cluster(n_atoms, seed=seed, T=3000.0)
+    fld = I.Field(E0=0.01, omega=0.1, phase=0.2, t_center=20.0, fwhm=20.0, envelope=1) if laser else None
+    run = I.Run(dt=0.2, n_steps=0, scc=True, move_nuclei=True, kick=1e-2 if not laser else 0.0,
+                field=fld, kT=I.SCC_KT)
+    n = 200
+    g = _md_gpu(B, sysm, run, n)
+    rho0, gs, S, Sinv = O.setup(sysm, run)
+    tr = O.propagate(sysm, run, rho0, n, keep_forces=True)
+    mu = np.vstack([g["hist"], g["obs"]["dipole"][None, :]])
+    assert np.max(np.abs(mu - tr.dipole)) < 1e-9
+    assert np.max(np.abs(g["R"] - tr.R)) < 1e-9
+    assert np.max(np.abs(g["V"] - tr.V)) < 1e-12
+    assert np.max(np.abs(g["obs"]["forces"] - tr.forces[-1])) < 1e-9
+    assert np.max(np.abs(g["obs"]["charges"] - tr.charges[-1])) < 1e-9
+    assert np.max(np.abs(g["rho"] - tr.rho)) < 1e-9
+    assert abs(g["obs"]["E_total"] - tr.energy[-1]) < 1e-9
+    assert abs(g["obs"]["work"] - tr.work[-1]) < 1e-10
+    assert abs(g["obs"]["trace_re"] - tr.trace[-1].real) < 1e-10
+    assert g["obs"]["herm_err"] == 0.0
+
+
+def test_ehrenfest_energy_balance_on_gpu(B):
+    # E - int P dt stays constant to O(dt^2) on the device too (the oracle's pin, GPU form)
+    sysm = I.small_cluster(8, seed=29, T=3000.0)
+    run = I.Run(dt=0.1, n_steps=0, scc=True, move_nuclei=True, kick=1e-2, kT=I.SCC_KT)
+    bal = []
+    with B.Propagator(sysm, run, "fp64") as p:
+        p.setup()
+        for _ in range(8):
+            o = p.observables()
+            bal.append(o["E_total"] - o["work"])
+            p.step(100)
+    assert np.max(np.abs(np.array(bal) - bal[0])) < 1e-6
+
+
+def test_ehrenfest_checkpoint_resume_is_bitwise(B):
+    sysm = I.small_cluster(10, seed=3, T=1000.0)
+    run = I.Run(dt=0.2, n_steps=0, scc=True, move_nuclei=True, kick=1e-2, kT=I.SCC_KT)
+    with B.Propagator(sysm, run) as a, B.Propagator(sysm, run) as b:
+        a.setup()
+        b.setup()
+        a.step(23)
+        B.tdb_set_state(b.ctx, B.tdb_get_state(a.ctx))
+        a.step(40)
+        b.step(40)
+        assert np.array_equal(B.tdb_get_rho(a.ctx), B.tdb_get_rho(b.ctx))
+        assert B.tdb_get_state(a.ctx) == B.tdb_get_state(b.ctx)
