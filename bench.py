@@ -48,8 +48,10 @@ KERNEL_BYTES = {
     # reads X (re, im; both halves once), rho_{n-1}, S; writes rho_{n+1} (+ operands)
     "update_f64": lambda N: N * N * 8 * (2 + 2 + 1 + 2),
     "update_f32": lambda N: N * N * (4 * 2 + 8 * 2 + 8 + 8 * 2 + 4 * 2),
-    # reads X (2 x f32), rho_{n-1} (2 x f64), S, rho_ref; writes rho_{n+1} (2 x f64), 4 x 16-bit pieces
+    # reads X (2 x f32; FP16X6 3 x f32), rho_{n-1} (2 x f64), S, rho_ref; writes rho_{n+1}
+    # (2 x f64) and the operand pieces (hi/lo: 4 x 16 bit; FP16X6: 6 x 16 bit)
     "update_tc": lambda N: N * N * (4 * 2 + 8 * 2 + 8 + 8 + 8 * 2 + 2 * 4),
+    "update_fp16x6": lambda N: N * N * (4 * 3 + 8 * 2 + 8 + 8 + 8 * 2 + 2 * 6),
     # reads S (f64), writes 2 x 16-bit pieces
     "split_dH": lambda N: N * N * (8 + 2 * 2),
     # reads rho (2 x f64) and rho_ref, writes 6 x 16-bit pieces
@@ -297,7 +299,7 @@ def main():
                 "peak_source": f"derived from unit counts at {peaks.get('sm_max_mhz', 2070.0):.0f} MHz"
                 if kind == "f32" else "GB300 nominal FP64 1.25 TFLOP/s"}
     else:
-        key = {"fp64": "update_f64", "fp32": "update_f32"}.get(head, "update_tc")
+        key = {"fp64": "update_f64", "fp32": "update_f32", "fp16x6": "update_fp16x6"}.get(head, "update_tc")
         key = name if name in KERNEL_BYTES else key
         ach = KERNEL_BYTES[key](N) / (t_ms * 1e-3) / 1e9
         roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",

@@ -169,18 +169,27 @@ __global__ void k_transpose(int N, const double* __restrict__ in, double* __rest
 }
 
 // partial[row][ct] = sum over the 32 columns of tile ct of Re rho[row][col] * S[row][col]
-// (eq:qmulik: q_A = sum_{nu in A} Re (rho S)_{nu nu}; S is symmetric).
+// (eq:qmulik: q_A = sum_{nu in A} Re (rho S)_{nu nu}; S is symmetric).  Summed in
+// column order, exactly as the update kernel sums them, so a state loaded from a
+// checkpoint continues bitwise.
 __global__ void k_mulliken_partials(int N, int nct, const double* __restrict__ rre,
                                     const double* __restrict__ S, double* __restrict__ partial) {
+    __shared__ double pv_s[kTile][kTile + 1];
     const int ct = blockIdx.x;
     const int col = ct * kTile + threadIdx.x;
     for (int y = threadIdx.y; y < kTile; y += blockDim.y) {
         const int row = blockIdx.y * kTile + y;
-        if (row >= N) continue;
         double v = 0.0;
-        if (col < N) v = rre[(size_t)row * N + col] * S[(size_t)row * N + col];
-        v = warp_sum(v);
-        if (threadIdx.x == 0) partial[(size_t)row * nct + ct] = v;
+        if (row < N && col < N) v = rre[(size_t)row * N + col] * S[(size_t)row * N + col];
+        pv_s[y][threadIdx.x] = v;
+    }
+    __syncthreads();
+    if (threadIdx.y == 0) {
+        const int row = blockIdx.y * kTile + threadIdx.x;
+        double sum = 0.0;
+#pragma unroll 8
+        for (int k = 0; k < kTile; ++k) sum += pv_s[threadIdx.x][k];
+        if (row < N) partial[(size_t)row * nct + ct] = sum;
     }
 }
 
@@ -188,12 +197,20 @@ __global__ void k_mulliken_partials(int N, int nct, const double* __restrict__ r
 // [row][ct] layout): one warp per atom.
 __global__ void k_charges(int nat, int nper, int nct, const double* __restrict__ partial,
                           const double* __restrict__ q0, double* __restrict__ q,
-                          double* __restrict__ dq, double* reset0, double* reset1) {
+                          double* __restrict__ dq, double* reset0, double* reset1,
+                          tc::DynScales* __restrict__ dyn, int cur) {
     const int lane = threadIdx.x & 31;
     const int A = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         if (reset0) *reset0 = 0.0;
         if (reset1) *reset1 = 0.0;
+        if (dyn) {
+            // FP16X6 bookkeeping of a step: the maximum of the deviation written by the
+            // previous update now describes buffer cur; start this step's maxima
+            dyn->max_drho[cur] = dyn->max_drho[2];
+            dyn->max_drho[2] = 0.0;
+            dyn->max_x[0] = dyn->max_x[1] = dyn->max_x[2] = 0.0;
+        }
     }
     if (A >= nat) return;
     const double* p = partial + (size_t)A * nper * nct;
@@ -285,6 +302,121 @@ __global__ void k_potential(int nat, int nper, int scc, const double* __restrict
     }
 }
 
+// Charges and SCC potential in one launch (frozen-nuclei steps).  Every block first
+// sums the Mulliken row partials of all atoms into shared memory (they are small and
+// L2-resident), then each warp forms v_A = [scc] sum_B gamma_AB dq_B + R_A . E(t_n) for
+// its atoms.  Block 0 writes q, dq, the dipole and E(t_n), and does the FP16X6 scale
+// bookkeeping of this step (dyn may be null).
+__global__ void k_charges_potential(int nat, int nper, int nct, int scc,
+                                    const double* __restrict__ partial,
+                                    const double* __restrict__ q0,
+                                    const double* __restrict__ gamma, const double* __restrict__ R,
+                                    DevScalars* __restrict__ sc, double* __restrict__ q,
+                                    double* __restrict__ dq, double* __restrict__ v_orb,
+                                    double* __restrict__ v_atom, double* __restrict__ gdq,
+                                    double* __restrict__ hist, const double* __restrict__ v_ref,
+                                    float* __restrict__ dv_f, tc::DynScales* __restrict__ dyn,
+                                    int cur) {
+    extern __shared__ double dq_s[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarp = blockDim.x >> 5;
+    if (dyn && blockIdx.x == 0 && threadIdx.x == 0) {
+        // the maximum of the deviation written by the previous update now describes
+        // buffer cur; start the maxima of this step
+        dyn->max_drho[cur] = dyn->max_drho[2];
+        dyn->max_drho[2] = 0.0;
+        dyn->max_x[0] = dyn->max_x[1] = dyn->max_x[2] = 0.0;
+    }
+    // charges of all atoms: each warp reduces groups of 8 atoms, issuing the loads of the
+    // whole group before the reductions so they overlap
+    const int L = nper * nct;
+    for (int B0 = warp * 8; B0 < nat; B0 += nwarp * 8) {
+        double s[8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            s[a] = 0.0;
+            if (B0 + a < nat) {
+                const double* p = partial + (size_t)(B0 + a) * L;
+                for (int i = lane; i < L; i += 32) s[a] += p[i];
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const double t = warp_sum(s[a]);
+            if (lane == 0 && B0 + a < nat) dq_s[B0 + a] = t - q0[B0 + a];
+        }
+    }
+    __syncthreads();
+    const long long n = sc->step;
+    const double t = sc->t_base + (double)(n - sc->n_base) * sc->dt;
+    double E[3];
+    field_at(sc->field, t, E);
+    for (int A = blockIdx.x * nwarp + warp; A < nat; A += gridDim.x * nwarp) {
+        double s = 0.0;
+        if (scc)
+            for (int B = lane; B < nat; B += 32) s += gamma[(size_t)A * nat + B] * dq_s[B];
+        s = warp_sum(s);
+        const double vA = s + R[3 * A] * E[0] + R[3 * A + 1] * E[1] + R[3 * A + 2] * E[2];
+        if (lane < nper) {
+            const int o = A * nper + lane;
+            v_orb[o] = vA;
+            if (dv_f) dv_f[o] = (float)(vA - v_ref[o]);
+        }
+        if (lane == 0) {
+            v_atom[A] = vA;
+            gdq[A] = s;
+            if (dyn)
+                atomicMax(reinterpret_cast<unsigned long long*>(&dyn->max_dv),
+                          (unsigned long long)__double_as_longlong(fabs(vA - v_ref[A * nper])));
+        }
+    }
+    if (blockIdx.x == 0) {
+        __shared__ double red[4][32];
+        double m0 = 0, m1 = 0, m2 = 0, ee = 0;
+        for (int A = threadIdx.x; A < nat; A += blockDim.x) {
+            const double d = dq_s[A];
+            q[A] = d + q0[A];
+            dq[A] = d;
+            m0 -= d * R[3 * A];
+            m1 -= d * R[3 * A + 1];
+            m2 -= d * R[3 * A + 2];
+            ee += d * (R[3 * A] * E[0] + R[3 * A + 1] * E[1] + R[3 * A + 2] * E[2]);
+        }
+        m0 = warp_sum(m0);
+        m1 = warp_sum(m1);
+        m2 = warp_sum(m2);
+        ee = warp_sum(ee);
+        if (lane == 0) {
+            red[0][warp] = m0;
+            red[1][warp] = m1;
+            red[2][warp] = m2;
+            red[3][warp] = ee;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0, b = 0, c = 0, e = 0;
+            for (int w = 0; w < nwarp; ++w) {
+                a += red[0][w];
+                b += red[1][w];
+                c += red[2][w];
+                e += red[3][w];
+            }
+            sc->mu[0] = a;
+            sc->mu[1] = b;
+            sc->mu[2] = c;
+            sc->e_ext = e;
+            sc->E[0] = E[0];
+            sc->E[1] = E[1];
+            sc->E[2] = E[2];
+            const long long slot = n % sc->hist_cap;
+            const long long s2 = slot < 0 ? slot + sc->hist_cap : slot;
+            hist[3 * s2] = a;
+            hist[3 * s2 + 1] = b;
+            hist[3 * s2 + 2] = c;
+        }
+    }
+}
+
 __global__ void k_build_hamiltonian(int N, const double* __restrict__ H0,
                                     const double* __restrict__ S, const double* __restrict__ v,
                                     double* __restrict__ H) {
@@ -311,6 +443,20 @@ __global__ void __launch_bounds__(256)
     const int bi = blockIdx.y, bj = blockIdx.x;
     if (bi > bj) return;
     constexpr int RPT = kTile / 8;   // rows per thread
+    double op_scale = ops.scale;
+    if (ops.dyn) {
+        // rigorous bound on |rho_{n+1} - rho_ref|: |base| + factor 2 max|X| (Re rhodot uses
+        // Im X twice, Im rhodot uses Re X = X_a + X_re twice); one thread per block
+        // evaluates it (FP64 frexp/ldexp are slow here)
+        __shared__ float s_bound;
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            const tc::DynScales* d = ops.dyn;
+            const double xm = fmax(d->max_x[2], d->max_x[0] + d->max_x[1]);
+            s_bound = tc::pscale(d->max_drho[ops.base_slot] + fabs(factor) * 2.0 * xm);
+        }
+        __syncthreads();
+        op_scale = (double)s_bound;
+    }
     __shared__ T xr_ij[kTile][kTile + 1], xi_ij[kTile][kTile + 1];
     __shared__ T xr_ji[kTile][kTile + 1], xi_ji[kTile][kTile + 1];
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -341,7 +487,8 @@ __global__ void __launch_bounds__(256)
         xi_ji[y][tx] = b;
     }
     __syncthreads();
-    float dmax = 0.f;   // max |rho_{n+1} - rho_ref| (FP16X6 scale tracking)
+    float dmax = 0.f;   // max |rho_{n+1} - rho_ref| of this block (FP16X6 scale tracking)
+    __shared__ double pv_s[kTile][kTile + 1];
     for (int half = 0; half < (bi == bj ? 1 : 2); ++half) {
         const int ti = half ? bj : bi, tj = half ? bi : bj;
         double b_re[RPT], b_im[RPT], s_v[RPT], r_v[RPT];
@@ -393,12 +540,30 @@ __global__ void __launch_bounds__(256)
                 pv = nre * s_v[k];
                 if (ops.rho_ref) {
                     const double d_re = nre - r_v[k];
-                    if (ops.dyn) dmax = fmaxf(dmax, fmaxf(fabsf((float)d_re), fabsf((float)nim)));
+                    if (ops.dyn) {
+                        const float fre = (float)d_re, fim = (float)nim;
+                        dmax = fmaxf(dmax, fmaxf(fabsf(fre), fabsf(fim)));
+                        if (ops.re[2]) {
+                            // FP16X6 operands: head + two tails of the scaled deviation
+                            const float fs = (float)op_scale;
+                            uint16_t q[3];
+                            const size_t jr = (size_t)r * ops.ld_re + c;
+                            const size_t ji = (size_t)r * ops.ld_im + c;
+                            split_head3(fre * fs, q);
+                            ops.re[0][jr] = q[0];
+                            ops.re[1][jr] = q[1];
+                            ops.re[2][jr] = q[2];
+                            split_head3(-fim * fs, q);
+                            ops.im[0][ji] = q[0];
+                            ops.im[1][ji] = q[1];
+                            ops.im[2][ji] = q[2];
+                        }
+                    }
                     if (ops.f_re) {
                         ops.f_re[i] = (float)d_re;
                         ops.f_im[i] = (float)nim;
                     }
-                    if (ops.re[0]) {
+                    if (ops.re[0] && !ops.re[2]) {
                         // operands of the tensor-core products are K-major: Re rho is
                         // symmetric, and the transpose of Im rho is -Im rho
                         const size_t jr = (size_t)r * ops.ld_re + c;
@@ -414,15 +579,28 @@ __global__ void __launch_bounds__(256)
                     }
                 }
             }
-            pv = warp_sum(pv);
-            if (tx == 0 && r < N) partial[(size_t)r * nct + tj] = pv;
+            pv_s[y][tx] = pv;
         }
+        // Mulliken row partials: thread (tx, ty == 0) sums row tx of this tile
+        __syncthreads();
+        if (ty == 0) {
+            const int r = ti * kTile + tx;
+            double sum = 0.0;
+#pragma unroll 8
+            for (int k = 0; k < kTile; ++k) sum += pv_s[tx][k];
+            if (r < N) partial[(size_t)r * nct + tj] = sum;
+        }
+        __syncthreads();
     }
     if (ops.dyn) {
         for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
         if (tx == 0)
-            atomicMax(reinterpret_cast<unsigned long long*>(&ops.dyn->max_drho[ops.cur ^ 1]),
+            atomicMax(reinterpret_cast<unsigned long long*>(&ops.dyn->max_drho[2]),
                       (unsigned long long)__double_as_longlong((double)dmax));
+        if (bi == 0 && bj == 0 && tx == 0 && ty == 0) {
+            ops.dyn->s_rho = (float)op_scale;   // scale of the pieces just written
+            ops.dyn->max_dv = 0.0;              // the next step's potential accumulates anew
+        }
     }
     if (bi == 0 && bj == 0 && threadIdx.x == 0 && threadIdx.y == 0) sc->step += 1;
 }
@@ -563,9 +741,9 @@ void launch_mulliken_partials(int N, const double* rho_re, const double* S, doub
 }
 
 void launch_charges(const Ctx& c, const double* partial, double* q, double* dq, cudaStream_t st,
-                    double* reset0, double* reset1) {
+                    double* reset0, double* reset1, tc::DynScales* dyn, int cur) {
     k_charges<<<(c.nat + 7) / 8, 256, 0, st>>>(c.nat, c.nper, c.nct, partial, c.d_q0, q, dq,
-                                               reset0, reset1);
+                                               reset0, reset1, dyn, cur);
 }
 
 void launch_potential(const Ctx& c, const double* gamma, const double* dq, const double* R,
@@ -575,6 +753,14 @@ void launch_potential(const Ctx& c, const double* gamma, const double* dq, const
     const int blocks = (c.nat + warps - 1) / warps;
     k_potential<<<blocks, warps * 32, 0, st>>>(c.nat, c.nper, c.prm.scc, gamma, dq, R, sc, v_orb,
                                                v_atom, gdq, hist, v_ref, dv_orb, max_dv);
+}
+
+void launch_charges_potential(const Ctx& c, tc::DynScales* dyn, int cur, cudaStream_t st) {
+    const int warps = 8;
+    const int blocks = (c.nat + warps - 1) / warps;
+    k_charges_potential<<<blocks, warps * 32, sizeof(double) * c.nat, st>>>(
+        c.nat, c.nper, c.nct, c.prm.scc, c.partial, c.d_q0, c.gamma, c.d_R, c.sc, c.q, c.dq,
+        c.v_orb, c.v_atom, c.gdq, c.hist, c.v_ref, c.dv_f, dyn, cur);
 }
 
 void launch_build_hamiltonian(int N, const double* H0, const double* S, const double* v_orb,

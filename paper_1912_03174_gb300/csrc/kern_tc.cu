@@ -37,19 +37,26 @@ template <int SCHEME>
 struct Cfg;
 template <>
 struct Cfg<kHiLo> {
-    static constexpr int PIECES = 2, STAGES = 3, ACCS = 1;
+    static constexpr int PIECES = 2, ACCS = 1;
 };
 template <>
 struct Cfg<kHead3> {
-    static constexpr int PIECES = 3, STAGES = 2, ACCS = 2;
+    static constexpr int PIECES = 3, ACCS = 2;
 };
 template <int S, int BN>
 __host__ __device__ constexpr int stage_bytes() {
     return Cfg<S>::PIECES * (TILE_BYTES + BN * BK * 2);
 }
+// as many ring stages as fit in 227 KiB of shared memory (at most 4)
+template <int S, int BN>
+__host__ __device__ constexpr int stages() {
+    return (227 * 1024 - 1024 - 256) / stage_bytes<S, BN>() > 4
+               ? 4
+               : (227 * 1024 - 1024 - 256) / stage_bytes<S, BN>();
+}
 template <int S, int BN>
 __host__ __device__ constexpr int smem_total() {
-    return Cfg<S>::STAGES * stage_bytes<S, BN>() + 1024 + 256;
+    return stages<S, BN>() * stage_bytes<S, BN>() + 1024 + 256;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -181,7 +188,7 @@ __device__ __forceinline__ bool split_value(float x, int bf16, uint16_t (&q)[3])
 template <int SCHEME, int BN>
 __global__ void __launch_bounds__(128, 1)
     k_split_gemm(const __grid_constant__ Maps maps, GemmParams p) {
-    constexpr int PIECES = Cfg<SCHEME>::PIECES, STAGES = Cfg<SCHEME>::STAGES;
+    constexpr int PIECES = Cfg<SCHEME>::PIECES, STAGES = stages<SCHEME, BN>();
     constexpr int ACCS = Cfg<SCHEME>::ACCS, SB = stage_bytes<SCHEME, BN>();
     constexpr int BTILE = BN * BK * 2;
     constexpr uint32_t TMEM_COLS = static_cast<uint32_t>(ACCS * BN) < 32u ? 32u : static_cast<uint32_t>(ACCS * BN);
@@ -294,6 +301,17 @@ __global__ void __launch_bounds__(128, 1)
                 for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]) * inv;
             }
             const int col0 = n0 + c * 32;
+            if (P.mode == 0 && p.max_out) {
+                float m = 0.f;
+                if (row < p.M)
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (col0 + j < p.N) m = fmaxf(m, fabsf(v[j]));
+                for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                if (lane == 0)
+                    atomicMax(reinterpret_cast<unsigned long long*>(&p.max_out[blockIdx.z]),
+                              static_cast<unsigned long long>(__double_as_longlong(static_cast<double>(m))));
+            }
             if (row >= p.M) continue;
             if (P.mode == 0) {
                 float* out = P.C + static_cast<size_t>(row) * P.ldc + col0;

@@ -432,6 +432,10 @@ tdb_status refresh_derived(Ctx& c) {
                           c.rho_ref);
             launch_absmax((size_t)N * N, c.rho_im[c.cur], &c.dyn->max_drho[c.cur], c.stream);
             launch_split_rho(c, c.cur, c.rho_re[c.cur], c.rho_im[c.cur], c.stream);
+            // the next step's bookkeeping moves max_drho[2] into max_drho[cur]: keep it equal
+            CK(cudaMemcpyAsync(&c.dyn->max_drho[2], &c.dyn->max_drho[c.cur], sizeof(double),
+                               cudaMemcpyDeviceToDevice, c.stream));
+            CK(cudaMemsetAsync(&c.dyn->max_dv, 0, sizeof(double), c.stream));
         } else {
             uint16_t* re[3] = {c.pc_bre[0] + c.Np, c.pc_bre[1] + c.Np, nullptr};
             tc::launch_split(c.scheme, N, N, c.rho_re[c.cur], N, c.s_rho, 1, b, re, 2 * c.Np,
@@ -494,6 +498,9 @@ tdb_status setup_tensor(Ctx& c) {
     return TDB_OK;
 }
 
+// tile width of the X product (128: measured faster than 64-wide tiles for every scheme)
+int xbn(const Ctx&) { return 128; }
+
 tdb_status build_maps(Ctx& c) {
     CK(tc::prepare());
     const int N = c.N, Np = c.Np, b = piece_bf16(c);
@@ -502,8 +509,8 @@ tdb_status build_maps(Ctx& c) {
         ok = ok && tc::make_map(&c.maps_dm.a[q], c.pc_sinv[q], N, N, Np, b) &&
              tc::make_map(&c.maps_dm.b[0][q], c.pc_dh[q], N, N, Np, b, 64) &&
              tc::make_map(&c.maps_x.a[q], c.pc_am[q], N, 2 * Np, 2 * Np, b) &&
-             tc::make_map(&c.maps_x.b[0][q], c.pc_bre[q], N, 2 * Np, 2 * Np, b) &&
-             tc::make_map(&c.maps_x.b[1][q], c.pc_bim[q], N, Np, Np, b);
+             tc::make_map(&c.maps_x.b[0][q], c.pc_bre[q], N, 2 * Np, 2 * Np, b, xbn(c)) &&
+             tc::make_map(&c.maps_x.b[1][q], c.pc_bim[q], N, Np, Np, b, xbn(c));
     }
     if (!ok) {
         set_err("cuTensorMapEncodeTiled failed");
@@ -604,10 +611,8 @@ tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* t
     const double* bim = euler ? c.rho_im[cur] : c.rho_im[prv];
     int n = 0;
     MARK("charges");
-    if (head3(c))
-        launch_charges(c, c.partial, c.q, c.dq, c.stream, &c.dyn->max_dv, &c.dyn->max_drho[prv]);
-    else
-        launch_charges(c, c.partial, c.q, c.dq, c.stream);
+    launch_charges(c, c.partial, c.q, c.dq, c.stream, nullptr, nullptr, head3(c) ? c.dyn : nullptr,
+                   cur);
     ++n;
     MARK("potential");
     launch_potential(c, c.gamma, c.dq, c.d_R, c.sc, c.v_orb, c.v_atom, c.gdq, c.hist, c.v_ref,
@@ -654,9 +659,10 @@ tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* t
         tc::GemmParams x{};
         x.M = N;
         x.N = N;
-        x.idesc = tc::idesc_f16(b, 128);
+        x.idesc = tc::idesc_f16(b, xbn(c));
         x.bf16 = b;
         x.err = c.d_err;
+        x.max_out = h3 ? c.dyn->max_x : nullptr;
         int nparts;
         if (h3) {
             // X_a = dM rho_ref, X_re = M Re(rho - rho_ref), X_im = M Im(rho): each K = N
@@ -671,7 +677,7 @@ tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* t
             nparts = 2;
         }
         MARK("tc_gemm_X");
-        CK(tc::launch(c.scheme, c.maps_x, x, nparts, c.stream));
+        CK(tc::launch(c.scheme, c.maps_x, x, nparts, c.stream, xbn(c)));
         ++n;
         UpdateOperands ops;
         ops.rho_ref = c.rho_ref;
@@ -679,8 +685,17 @@ tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* t
         ops.bf16 = b;
         ops.cur = cur;
         if (h3) {
-            ops.dyn = c.dyn;          // tracks max |rho_{n+1} - rho_ref|; pieces come after
+            // the update writes the head pieces of rho_{n+1} - rho_ref itself, scaled from a
+            // bound on their size, and tracks their maximum
+            ops.dyn = c.dyn;
+            ops.base_slot = euler ? cur : prv;
             ops.Xre2 = c.Xa_f;
+            for (int q = 0; q < 3; ++q) {
+                ops.re[q] = c.pc_bre[q] + Np;
+                ops.im[q] = c.pc_bim[q];
+            }
+            ops.ld_re = 2 * Np;
+            ops.ld_im = Np;
         } else {
             ops.re[0] = c.pc_bre[0] + Np;
             ops.re[1] = c.pc_bre[1] + Np;
@@ -694,11 +709,6 @@ tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* t
         launch_update_f32(c, c.Xre_f, c.Xim_f, bre, bim, c.rho_re[prv], c.rho_im[prv], factor,
                           c.S, c.partial, c.sc, ops, c.stream);
         ++n;
-        if (h3) {
-            MARK("split_rho");
-            launch_split_rho(c, prv, c.rho_re[prv], c.rho_im[prv], c.stream);
-            ++n;
-        }
     } else {
         const int N = c.N;
         // delta M = S^-1 delta H (left half of [dM | M]), M = M_gs + delta M (right half)

@@ -143,7 +143,8 @@ void launch_mulliken_partials(int N, const double* rho_re, const double* S, doub
                               cudaStream_t st);
 // reset0/reset1 (may be null): device doubles zeroed by the kernel
 void launch_charges(const Ctx& c, const double* partial, double* q, double* dq, cudaStream_t st,
-                    double* reset0 = nullptr, double* reset1 = nullptr);
+                    double* reset0 = nullptr, double* reset1 = nullptr,
+                    tc::DynScales* dyn = nullptr, int cur = 0);
 // max_dv (may be null): atomicMax of |v - v_ref| over atoms
 void launch_potential(const Ctx& c, const double* gamma, const double* dq, const double* R,
                       DevScalars* sc, double* v_orb, double* v_atom, double* gdq, double* hist,
@@ -151,6 +152,8 @@ void launch_potential(const Ctx& c, const double* gamma, const double* dq, const
                       double* max_dv = nullptr);
 void launch_build_hamiltonian(int N, const double* H0, const double* S, const double* v_orb,
                               double* H, cudaStream_t st);
+// charges + potential of a frozen-nuclei step in one launch (dyn: FP16X6 bookkeeping or null)
+void launch_charges_potential(const Ctx& c, tc::DynScales* dyn, int cur, cudaStream_t st);
 void launch_update(const Ctx& c, const double* Xre, const double* Xim, const double* base_re,
                    const double* base_im, double* out_re, double* out_im, double factor,
                    const double* S, double* partial, DevScalars* sc, cudaStream_t st,
@@ -170,6 +173,7 @@ struct UpdateOperands {
     const float* Xre2 = nullptr;       // added to X_re when set
     const double* zre = nullptr;       // NAC term Z = S^-1 D rho (moving nuclei, FP64 form)
     const double* zim = nullptr;
+    int base_slot = 0;                 // FP16X6: buffer whose max bounds the update's base
 };
 void launch_update_f32(const Ctx& c, const float* Xre, const float* Xim, const double* base_re,
                        const double* base_im, double* out_re, double* out_im, double factor,

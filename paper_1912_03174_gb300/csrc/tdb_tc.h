@@ -33,6 +33,7 @@ struct GemmPart {
 struct GemmParams {
     int M, N;
     GemmPart part[3];
+    double* max_out;   // mode 0: atomicMax of |C| per part into max_out[part] (may be null)
     uint32_t idesc;
     int bf16;
     // mode 1 (delta M): writes the pieces of s_dm dM at column j and of s_m (Mgs + dM) at
@@ -75,8 +76,9 @@ void launch_split(int scheme, int rows, int cols, const double* in, int ld_in, f
 // and s_dm = pscale(||S^-1||_inf max|dv|) are stored in dyn->s_dh / dyn->s_dm.
 struct DynScales {
     double max_dv;        // max |v - v_ref| of this step (atomicMax on the bit pattern)
-    double max_drho[2];   // max |rho - rho_ref| per density buffer
+    double max_drho[3];   // max |rho - rho_ref| per density buffer; [2]: the one being written
     double sinv_norm;     // ||S^-1||_inf
+    double max_x[3];      // max |X| of the product outputs of this step (parts 0..2)
     float s_dh, s_dm, s_rho;
     int pad;
 };
