@@ -104,7 +104,7 @@ typedef struct {
     double scc_tol;            /* ground-state tolerance on max |dq_out - dq_in| */
     int scc_max_iter;
     double kT;                 /* ground-state electronic temperature (Ha); 0 = aufbau */
-    double scc_mix;            /* Anderson mixing parameter of the ground state (0, 1] */
+    double scc_mix;            /* Anderson mixing parameter of the ground state (0, 1], 0.3 */
     long history_cap;          /* dipole ring-buffer length (steps), >= 1 */
     void* cuda_stream;         /* cudaStream_t, or NULL */
 } tdb_params;
@@ -134,7 +134,7 @@ typedef struct {
 } tdb_obs;
 
 /* Default parameters (dt 0.2, scc 1, frozen nuclei, FP64, window 100,
- * scc_tol 1e-12, 400 iterations, kT 0, mix 0.1, history 65536, stream NULL). */
+ * scc_tol 1e-12, 400 iterations, kT 0, mix 0.3, history 65536, stream NULL). */
 void tdb_default_params(tdb_params* out);
 
 /* Device bytes a context needs for this system and these parameters. */
@@ -149,7 +149,10 @@ tdb_status tdb_create(const tdb_system* sys, const tdb_params* prm, void* worksp
 
 /* Ground state (Sec. 2.1: cycles of diagonalisation and Hamiltonian build to
  * self-consistency): rho_0 = C f C^T of H C = S C eps, charges mixed until
- * max |dq_out - dq_in| <= scc_tol.  Resets t = 0, n = 0, next step Euler. */
+ * max |dq_out - dq_in| <= scc_tol.  The charge residual is preconditioned with a
+ * constant-density-of-states response model (1 - chi gamma)^-1 before Anderson
+ * mixing (scc_mix), which keeps large metallic clusters from charge sloshing.
+ * Resets t = 0, n = 0, next step Euler. */
 tdb_status tdb_ground_state(tdb_ctx* ctx, int* iters_out, double* residual_out);
 
 /* Delta kick of eq:rhokick applied to the current rho (and to the previous
@@ -192,7 +195,8 @@ long tdb_last_launch_count(const tdb_ctx* ctx);
 /* Advance one step like tdb_step(ctx, 1) but without the captured graph, with a
  * CUDA event recorded on the context stream before each kernel; synchronises.
  * ms[i] = device time of kernel i (milliseconds), names[i] = a static string
- * naming it (names may be NULL); *n_out = kernels timed (<= cap). */
+ * naming it (names may be NULL); *n_out = kernels timed (<= cap).  With moving
+ * nuclei the whole Ehrenfest step is one entry ("ehrenfest_step"). */
 tdb_status tdb_step_profiled(tdb_ctx* ctx, double* ms, const char** names, int cap, int* n_out);
 
 /* C = A B through the tensor-core split-precision GEMM on its own, for
@@ -202,7 +206,8 @@ tdb_status tdb_step_profiled(tdb_ctx* ctx, double* ms, const char** names, int c
  *        A_hi B_hi + A_hi B_lo + A_lo B_hi in one FP32 accumulator (tcgen05, TMEM);
  * fmt 1: the same with BF16 pieces (~16 bits);
  * fmt 2: 7-bit integer head + two FP16 tails (~29 bits); head products summed
- *        exactly in one accumulator (K <= 1024), five tail products in another.
+ *        exactly, one accumulator per 1024 of K (K <= 3072, else TDB_ERR_ARG),
+ *        five tail products in another.
  * ms (may be NULL): kernel time.
  * TDB_ERR_TIMEOUT if a bounded device wait expired. */
 tdb_status tdb_split_gemm(int M, int N, int K, const double* A, const double* B, int fmt, double* C,

@@ -340,10 +340,34 @@ class GroundState:
     residual: float
 
 
+# Electronic temperature floor of the charge-response estimate in the SCC preconditioner.
+PRECOND_KT = 0.02
+
+
+def scc_preconditioned(sysm, eps, gamma, resid, kT):
+    """Charge-sloshing preconditioner of the SCC residual (the paper names no mixer;
+    the fixed point does not depend on it).
+
+    A potential change dv moves the charges by about chi dv; model chi as a constant
+    density of states per atom at the Fermi level, c, acting on the charge-neutral
+    subspace: chi = -c (1 - 11^T / n_atoms).  One Newton step of the charge cycle,
+    dq_out = dq_in + chi gamma dq_in, is then x = (1 - chi gamma)^-1 resid.  c is
+    the Fermi-function derivative summed over the levels, at an electronic
+    temperature of at least PRECOND_KT so that a gap at the Fermi level does not
+    switch it off."""
+    nat = sysm.n_atoms
+    ke = max(kT, PRECOND_KT)
+    f = fermi_occupations(eps, sysm.n_electrons, ke)
+    c = float(np.sum(f * (1.0 - f / 2.0) / ke)) / nat
+    chi = -c * (np.eye(nat) - np.full((nat, nat), 1.0 / nat))
+    return np.linalg.solve(np.eye(nat) - chi @ gamma, resid)
+
+
 def ground_state(sysm, S, H0, gamma, R, scc, E_static=None, tol=1e-12, max_iter=400,
-                 mix=0.1, history=8, kT=0.0):
-    """SCC ground state.  Anderson mixing of the charge fluctuations (the paper
-    names no mixer; the fixed point does not depend on it)."""
+                 mix=0.3, history=8, kT=0.0):
+    """SCC ground state: Anderson mixing of the preconditioned charge residual
+    (scc_preconditioned; the paper names no mixer, and the fixed point does not
+    depend on it)."""
     q0 = reference_populations(sysm)
     E = np.zeros(3) if E_static is None else np.asarray(E_static, dtype=np.float64)
     dq = np.zeros(sysm.n_atoms)
@@ -361,16 +385,17 @@ def ground_state(sysm, S, H0, gamma, R, scc, E_static=None, tol=1e-12, max_iter=
         res = float(np.max(np.abs(resid))) if scc else 0.0
         if not scc or res <= tol:
             return GroundState(rho, eps, C, f, q, dq_out, it, res)
+        pres = scc_preconditioned(sysm, eps, gamma, resid, kT)
         xs.append(dq.copy())
-        fs.append(resid.copy())
+        fs.append(pres.copy())
         xs, fs = xs[-history:], fs[-history:]
         if len(xs) > 1:
             dX = np.array([xs[i + 1] - xs[i] for i in range(len(xs) - 1)]).T
             dF = np.array([fs[i + 1] - fs[i] for i in range(len(fs) - 1)]).T
-            g, *_ = np.linalg.lstsq(dF, resid, rcond=None)
-            dq = dq + mix * resid - (dX + mix * dF) @ g
+            g, *_ = np.linalg.lstsq(dF, pres, rcond=None)
+            dq = dq + mix * pres - (dX + mix * dF) @ g
         else:
-            dq = dq + mix * resid
+            dq = dq + mix * pres
     raise RuntimeError(f"SCC not converged: residual {res}")
 
 

@@ -38,8 +38,8 @@ struct DeltaHamF {
 // thread-grid size, so shared-memory reads of a warp are conflict-free.
 template <typename T, int BM, int BN, int BK, int TM, int TN, class LA, class LB>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
-    k_gemm(int M, int Ncol, int K, LA la, LB lb, T* __restrict__ C, int ldc,
-           const T* __restrict__ Cadd) {
+    k_gemm(int M, int Ncol, int K, LA la, LB lb, T* C, int ldc,
+           const T* Cadd) {
     constexpr int TX = BN / TN, TY = BM / TM, NT = TX * TY;
     __shared__ T As[BK][BM + 1];
     __shared__ T Bs[BK][BN];
@@ -135,7 +135,7 @@ void gemm_f32_dham(int N, const float* A, const float* S, const float* dv, float
     run_f32(N, N, N, Dense<float>{A, N}, DeltaHamF{S, dv, N}, C, ldc, Cadd, st);
 }
 
-// C = A * B + Cadd (FP32)
+// C = A * B + Cadd (FP32; Cadd may be C itself)
 void gemm_f32_add(int M, int Ncol, int K, const float* A, int lda, const float* B, int ldb,
                   float* C, int ldc, const float* Cadd, cudaStream_t st) {
     run_f32(M, Ncol, K, Dense<float>{A, lda}, Dense<float>{B, ldb}, C, ldc, Cadd, st);

@@ -198,7 +198,8 @@ __global__ void k_mulliken_partials(int N, int nct, const double* __restrict__ r
 __global__ void k_charges(int nat, int nper, int nct, const double* __restrict__ partial,
                           const double* __restrict__ q0, double* __restrict__ q,
                           double* __restrict__ dq, double* reset0, double* reset1,
-                          tc::DynScales* __restrict__ dyn, int cur) {
+                          tc::DynScales* __restrict__ dyn, int cur,
+                          const double* __restrict__ qbase) {
     const int lane = threadIdx.x & 31;
     const int A = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -209,7 +210,7 @@ __global__ void k_charges(int nat, int nper, int nct, const double* __restrict__
             // previous update now describes buffer cur; start this step's maxima
             dyn->max_drho[cur] = dyn->max_drho[2];
             dyn->max_drho[2] = 0.0;
-            dyn->max_x[0] = dyn->max_x[1] = dyn->max_x[2] = 0.0;
+            for (int k = 0; k < tc::kMaxParts; ++k) dyn->max_x[k] = 0.0;
         }
     }
     if (A >= nat) return;
@@ -218,6 +219,7 @@ __global__ void k_charges(int nat, int nper, int nct, const double* __restrict__
     for (int i = lane; i < nper * nct; i += 32) s += p[i];
     s = warp_sum(s);
     if (lane == 0) {
+        if (qbase) s += qbase[A];   // partials of the deviation rho - rho_ref
         q[A] = s;
         dq[A] = s - q0[A];
     }
@@ -302,121 +304,6 @@ __global__ void k_potential(int nat, int nper, int scc, const double* __restrict
     }
 }
 
-// Charges and SCC potential in one launch (frozen-nuclei steps).  Every block first
-// sums the Mulliken row partials of all atoms into shared memory (they are small and
-// L2-resident), then each warp forms v_A = [scc] sum_B gamma_AB dq_B + R_A . E(t_n) for
-// its atoms.  Block 0 writes q, dq, the dipole and E(t_n), and does the FP16X6 scale
-// bookkeeping of this step (dyn may be null).
-__global__ void k_charges_potential(int nat, int nper, int nct, int scc,
-                                    const double* __restrict__ partial,
-                                    const double* __restrict__ q0,
-                                    const double* __restrict__ gamma, const double* __restrict__ R,
-                                    DevScalars* __restrict__ sc, double* __restrict__ q,
-                                    double* __restrict__ dq, double* __restrict__ v_orb,
-                                    double* __restrict__ v_atom, double* __restrict__ gdq,
-                                    double* __restrict__ hist, const double* __restrict__ v_ref,
-                                    float* __restrict__ dv_f, tc::DynScales* __restrict__ dyn,
-                                    int cur) {
-    extern __shared__ double dq_s[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarp = blockDim.x >> 5;
-    if (dyn && blockIdx.x == 0 && threadIdx.x == 0) {
-        // the maximum of the deviation written by the previous update now describes
-        // buffer cur; start the maxima of this step
-        dyn->max_drho[cur] = dyn->max_drho[2];
-        dyn->max_drho[2] = 0.0;
-        dyn->max_x[0] = dyn->max_x[1] = dyn->max_x[2] = 0.0;
-    }
-    // charges of all atoms: each warp reduces groups of 8 atoms, issuing the loads of the
-    // whole group before the reductions so they overlap
-    const int L = nper * nct;
-    for (int B0 = warp * 8; B0 < nat; B0 += nwarp * 8) {
-        double s[8];
-#pragma unroll
-        for (int a = 0; a < 8; ++a) {
-            s[a] = 0.0;
-            if (B0 + a < nat) {
-                const double* p = partial + (size_t)(B0 + a) * L;
-                for (int i = lane; i < L; i += 32) s[a] += p[i];
-            }
-        }
-#pragma unroll
-        for (int a = 0; a < 8; ++a) {
-            const double t = warp_sum(s[a]);
-            if (lane == 0 && B0 + a < nat) dq_s[B0 + a] = t - q0[B0 + a];
-        }
-    }
-    __syncthreads();
-    const long long n = sc->step;
-    const double t = sc->t_base + (double)(n - sc->n_base) * sc->dt;
-    double E[3];
-    field_at(sc->field, t, E);
-    for (int A = blockIdx.x * nwarp + warp; A < nat; A += gridDim.x * nwarp) {
-        double s = 0.0;
-        if (scc)
-            for (int B = lane; B < nat; B += 32) s += gamma[(size_t)A * nat + B] * dq_s[B];
-        s = warp_sum(s);
-        const double vA = s + R[3 * A] * E[0] + R[3 * A + 1] * E[1] + R[3 * A + 2] * E[2];
-        if (lane < nper) {
-            const int o = A * nper + lane;
-            v_orb[o] = vA;
-            if (dv_f) dv_f[o] = (float)(vA - v_ref[o]);
-        }
-        if (lane == 0) {
-            v_atom[A] = vA;
-            gdq[A] = s;
-            if (dyn)
-                atomicMax(reinterpret_cast<unsigned long long*>(&dyn->max_dv),
-                          (unsigned long long)__double_as_longlong(fabs(vA - v_ref[A * nper])));
-        }
-    }
-    if (blockIdx.x == 0) {
-        __shared__ double red[4][32];
-        double m0 = 0, m1 = 0, m2 = 0, ee = 0;
-        for (int A = threadIdx.x; A < nat; A += blockDim.x) {
-            const double d = dq_s[A];
-            q[A] = d + q0[A];
-            dq[A] = d;
-            m0 -= d * R[3 * A];
-            m1 -= d * R[3 * A + 1];
-            m2 -= d * R[3 * A + 2];
-            ee += d * (R[3 * A] * E[0] + R[3 * A + 1] * E[1] + R[3 * A + 2] * E[2]);
-        }
-        m0 = warp_sum(m0);
-        m1 = warp_sum(m1);
-        m2 = warp_sum(m2);
-        ee = warp_sum(ee);
-        if (lane == 0) {
-            red[0][warp] = m0;
-            red[1][warp] = m1;
-            red[2][warp] = m2;
-            red[3][warp] = ee;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double a = 0, b = 0, c = 0, e = 0;
-            for (int w = 0; w < nwarp; ++w) {
-                a += red[0][w];
-                b += red[1][w];
-                c += red[2][w];
-                e += red[3][w];
-            }
-            sc->mu[0] = a;
-            sc->mu[1] = b;
-            sc->mu[2] = c;
-            sc->e_ext = e;
-            sc->E[0] = E[0];
-            sc->E[1] = E[1];
-            sc->E[2] = E[2];
-            const long long slot = n % sc->hist_cap;
-            const long long s2 = slot < 0 ? slot + sc->hist_cap : slot;
-            hist[3 * s2] = a;
-            hist[3 * s2 + 1] = b;
-            hist[3 * s2 + 2] = c;
-        }
-    }
-}
-
 __global__ void k_build_hamiltonian(int N, const double* __restrict__ H0,
                                     const double* __restrict__ S, const double* __restrict__ v,
                                     double* __restrict__ H) {
@@ -427,48 +314,34 @@ __global__ void k_build_hamiltonian(int N, const double* __restrict__ H0,
     H[i] = H0[i] + 0.5 * S[i] * (v[r] + v[c]);
 }
 
-// Leapfrog / Euler update (eq:leapfrog with eq:eomrho, frozen nuclei):
-//   out = base + factor * rhodot,  rhodot = -i (X - X^dagger),  X = S^-1 H rho.
+// Leapfrog / Euler update of the FP64 form (eq:leapfrog with eq:eomrho):
+//   out = base + factor * rhodot,  rhodot = -i (X - X^dagger) - (Z + Z^dagger),
+//   X = S^-1 H rho, Z = S^-1 D rho (moving nuclei only).
 // Re rhodot_ij = Im X_ij + Im X_ji;  Im rhodot_ij = -(Re X_ij - Re X_ji).
 // A block (32 x 8 threads) owns the tile pair (bi, bj), bi <= bj, so both halves
 // come out of the same operands and rho stays exactly Hermitian.  The Mulliken
-// row partials of the new rho are fused in.  T is the type of X.
-template <typename T>
+// row partials of the new rho are fused in.
 __global__ void __launch_bounds__(256)
-    k_update(int N, int nct, const T* __restrict__ Xre, const T* __restrict__ Xim,
+    k_update(int N, int nct, const double* __restrict__ Xre, const double* __restrict__ Xim,
              const double* __restrict__ bre, const double* __restrict__ bim,
              double* __restrict__ ore, double* __restrict__ oim, double factor,
              const double* __restrict__ S, double* __restrict__ partial,
-             DevScalars* __restrict__ sc, UpdateOperands ops) {
+             DevScalars* __restrict__ sc, const double* __restrict__ zre,
+             const double* __restrict__ zim) {
     const int bi = blockIdx.y, bj = blockIdx.x;
     if (bi > bj) return;
     constexpr int RPT = kTile / 8;   // rows per thread
-    double op_scale = ops.scale;
-    if (ops.dyn) {
-        // rigorous bound on |rho_{n+1} - rho_ref|: |base| + factor 2 max|X| (Re rhodot uses
-        // Im X twice, Im rhodot uses Re X = X_a + X_re twice); one thread per block
-        // evaluates it (FP64 frexp/ldexp are slow here)
-        __shared__ float s_bound;
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
-            const tc::DynScales* d = ops.dyn;
-            const double xm = fmax(d->max_x[2], d->max_x[0] + d->max_x[1]);
-            s_bound = tc::pscale(d->max_drho[ops.base_slot] + fabs(factor) * 2.0 * xm);
-        }
-        __syncthreads();
-        op_scale = (double)s_bound;
-    }
-    __shared__ T xr_ij[kTile][kTile + 1], xi_ij[kTile][kTile + 1];
-    __shared__ T xr_ji[kTile][kTile + 1], xi_ji[kTile][kTile + 1];
+    __shared__ double xr_ij[kTile][kTile + 1], xi_ij[kTile][kTile + 1];
+    __shared__ double xr_ji[kTile][kTile + 1], xi_ji[kTile][kTile + 1];
     const int tx = threadIdx.x, ty = threadIdx.y;
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
         const int y = ty + 8 * k;
         int r = bi * kTile + y, c = bj * kTile + tx;
-        T a = 0, b = 0;
+        double a = 0, b = 0;
         if (r < N && c < N) {
             const size_t i = (size_t)r * N + c;
             a = Xre[i];
-            if (ops.Xre2) a += ops.Xre2[i];
             b = Xim[i];
         }
         xr_ij[y][tx] = a;
@@ -480,28 +353,25 @@ __global__ void __launch_bounds__(256)
         if (r < N && c < N) {
             const size_t i = (size_t)r * N + c;
             a = Xre[i];
-            if (ops.Xre2) a += ops.Xre2[i];
             b = Xim[i];
         }
         xr_ji[y][tx] = a;
         xi_ji[y][tx] = b;
     }
     __syncthreads();
-    float dmax = 0.f;   // max |rho_{n+1} - rho_ref| of this block (FP16X6 scale tracking)
     __shared__ double pv_s[kTile][kTile + 1];
     for (int half = 0; half < (bi == bj ? 1 : 2); ++half) {
         const int ti = half ? bj : bi, tj = half ? bi : bj;
-        double b_re[RPT], b_im[RPT], s_v[RPT], r_v[RPT];
+        double b_re[RPT], b_im[RPT], s_v[RPT];
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
             const int r = ti * kTile + ty + 8 * k, c = tj * kTile + tx;
-            b_re[k] = b_im[k] = s_v[k] = r_v[k] = 0.0;
+            b_re[k] = b_im[k] = s_v[k] = 0.0;
             if (r < N && c < N) {
                 const size_t i = (size_t)r * N + c;
                 b_re[k] = bre[i];
                 b_im[k] = bim[i];
                 s_v[k] = S[i];
-                if (ops.rho_ref) r_v[k] = ops.rho_ref[i];
             }
         }
 #pragma unroll
@@ -510,7 +380,7 @@ __global__ void __launch_bounds__(256)
             const int r = ti * kTile + y, c = tj * kTile + tx;
             double pv = 0.0;
             if (r < N && c < N) {
-                T x_ij_re, x_ij_im, x_ji_re, x_ji_im;
+                double x_ij_re, x_ij_im, x_ji_re, x_ji_im;
                 if (!half) {
                     x_ij_re = xr_ij[y][tx];
                     x_ij_im = xi_ij[y][tx];
@@ -522,62 +392,20 @@ __global__ void __launch_bounds__(256)
                     x_ji_re = xr_ij[tx][y];
                     x_ji_im = xi_ij[tx][y];
                 }
-                // in the precision of X (exactly Hermitian either way: the (j,i) element
-                // repeats these operations on the swapped operands)
-                double dre = (double)(x_ij_im + x_ji_im);
-                double dim = (double)(-(x_ij_re - x_ji_re));
+                // the (j,i) element repeats these operations on the swapped operands
+                double dre = x_ij_im + x_ji_im;
+                double dim = -(x_ij_re - x_ji_re);
                 const size_t i = (size_t)r * N + c;
-                if (ops.zre) {
-                    // - (Z + Z^dagger), Z = S^-1 D rho (eq:eomrho, moving nuclei)
+                if (zre) {
                     const size_t j = (size_t)c * N + r;
-                    dre -= ops.zre[i] + ops.zre[j];
-                    dim -= ops.zim[i] - ops.zim[j];
+                    dre -= zre[i] + zre[j];
+                    dim -= zim[i] - zim[j];
                 }
                 const double nre = b_re[k] + factor * dre;
                 const double nim = b_im[k] + factor * dim;
                 ore[i] = nre;
                 oim[i] = nim;
                 pv = nre * s_v[k];
-                if (ops.rho_ref) {
-                    const double d_re = nre - r_v[k];
-                    if (ops.dyn) {
-                        const float fre = (float)d_re, fim = (float)nim;
-                        dmax = fmaxf(dmax, fmaxf(fabsf(fre), fabsf(fim)));
-                        if (ops.re[2]) {
-                            // FP16X6 operands: head + two tails of the scaled deviation
-                            const float fs = (float)op_scale;
-                            uint16_t q[3];
-                            const size_t jr = (size_t)r * ops.ld_re + c;
-                            const size_t ji = (size_t)r * ops.ld_im + c;
-                            split_head3(fre * fs, q);
-                            ops.re[0][jr] = q[0];
-                            ops.re[1][jr] = q[1];
-                            ops.re[2][jr] = q[2];
-                            split_head3(-fim * fs, q);
-                            ops.im[0][ji] = q[0];
-                            ops.im[1][ji] = q[1];
-                            ops.im[2][ji] = q[2];
-                        }
-                    }
-                    if (ops.f_re) {
-                        ops.f_re[i] = (float)d_re;
-                        ops.f_im[i] = (float)nim;
-                    }
-                    if (ops.re[0] && !ops.re[2]) {
-                        // operands of the tensor-core products are K-major: Re rho is
-                        // symmetric, and the transpose of Im rho is -Im rho
-                        const size_t jr = (size_t)r * ops.ld_re + c;
-                        const size_t ji = (size_t)r * ops.ld_im + c;
-                        const float x = (float)(d_re * ops.scale);
-                        const uint16_t h1 = to16(x, ops.bf16);
-                        ops.re[0][jr] = h1;
-                        ops.re[1][jr] = to16(x - from16(h1, ops.bf16), ops.bf16);
-                        const float yv = (float)(-nim * ops.scale);
-                        const uint16_t h2 = to16(yv, ops.bf16);
-                        ops.im[0][ji] = h2;
-                        ops.im[1][ji] = to16(yv - from16(h2, ops.bf16), ops.bf16);
-                    }
-                }
             }
             pv_s[y][tx] = pv;
         }
@@ -591,16 +419,6 @@ __global__ void __launch_bounds__(256)
             if (r < N) partial[(size_t)r * nct + tj] = sum;
         }
         __syncthreads();
-    }
-    if (ops.dyn) {
-        for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-        if (tx == 0)
-            atomicMax(reinterpret_cast<unsigned long long*>(&ops.dyn->max_drho[2]),
-                      (unsigned long long)__double_as_longlong((double)dmax));
-        if (bi == 0 && bj == 0 && tx == 0 && ty == 0) {
-            ops.dyn->s_rho = (float)op_scale;   // scale of the pieces just written
-            ops.dyn->max_dv = 0.0;              // the next step's potential accumulates anew
-        }
     }
     if (bi == 0 && bj == 0 && threadIdx.x == 0 && threadIdx.y == 0) sc->step += 1;
 }
@@ -741,9 +559,10 @@ void launch_mulliken_partials(int N, const double* rho_re, const double* S, doub
 }
 
 void launch_charges(const Ctx& c, const double* partial, double* q, double* dq, cudaStream_t st,
-                    double* reset0, double* reset1, tc::DynScales* dyn, int cur) {
+                    double* reset0, double* reset1, tc::DynScales* dyn, int cur,
+                    const double* qbase) {
     k_charges<<<(c.nat + 7) / 8, 256, 0, st>>>(c.nat, c.nper, c.nct, partial, c.d_q0, q, dq,
-                                               reset0, reset1, dyn, cur);
+                                               reset0, reset1, dyn, cur, qbase);
 }
 
 void launch_potential(const Ctx& c, const double* gamma, const double* dq, const double* R,
@@ -753,14 +572,6 @@ void launch_potential(const Ctx& c, const double* gamma, const double* dq, const
     const int blocks = (c.nat + warps - 1) / warps;
     k_potential<<<blocks, warps * 32, 0, st>>>(c.nat, c.nper, c.prm.scc, gamma, dq, R, sc, v_orb,
                                                v_atom, gdq, hist, v_ref, dv_orb, max_dv);
-}
-
-void launch_charges_potential(const Ctx& c, tc::DynScales* dyn, int cur, cudaStream_t st) {
-    const int warps = 8;
-    const int blocks = (c.nat + warps - 1) / warps;
-    k_charges_potential<<<blocks, warps * 32, sizeof(double) * c.nat, st>>>(
-        c.nat, c.nper, c.nct, c.prm.scc, c.partial, c.d_q0, c.gamma, c.d_R, c.sc, c.q, c.dq,
-        c.v_orb, c.v_atom, c.gdq, c.hist, c.v_ref, c.dv_f, dyn, cur);
 }
 
 void launch_build_hamiltonian(int N, const double* H0, const double* S, const double* v_orb,
@@ -774,20 +585,8 @@ void launch_update(const Ctx& c, const double* Xre, const double* Xim, const dou
                    const double* S, double* partial, DevScalars* sc, cudaStream_t st,
                    const double* zre, const double* zim) {
     dim3 b(kTile, 8);
-    UpdateOperands ops;
-    ops.zre = zre;
-    ops.zim = zim;
-    k_update<double><<<dim3(c.nct, c.nct), b, 0, st>>>(c.N, c.nct, Xre, Xim, base_re, base_im,
-                                                       out_re, out_im, factor, S, partial, sc, ops);
-}
-
-void launch_update_f32(const Ctx& c, const float* Xre, const float* Xim, const double* base_re,
-                       const double* base_im, double* out_re, double* out_im, double factor,
-                       const double* S, double* partial, DevScalars* sc,
-                       const UpdateOperands& ops, cudaStream_t st) {
-    dim3 b(kTile, 8);
-    k_update<float><<<dim3(c.nct, c.nct), b, 0, st>>>(c.N, c.nct, Xre, Xim, base_re, base_im,
-                                                      out_re, out_im, factor, S, partial, sc, ops);
+    k_update<<<dim3(c.nct, c.nct), b, 0, st>>>(c.N, c.nct, Xre, Xim, base_re, base_im, out_re,
+                                               out_im, factor, S, partial, sc, zre, zim);
 }
 
 void launch_kick_phase(int N, int n_per, const double* R, double strength, const double* dir,
@@ -830,12 +629,10 @@ __global__ void k_f64_to_f32(size_t n, const double* __restrict__ in, float* __r
         out[i] = (float)in[i];
 }
 
-// out = (float)(a - b), b may be null
-__global__ void k_sub_to_f32(size_t n, const double* __restrict__ a, const double* __restrict__ b,
-                             float* __restrict__ out) {
+__global__ void k_f32_to_f64(size_t n, const float* __restrict__ in, double* __restrict__ out) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x)
-        out[i] = (float)(b ? a[i] - b[i] : a[i]);
+        out[i] = (double)in[i];
 }
 
 // out[r][c] = a[r][c] + b[r][c] with row strides N (a), ldb (b), ldo (out)
@@ -903,59 +700,18 @@ __global__ void k_absmax(size_t n, const double* __restrict__ x, const double* _
         atomicMax(reinterpret_cast<unsigned long long*>(out), (unsigned long long)__double_as_longlong(m));
 }
 
-// FP16X6 operands of rho: pieces of s (Re rho - rho_ref) at column Np + c of the
-// [rho_ref | Re] block (row stride 2 Np) and of -s Im rho (row stride Np), with
-// s = pscale(max |rho - rho_ref|) from the maximum tracked by the update.
-__global__ void k_split_rho(int N, int Np, const double* __restrict__ rre,
-                            const double* __restrict__ rim, const double* __restrict__ rref,
-                            tc::DynScales* __restrict__ dyn, int slot, UpdateOperands ops) {
-    __shared__ float s_sh;
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        s_sh = tc::pscale(dyn->max_drho[slot]);
-        if (blockIdx.x == 0 && blockIdx.y == 0) dyn->s_rho = s_sh;
-    }
-    __syncthreads();
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    const int r = blockIdx.y * blockDim.y + threadIdx.y;
-    if (r >= N || c >= N) return;
-    const size_t i = (size_t)r * N + c;
-    uint16_t q[3];
-    const float fs = s_sh;
-    split_head3((float)(rre[i] - rref[i]) * fs, q);
-    const size_t jr = (size_t)r * 2 * Np + Np + c;
-    ops.re[0][jr] = q[0];
-    ops.re[1][jr] = q[1];
-    ops.re[2][jr] = q[2];
-    split_head3((float)(-rim[i]) * fs, q);
-    const size_t ji = (size_t)r * Np + c;
-    ops.im[0][ji] = q[0];
-    ops.im[1][ji] = q[1];
-    ops.im[2][ji] = q[2];
-}
-
 }  // namespace
-
-void launch_split_rho(const Ctx& c, int slot, const double* rre, const double* rim,
-                      cudaStream_t st) {
-    UpdateOperands o;
-    for (int k = 0; k < 3; ++k) {
-        o.re[k] = c.pc_bre[k];
-        o.im[k] = c.pc_bim[k];
-    }
-    dim3 b(32, 8);
-    k_split_rho<<<grid2(c.N, c.N, b), b, 0, st>>>(c.N, c.Np, rre, rim, c.rho_ref, c.dyn, slot, o);
-}
 
 void launch_absmax(size_t n, const double* x, double* out, cudaStream_t st, const double* sub) {
     k_absmax<<<608, 256, 0, st>>>(n, x, sub, out);
 }
 
-void launch_f64_to_f32(size_t n, const double* in, float* out, cudaStream_t st) {
-    k_f64_to_f32<<<1216, 256, 0, st>>>(n, in, out);
+void launch_f32_to_f64(size_t n, const float* in, double* out, cudaStream_t st) {
+    k_f32_to_f64<<<1216, 256, 0, st>>>(n, in, out);
 }
 
-void launch_sub_to_f32(size_t n, const double* a, const double* b, float* out, cudaStream_t st) {
-    k_sub_to_f32<<<1216, 256, 0, st>>>(n, a, b, out);
+void launch_f64_to_f32(size_t n, const double* in, float* out, cudaStream_t st) {
+    k_f64_to_f32<<<1216, 256, 0, st>>>(n, in, out);
 }
 
 void launch_add_f32_strided(int N, const float* a, const float* b, int ldb, float* out, int ldo,
@@ -967,6 +723,337 @@ void launch_add_f32_strided(int N, const float* a, const float* b, int ldb, floa
 void launch_small_energies(const Ctx& c, double* out, cudaStream_t st) {
     k_small_energies<<<1, 256, 0, st>>>(c.nat, c.dq, c.gdq, c.d_R, c.d_Vn, c.d_mass, c.mp.rep_A,
                                         c.mp.rep_b, c.prm.move_nuclei, out);
+}
+
+}  // namespace tdb
+
+// ---------------------------------------------------------------------------
+// Reduced-precision forms: the density master is rho - rho_ref held as an FP32
+// pair (hi + lo, ~48 bits) per element, so the per-step update runs without FP64
+// arithmetic (FP64 issues at 1/64 of the FP32 rate on this part).  The FP64
+// matrices rho_re / rho_im are a view, materialised for observables, kicks and
+// checkpoints.
+// ---------------------------------------------------------------------------
+
+namespace tdb {
+
+namespace {
+
+// s + e = a + b exactly (Knuth's two-sum)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// (hi, lo) += inc, renormalised
+__device__ __forceinline__ void df_add(float& hi, float& lo, float inc) {
+    float s, e;
+    two_sum(hi, inc, s, e);
+    e += lo;
+    hi = s + e;
+    lo = e - (hi - s);
+}
+
+// Update of the FP32-pair master (eq:leapfrog, eq:eomrho, frozen nuclei): the same
+// tile-pair scheme and operands as k_update, with the increment factor * rhodot formed
+// as fh * d + fl * d (factor = fh + fl) so the step length carries no FP32 rounding.
+// Mulliken row partials of the deviation: FP32 products with S, summed in FP64.
+__global__ void __launch_bounds__(256, 6)
+    k_update_df(int N, int nct, MasterPtrs base, MasterPtrs out, float fh, float fl,
+                double factor, const float* __restrict__ Sf, double* __restrict__ partial,
+                DevScalars* __restrict__ sc, UpdateOperands ops) {
+    // one block per tile pair bi <= bj: block b = bj (bj + 1) / 2 + bi
+    const int b = blockIdx.x;
+    int bj = (int)((sqrtf(8.0f * (float)b + 1.0f) - 1.0f) * 0.5f);
+    while (bj * (bj + 1) / 2 > b) --bj;
+    while ((bj + 1) * (bj + 2) / 2 <= b) ++bj;
+    const int bi = b - bj * (bj + 1) / 2;
+    constexpr int RPT = kTile / 8;
+    float op_scale = ops.scale;
+    if (ops.dyn) {
+        __shared__ float s_bound;
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            // |X| <= the sum of the maxima of its partial products
+            const tc::DynScales* d = ops.dyn;
+            double mre = 0.0, mim = 0.0;
+            for (int q = 0; q < ops.nre; ++q) mre += d->max_x[q];
+            for (int q = 0; q < ops.nim; ++q) mim += d->max_x[ops.nre + q];
+            s_bound = tc::pscale(d->max_drho[ops.base_slot] + fabs(factor) * 2.0 * fmax(mre, mim));
+        }
+        __syncthreads();
+        op_scale = s_bound;
+    }
+    __shared__ float xr_ij[kTile][kTile + 1], xi_ij[kTile][kTile + 1];
+    __shared__ float xr_ji[kTile][kTile + 1], xi_ji[kTile][kTile + 1];
+    __shared__ double pv_s[kTile][kTile + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    // X = sum of its partial products, in a fixed order (all loads issued first)
+    auto load_x = [&](size_t i, float& a, float& b) {
+        float t[6];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) t[q] = q < ops.nre ? ops.xre[q][i] : 0.f;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) t[4 + q] = q < ops.nim ? ops.xim[q][i] : 0.f;
+        a = ((t[0] + t[1]) + t[2]) + t[3];
+        b = t[4] + t[5];
+    };
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int y = ty + 8 * k;
+        int r = bi * kTile + y, c = bj * kTile + tx;
+        float a = 0.f, b = 0.f;
+        if (r < N && c < N) load_x((size_t)r * N + c, a, b);
+        xr_ij[y][tx] = a;
+        xi_ij[y][tx] = b;
+        r = bj * kTile + y;
+        c = bi * kTile + tx;
+        a = b = 0.f;
+        if (r < N && c < N) load_x((size_t)r * N + c, a, b);
+        xr_ji[y][tx] = a;
+        xi_ji[y][tx] = b;
+    }
+    __syncthreads();
+    float dmax = 0.f;
+    for (int half = 0; half < (bi == bj ? 1 : 2); ++half) {
+        const int ti = half ? bj : bi, tj = half ? bi : bj;
+        float brh[RPT], brl[RPT], bih[RPT], bil[RPT], sv[RPT];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int r = ti * kTile + ty + 8 * k, c = tj * kTile + tx;
+            brh[k] = brl[k] = bih[k] = bil[k] = sv[k] = 0.f;
+            if (r < N && c < N) {
+                const size_t i = (size_t)r * N + c;
+                brh[k] = base.re_hi[i];
+                brl[k] = base.re_lo[i];
+                bih[k] = base.im_hi[i];
+                bil[k] = base.im_lo[i];
+                sv[k] = Sf[i];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int y = ty + 8 * k;
+            const int r = ti * kTile + y, c = tj * kTile + tx;
+            double pv = 0.0;
+            if (r < N && c < N) {
+                float x_ij_re, x_ij_im, x_ji_re, x_ji_im;
+                if (!half) {
+                    x_ij_re = xr_ij[y][tx];
+                    x_ij_im = xi_ij[y][tx];
+                    x_ji_re = xr_ji[tx][y];
+                    x_ji_im = xi_ji[tx][y];
+                } else {
+                    x_ij_re = xr_ji[y][tx];
+                    x_ij_im = xi_ji[y][tx];
+                    x_ji_re = xr_ij[tx][y];
+                    x_ji_im = xi_ij[tx][y];
+                }
+                // rhodot = -i (X - X^dagger); the (j,i) element repeats these operations on
+                // the swapped operands, so the master stays exactly Hermitian
+                const float dre = x_ij_im + x_ji_im;
+                const float dim = -(x_ij_re - x_ji_re);
+                const float ire = fmaf(fh, dre, fl * dre);
+                const float iim = fmaf(fh, dim, fl * dim);
+                float rh = brh[k], rl = brl[k], ih = bih[k], il = bil[k];
+                df_add(rh, rl, ire);
+                df_add(ih, il, iim);
+                const size_t i = (size_t)r * N + c;
+                out.re_hi[i] = rh;
+                out.re_lo[i] = rl;
+                out.im_hi[i] = ih;
+                out.im_lo[i] = il;
+                pv = (double)(rh * sv[k]);
+                if (ops.dyn) dmax = fmaxf(dmax, fmaxf(fabsf(rh), fabsf(ih)));
+                if (ops.re[0]) {
+                    // operands of the tensor-core products are K-major: Re rho is symmetric,
+                    // the transpose of Im rho is -Im rho
+                    const size_t jr = (size_t)r * ops.ld_re + c;
+                    const size_t ji = (size_t)r * ops.ld_im + c;
+                    if (ops.re[2]) {
+                        uint16_t q[3];
+                        split_head3(rh * op_scale, q);
+                        ops.re[0][jr] = q[0];
+                        ops.re[1][jr] = q[1];
+                        ops.re[2][jr] = q[2];
+                        split_head3(-ih * op_scale, q);
+                        ops.im[0][ji] = q[0];
+                        ops.im[1][ji] = q[1];
+                        ops.im[2][ji] = q[2];
+                    } else {
+                        const float xa = rh * op_scale;
+                        const uint16_t h1 = to16(xa, ops.bf16);
+                        ops.re[0][jr] = h1;
+                        ops.re[1][jr] = to16(xa - from16(h1, ops.bf16), ops.bf16);
+                        const float yb = -ih * op_scale;
+                        const uint16_t h2 = to16(yb, ops.bf16);
+                        ops.im[0][ji] = h2;
+                        ops.im[1][ji] = to16(yb - from16(h2, ops.bf16), ops.bf16);
+                    }
+                }
+            }
+            pv_s[y][tx] = pv;
+        }
+        __syncthreads();
+        if (ty == 0) {
+            const int r = ti * kTile + tx;
+            double sum = 0.0;
+#pragma unroll 8
+            for (int k = 0; k < kTile; ++k) sum += pv_s[tx][k];
+            if (r < N) partial[(size_t)r * nct + tj] = sum;
+        }
+        __syncthreads();
+    }
+    if (ops.dyn) {
+        for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        if (tx == 0)
+            atomicMax(reinterpret_cast<unsigned long long*>(&ops.dyn->max_drho[2]),
+                      (unsigned long long)__double_as_longlong((double)dmax));
+        if (bi == 0 && bj == 0 && tx == 0 && ty == 0) {
+            ops.dyn->s_rho = op_scale;
+            ops.dyn->max_dv = 0.0;
+        }
+    }
+    if (bi == 0 && bj == 0 && tx == 0 && ty == 0) sc->step += 1;
+}
+
+// master (hi, lo) of rho - rho_ref from the FP64 view
+__global__ void k_view_to_master(size_t n, const double* __restrict__ rre,
+                                 const double* __restrict__ rim, const double* __restrict__ ref,
+                                 MasterPtrs m) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const double d = rre[i] - ref[i];
+        const float h = (float)d;
+        m.re_hi[i] = h;
+        m.re_lo[i] = (float)(d - (double)h);
+        const double e = rim[i];
+        const float g = (float)e;
+        m.im_hi[i] = g;
+        m.im_lo[i] = (float)(e - (double)g);
+    }
+}
+
+// FP64 view rho = rho_ref + hi + lo from the master
+__global__ void k_master_to_view(size_t n, MasterPtrs m, const double* __restrict__ ref,
+                                 double* __restrict__ rre, double* __restrict__ rim) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        rre[i] = ref[i] + ((double)m.re_hi[i] + (double)m.re_lo[i]);
+        rim[i] = (double)m.im_hi[i] + (double)m.im_lo[i];
+    }
+}
+
+// Mulliken row partials of the deviation held by the master, with the arithmetic of
+// k_update_df (FP32 products, FP64 column-order sums)
+__global__ void k_master_partials(int N, int nct, MasterPtrs m, const float* __restrict__ Sf,
+                                  double* __restrict__ partial) {
+    __shared__ double pv_s[kTile][kTile + 1];
+    const int ct = blockIdx.x;
+    const int col = ct * kTile + threadIdx.x;
+    for (int y = threadIdx.y; y < kTile; y += blockDim.y) {
+        const int row = blockIdx.y * kTile + y;
+        double v = 0.0;
+        if (row < N && col < N) v = (double)(m.re_hi[(size_t)row * N + col] * Sf[(size_t)row * N + col]);
+        pv_s[y][threadIdx.x] = v;
+    }
+    __syncthreads();
+    if (threadIdx.y == 0) {
+        const int row = blockIdx.y * kTile + threadIdx.x;
+        double sum = 0.0;
+#pragma unroll 8
+        for (int k = 0; k < kTile; ++k) sum += pv_s[threadIdx.x][k];
+        if (row < N) partial[(size_t)row * nct + ct] = sum;
+    }
+}
+
+// max(|re_hi|, |im_hi|) into out (out must start at 0)
+__global__ void k_master_absmax(size_t n, MasterPtrs m, double* __restrict__ out) {
+    float mx = 0.f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        mx = fmaxf(mx, fmaxf(fabsf(m.re_hi[i]), fabsf(m.im_hi[i])));
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(reinterpret_cast<unsigned long long*>(out),
+                  (unsigned long long)__double_as_longlong((double)mx));
+}
+
+// operand pieces of the master deviation (the update's arithmetic); the scale is
+// pscale(*mx_exact) (FP16X6, exact maximum), else *dev_scale (FP16X6, restored), else
+// the constant ops.scale
+__global__ void k_master_pieces(int N, MasterPtrs m, UpdateOperands ops, const double* mx_exact,
+                                const float* dev_scale) {
+    __shared__ float s_sh;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        s_sh = mx_exact ? tc::pscale(*mx_exact) : dev_scale ? *dev_scale : ops.scale;
+        if (mx_exact && ops.dyn && blockIdx.x == 0 && blockIdx.y == 0) ops.dyn->s_rho = s_sh;
+    }
+    __syncthreads();
+    const float sc = s_sh;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    if (r >= N || c >= N) return;
+    const size_t i = (size_t)r * N + c;
+    const float rh = m.re_hi[i], ih = m.im_hi[i];
+    const size_t jr = (size_t)r * ops.ld_re + c;
+    const size_t ji = (size_t)r * ops.ld_im + c;
+    if (ops.re[2]) {
+        uint16_t q[3];
+        split_head3(rh * sc, q);
+        ops.re[0][jr] = q[0];
+        ops.re[1][jr] = q[1];
+        ops.re[2][jr] = q[2];
+        split_head3(-ih * sc, q);
+        ops.im[0][ji] = q[0];
+        ops.im[1][ji] = q[1];
+        ops.im[2][ji] = q[2];
+    } else {
+        const float xa = rh * sc;
+        const uint16_t h1 = to16(xa, ops.bf16);
+        ops.re[0][jr] = h1;
+        ops.re[1][jr] = to16(xa - from16(h1, ops.bf16), ops.bf16);
+        const float yb = -ih * sc;
+        const uint16_t h2 = to16(yb, ops.bf16);
+        ops.im[0][ji] = h2;
+        ops.im[1][ji] = to16(yb - from16(h2, ops.bf16), ops.bf16);
+    }
+}
+
+}  // namespace
+
+void launch_update_df(const Ctx& c, const MasterPtrs& base, const MasterPtrs& out, double factor,
+                      double* partial, DevScalars* sc, const UpdateOperands& ops, cudaStream_t st) {
+    const float fh = (float)factor;
+    const float fl = (float)(factor - (double)fh);
+    dim3 b(kTile, 8);
+    k_update_df<<<c.nct * (c.nct + 1) / 2, b, 0, st>>>(c.N, c.nct, base, out, fh, fl, factor,
+                                                        c.S_f, partial, sc, ops);
+}
+
+void launch_view_to_master(const Ctx& c, const double* rre, const double* rim, const MasterPtrs& m,
+                           cudaStream_t st) {
+    k_view_to_master<<<1216, 256, 0, st>>>((size_t)c.N * c.N, rre, rim, c.rho_ref, m);
+}
+
+void launch_master_to_view(const Ctx& c, const MasterPtrs& m, double* rre, double* rim,
+                           cudaStream_t st) {
+    k_master_to_view<<<1216, 256, 0, st>>>((size_t)c.N * c.N, m, c.rho_ref, rre, rim);
+}
+
+void launch_master_partials(const Ctx& c, const MasterPtrs& m, double* partial, cudaStream_t st) {
+    dim3 b(kTile, 8);
+    k_master_partials<<<dim3(c.nct, c.nct), b, 0, st>>>(c.N, c.nct, m, c.S_f, partial);
+}
+
+void launch_master_absmax(const Ctx& c, const MasterPtrs& m, double* out, cudaStream_t st) {
+    k_master_absmax<<<608, 256, 0, st>>>((size_t)c.N * c.N, m, out);
+}
+
+void launch_master_pieces(const Ctx& c, const MasterPtrs& m, const UpdateOperands& ops,
+                          const double* mx_exact, const float* dev_scale, cudaStream_t st) {
+    dim3 b(32, 8);
+    k_master_pieces<<<grid2(c.N, c.N, b), b, 0, st>>>(c.N, m, ops, mx_exact, dev_scale);
 }
 
 }  // namespace tdb

@@ -8,11 +8,13 @@
 // in their own accumulator and only the small tail products (~2^-7 of the
 // result) share the second, inexact one.
 //
-// Data path: TMA (cp.async.bulk.tensor, 128-byte swizzle) -> shared-memory
-// ring (mbarrier full/empty pairs) -> tcgen05.mma issued by one thread ->
-// TMEM accumulators (128 lanes x 128 columns each) -> tcgen05.ld -> epilogue
-// in registers -> global.  Both operands are K-major: A is M x K row-major
-// and B is given as its transpose Bt (N x K row-major).
+// Data path: TMA (cp.async.bulk.tensor, 64-byte swizzle, K blocks of 32) ->
+// shared-memory ring of up to 8 stages (mbarrier full/empty pairs) ->
+// tcgen05.mma issued by one thread -> TMEM accumulators (128 lanes x BN
+// columns each; kHead3 keeps one head accumulator per 1024 of K plus the tail
+// one) -> tcgen05.ld by all 8 warps -> epilogue in registers -> global.  Both
+// operands are K-major: A is M x K row-major and B is given as its transpose
+// Bt (N x K row-major).
 //
 // Every mbarrier wait is bounded; on time-out the kernel records an error
 // code, lets the issued MMAs drain, frees its TMEM and returns.
@@ -29,29 +31,45 @@ namespace tc {
 
 namespace {
 
-constexpr int BM = 128, BK = 64;
-constexpr int TILE_BYTES = BM * BK * 2;   // 16 KiB per A piece (B pieces: BN * BK * 2)
+// K blocks of 32 (64 bytes of 16-bit values, one 64-byte swizzle span): smaller stages,
+// so more of them fit and the TMA producer can run further ahead of the MMAs.
+constexpr int BM = 128, BK = 32;
+constexpr int TILE_BYTES = BM * BK * 2;   // 8 KiB per A piece (B pieces: BN * BK * 2)
 constexpr long long kSpinLimit = 1ll << 22;
+constexpr int kThreads = 256;             // 8 warps: all of them run the epilogue
+constexpr int kHeadKB = kHeadK / BK;      // K blocks per exact head accumulator
 
 template <int SCHEME>
 struct Cfg;
 template <>
 struct Cfg<kHiLo> {
-    static constexpr int PIECES = 2, ACCS = 1;
+    static constexpr int PIECES = 2;
 };
 template <>
 struct Cfg<kHead3> {
-    static constexpr int PIECES = 3, ACCS = 2;
+    static constexpr int PIECES = 3;
 };
+
+// Accumulators of a K-deep product: kHead3 one exact head accumulator per kHeadK slice
+// plus the tail accumulator; kHiLo one.
+__host__ __device__ inline int n_heads(int scheme, int K) {
+    return scheme == kHead3 ? (K + kHeadK - 1) / kHeadK : 0;
+}
+__host__ __device__ inline uint32_t tmem_cols(int scheme, int K, int bn) {
+    const uint32_t need = static_cast<uint32_t>((n_heads(scheme, K) + 1) * bn);
+    uint32_t cols = 32;
+    while (cols < need) cols <<= 1;
+    return cols;
+}
 template <int S, int BN>
 __host__ __device__ constexpr int stage_bytes() {
     return Cfg<S>::PIECES * (TILE_BYTES + BN * BK * 2);
 }
-// as many ring stages as fit in 227 KiB of shared memory (at most 4)
+// as many ring stages as fit in 227 KiB of shared memory (at most 8)
 template <int S, int BN>
 __host__ __device__ constexpr int stages() {
-    return (227 * 1024 - 1024 - 256) / stage_bytes<S, BN>() > 4
-               ? 4
+    return (227 * 1024 - 1024 - 256) / stage_bytes<S, BN>() > 8
+               ? 8
                : (227 * 1024 - 1024 - 256) / stage_bytes<S, BN>();
 }
 template <int S, int BN>
@@ -101,15 +119,15 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
-// groups 1024 bytes apart.
+// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle (rows of BK = 32
+// 16-bit values), 8-row groups 512 bytes apart.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     uint64_t d = 0;
     d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
-    d |= static_cast<uint64_t>(1) << 16;            // leading byte offset (unused for SW128 K-major)
-    d |= static_cast<uint64_t>(1024 >> 4) << 32;    // stride byte offset
+    d |= static_cast<uint64_t>(1) << 16;            // leading byte offset (unused for swizzled K-major)
+    d |= static_cast<uint64_t>(512 >> 4) << 32;     // stride byte offset: 8 rows x 64 bytes
     d |= static_cast<uint64_t>(1) << 46;            // descriptor version
-    d |= static_cast<uint64_t>(2) << 61;            // 128-byte swizzle
+    d |= static_cast<uint64_t>(4) << 61;            // 64-byte swizzle
     return d;
 }
 
@@ -186,12 +204,11 @@ __device__ __forceinline__ bool split_value(float x, int bf16, uint16_t (&q)[3])
 }
 
 template <int SCHEME, int BN>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kThreads, 1)
     k_split_gemm(const __grid_constant__ Maps maps, GemmParams p) {
     constexpr int PIECES = Cfg<SCHEME>::PIECES, STAGES = stages<SCHEME, BN>();
-    constexpr int ACCS = Cfg<SCHEME>::ACCS, SB = stage_bytes<SCHEME, BN>();
+    constexpr int SB = stage_bytes<SCHEME, BN>();
     constexpr int BTILE = BN * BK * 2;
-    constexpr uint32_t TMEM_COLS = static_cast<uint32_t>(ACCS * BN) < 32u ? 32u : static_cast<uint32_t>(ACCS * BN);
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -205,6 +222,9 @@ __global__ void __launch_bounds__(128, 1)
     const GemmPart& P = p.part[blockIdx.z];
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int nkb = (P.K + BK - 1) / BK;
+    // TMEM columns [h BN, (h + 1) BN): head accumulator of K slice h; then the tail one
+    const int nheads = n_heads(SCHEME, P.K);
+    const uint32_t ncols = tmem_cols(SCHEME, P.K, BN);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -217,7 +237,7 @@ __global__ void __launch_bounds__(128, 1)
     if (warp == 2) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
-                     "r"(TMEM_COLS)
+                     "r"(ncols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
         fence_before();
@@ -242,7 +262,7 @@ __global__ void __launch_bounds__(128, 1)
             }
         }
     } else if (warp == 1 && lane == 0) {
-        const uint32_t acc0 = tmem, acc1 = tmem + (ACCS == 2 ? static_cast<uint32_t>(BN) : 0u);
+        const uint32_t tail = tmem + static_cast<uint32_t>(nheads * BN);
         for (int kb = 0; kb < nkb; ++kb) {
             const int s = kb % STAGES, round = kb / STAGES;
             if (!mbar_wait(full0 + 8 * s, round & 1, p.err, 2)) break;
@@ -256,18 +276,20 @@ __global__ void __launch_bounds__(128, 1)
                     a[q] = sdesc(st + q * TILE_BYTES + k * 32);
                     b[q] = sdesc(st + PIECES * TILE_BYTES + q * BTILE + k * 32);
                 }
-                const uint32_t first = (kb | k) != 0;
+                const uint32_t accum = (kb | k) != 0;   // 0: the first product overwrites
                 if (SCHEME == kHiLo) {
-                    mma_f16(acc0, a[0], b[0], p.idesc, first);
-                    mma_f16(acc0, a[0], b[1], p.idesc, 1);
-                    mma_f16(acc0, a[1], b[0], p.idesc, 1);
+                    mma_f16(tail, a[0], b[0], p.idesc, accum);
+                    mma_f16(tail, a[0], b[1], p.idesc, 1);
+                    mma_f16(tail, a[1], b[0], p.idesc, 1);
                 } else {
-                    mma_f16(acc0, a[0], b[0], p.idesc, first);      // exact integer sums
-                    mma_f16(acc1, a[0], b[1], p.idesc, first);
-                    mma_f16(acc1, a[1], b[0], p.idesc, 1);
-                    mma_f16(acc1, a[1], b[1], p.idesc, 1);
-                    mma_f16(acc1, a[0], b[PIECES - 1], p.idesc, 1);
-                    mma_f16(acc1, a[PIECES - 1], b[0], p.idesc, 1);
+                    // exact integer sums, a fresh accumulator every kHeadK of K
+                    const uint32_t head = tmem + static_cast<uint32_t>((kb / kHeadKB) * BN);
+                    mma_f16(head, a[0], b[0], p.idesc, ((kb % kHeadKB) | k) != 0);
+                    mma_f16(tail, a[0], b[1], p.idesc, accum);
+                    mma_f16(tail, a[1], b[0], p.idesc, 1);
+                    mma_f16(tail, a[1], b[1], p.idesc, 1);
+                    mma_f16(tail, a[0], b[PIECES - 1], p.idesc, 1);
+                    mma_f16(tail, a[PIECES - 1], b[0], p.idesc, 1);
                 }
             }
             mma_commit(empty0 + 8 * s);
@@ -276,25 +298,35 @@ __global__ void __launch_bounds__(128, 1)
     }
     __syncwarp();
 
-    // epilogue: warp w owns accumulator rows 32w .. 32w + 31
+    // epilogue: warp w reads TMEM lanes (rows) 32 (w % 4) .. + 31 (the lane quarter a warp
+    // may access) and every second 32-column chunk starting at chunk w / 4
     const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0, p.err, 3) ? 1 : 0) != 0;
     fence_after();
     if (ok) {
         const float sa = P.sa_dev ? *P.sa_dev : P.sa, sb = P.sb_dev ? *P.sb_dev : P.sb;
         const float inv = 1.0f / (sa * sb);
-        const int row = m0 + warp * 32 + lane;
-        const uint32_t lane_off = static_cast<uint32_t>(warp * 32) << 16;
-        for (int c = 0; c < BN / 32; ++c) {
+        const int quarter = warp & 3;
+        const int row = m0 + quarter * 32 + lane;
+        const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
+        for (int c = warp >> 2; c < BN / 32; c += kThreads / 128) {
             uint32_t r[32];
             tmem_ld32(tmem + lane_off + c * 32, r);
             float v[32];
-            if (ACCS == 2) {
+            if (SCHEME == kHead3) {
+                // heads summed first (exact while below 2^24), then the tail
                 uint32_t r1[32];
-                tmem_ld32(tmem + static_cast<uint32_t>(BN) + lane_off + c * 32, r1);
+                tmem_ld32(tmem + static_cast<uint32_t>(nheads * BN) + lane_off + c * 32, r1);
                 tmem_wait_ld();
 #pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    v[j] = (__uint_as_float(r[j]) + __uint_as_float(r1[j])) * inv;
+                for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+                for (int h = 1; h < nheads; ++h) {
+                    tmem_ld32(tmem + static_cast<uint32_t>(h * BN) + lane_off + c * 32, r);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] += __uint_as_float(r[j]);
+                }
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = (v[j] + __uint_as_float(r1[j])) * inv;
             } else {
                 tmem_wait_ld();
 #pragma unroll
@@ -389,7 +421,7 @@ __global__ void __launch_bounds__(128, 1)
     if (warp == 2) {
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(TMEM_COLS)
+                     "r"(ncols)
                      : "memory");
     }
 }
@@ -481,7 +513,7 @@ bool make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int
     const CUresult r =
         encode(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
                const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
@@ -493,36 +525,44 @@ uint32_t idesc_f16(int bf16, int bn) {
            (static_cast<uint32_t>(bn >> 3) << 17) | (static_cast<uint32_t>(BM >> 4) << 24);
 }
 
+template <int S, int BN>
+cudaError_t set_smem() {
+    return cudaFuncSetAttribute(k_split_gemm<S, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem_total<S, BN>());
+}
+
 cudaError_t prepare() {
-    cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_split_gemm<kHiLo, 128>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem_total<kHiLo, 128>());
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_split_gemm<kHead3, 128>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem_total<kHead3, 128>());
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_split_gemm<kHiLo, 64>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem_total<kHiLo, 64>());
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_split_gemm<kHead3, 64>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem_total<kHead3, 64>());
+    cudaError_t e = set_smem<kHiLo, 64>();
+    if (e == cudaSuccess) e = set_smem<kHead3, 64>();
+    if (e == cudaSuccess) e = set_smem<kHiLo, 128>();
+    if (e == cudaSuccess) e = set_smem<kHead3, 128>();
+    if (e == cudaSuccess) e = set_smem<kHiLo, 256>();
+    if (e == cudaSuccess) e = set_smem<kHead3, 256>();
     return e;
 }
 
 cudaError_t launch(int scheme, const Maps& m, const GemmParams& p, int nparts, cudaStream_t st,
                    int bn) {
+    if (nparts < 1 || nparts > kMaxParts || (bn != 64 && bn != 128 && bn != 256))
+        return cudaErrorInvalidValue;
+    for (int z = 0; z < nparts; ++z)
+        if (p.part[z].K < 1 || tmem_cols(scheme, p.part[z].K, bn) > 512) return cudaErrorInvalidValue;
     dim3 grid((p.N + bn - 1) / bn, (p.M + BM - 1) / BM, nparts);
     if (bn == 64) {
         if (scheme == kHiLo)
-            k_split_gemm<kHiLo, 64><<<grid, 128, smem_total<kHiLo, 64>(), st>>>(m, p);
+            k_split_gemm<kHiLo, 64><<<grid, kThreads, smem_total<kHiLo, 64>(), st>>>(m, p);
         else
-            k_split_gemm<kHead3, 64><<<grid, 128, smem_total<kHead3, 64>(), st>>>(m, p);
+            k_split_gemm<kHead3, 64><<<grid, kThreads, smem_total<kHead3, 64>(), st>>>(m, p);
+    } else if (bn == 256) {
+        if (scheme == kHiLo)
+            k_split_gemm<kHiLo, 256><<<grid, kThreads, smem_total<kHiLo, 256>(), st>>>(m, p);
+        else
+            k_split_gemm<kHead3, 256><<<grid, kThreads, smem_total<kHead3, 256>(), st>>>(m, p);
     } else {
         if (scheme == kHiLo)
-            k_split_gemm<kHiLo, 128><<<grid, 128, smem_total<kHiLo, 128>(), st>>>(m, p);
+            k_split_gemm<kHiLo, 128><<<grid, kThreads, smem_total<kHiLo, 128>(), st>>>(m, p);
         else
-            k_split_gemm<kHead3, 128><<<grid, 128, smem_total<kHead3, 128>(), st>>>(m, p);
+            k_split_gemm<kHead3, 128><<<grid, kThreads, smem_total<kHead3, 128>(), st>>>(m, p);
     }
     return cudaGetLastError();
 }

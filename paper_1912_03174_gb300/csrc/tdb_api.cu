@@ -17,7 +17,9 @@ void gemm_f32_dham(int N, const float* A, const float* S, const float* dv, float
 void gemm_f32_add(int M, int Ncol, int K, const float* A, int lda, const float* B, int ldb,
                   float* C, int ldc, const float* Cadd, cudaStream_t st);
 void launch_f64_to_f32(size_t n, const double* in, float* out, cudaStream_t st);
-void launch_sub_to_f32(size_t n, const double* a, const double* b, float* out, cudaStream_t st);
+void launch_f32_to_f64(size_t n, const float* in, double* out, cudaStream_t st);
+void gemm_f32(int M, int Ncol, int K, const float* A, int lda, const float* B, int ldb, float* C,
+              int ldc, cudaStream_t st);
 void launch_add_f32_strided(int N, const float* a, const float* b, int ldb, float* out, int ldo,
                             cudaStream_t st);
 void launch_small_energies(const Ctx& c, double* out, cudaStream_t st);
@@ -97,12 +99,21 @@ struct Carver {
     }
 };
 
-bool mixed(const Ctx& c) { return c.prm.precision != TDB_FP64; }
+// Frozen-nuclei reduced forms (FP32-pair master of rho - rho_ref).
+bool mixed(const Ctx& c) { return c.prm.precision != TDB_FP64 && !c.prm.move_nuclei; }
+// Moving nuclei with FP32 products (FP64 density, forces and update).
+bool md32(const Ctx& c) { return c.prm.move_nuclei && c.prm.precision == TDB_FP32; }
 bool tensor(const Ctx& c) {
     return c.prm.precision == TDB_BF16X3 || c.prm.precision == TDB_FP16X3 ||
            c.prm.precision == TDB_FP16X6;
 }
 bool head3(const Ctx& c) { return c.prm.precision == TDB_FP16X6; }
+// The tensor-core X products (dM rho_ref, M Re(rho - rho_ref), M Im rho) are cut into
+// this many K slices with their own FP32 outputs, so that a slice of K <= 1024 keeps one
+// exact head accumulator per tile.  (Cutting N = 1024 in two as well spreads the tiles
+// more evenly over the SMs, but the update then reads twice the partial products and the
+// step is slower.)
+int x_split(const Ctx& c) { return c.N > 1024 ? 2 : 1; }
 int piece_bf16(const Ctx& c) { return c.prm.precision == TDB_BF16X3 ? 1 : 0; }
 
 // 2^floor(log2(target / m)): the power-of-two scale that maps magnitude m near target
@@ -144,22 +155,36 @@ size_t carve(Ctx& c, char* base) {
     c.obs_out = k.take<double>(16 + 2 * N);   // reductions, small energies, eigenvalues, occupations
     c.sc = k.take<DevScalars>(1);
     if (mixed(c)) {
+        for (int l = 0; l < 2; ++l) {
+            c.ms[l].re_hi = k.take<float>(NN);
+            c.ms[l].re_lo = k.take<float>(NN);
+            c.ms[l].im_hi = k.take<float>(NN);
+            c.ms[l].im_lo = k.take<float>(NN);
+        }
+        c.qbase = k.take<double>(nat);
         c.rho_ref = k.take<double>(NN);
         c.Mgs_f = k.take<float>(NN);
-        c.Xre_f = k.take<float>(NN);
-        c.Xim_f = k.take<float>(NN);
     }
     if (mixed(c)) {
         c.dv_f = k.take<float>(N);
         c.S_f = k.take<float>(NN);
     }
-    if (c.prm.precision == TDB_FP32) {
+    if (md32(c)) {
+        c.md_sinv = k.take<float>(NN);
+        c.md_b = k.take<float>(NN);
+        c.md_rre = k.take<float>(NN);
+        c.md_rim = k.take<float>(NN);
+        c.md_m = k.take<float>(NN);
+        c.md_xre = k.take<float>(NN);
+        c.md_xim = k.take<float>(NN);
+    }
+    if (c.prm.precision == TDB_FP32 && !c.prm.move_nuclei) {
+        c.Xre_f = k.take<float>(NN);
+        c.Xim_f = k.take<float>(NN);
         c.Sinv_f = k.take<float>(NN);
         c.dM_f = k.take<float>(2 * NN);     // [delta M | M], row stride 2N
         c.M_f = c.dM_f ? c.dM_f + N : nullptr;
-        c.rref_f = k.take<float>(2 * NN);   // [rho_ref ; Re(rho - rho_ref)] stacked, 2N x N
-        c.dre_f = c.rref_f ? c.rref_f + NN : nullptr;
-        c.dim_f = k.take<float>(NN);
+        c.rref_f = k.take<float>(NN);
     }
     if (tensor(c)) {
         const size_t Np = (N + 63) / 64 * 64;
@@ -173,7 +198,7 @@ size_t carve(Ctx& c, char* base) {
             c.pc_bre[q] = k.take<uint16_t>(2 * N * Np);
             c.pc_bim[q] = k.take<uint16_t>(N * Np);
         }
-        if (head3(c)) c.Xa_f = k.take<float>(NN);
+        for (int q = 0; q < 3 * x_split(c); ++q) c.xp[q] = k.take<float>(NN);
         c.dyn = k.take<tc::DynScales>(1);
     }
     if (c.prm.move_nuclei) {
@@ -220,13 +245,14 @@ tdb_status validate(const tdb_system* s, const tdb_params* p) {
         set_err("invalid params");
         return TDB_ERR_ARG;
     }
-    if (p->move_nuclei && p->precision != TDB_FP64) {
-        set_err("moving nuclei are implemented for the FP64 form only in this build");
+    if (p->move_nuclei && p->precision != TDB_FP64 && p->precision != TDB_FP32) {
+        set_err("moving nuclei run in the FP64 and FP32 forms only in this build");
         return TDB_ERR_UNSUPPORTED;
     }
-    if (p->precision == TDB_FP16X6 && N > 1024) {
-        // the integer head products of a K = N sum are exact only while K * 127^2 < 2^24
-        set_err("TDB_FP16X6 supports N <= 1024 in this build");
+    if (p->precision == TDB_FP16X6 && N > 2048) {
+        // the X products are cut into two K slices, and the integer head products of one
+        // slice sum exactly only while K * 127^2 < 2^24 (K <= 1040)
+        set_err("TDB_FP16X6 supports N <= 2048 in this build");
         return TDB_ERR_UNSUPPORTED;
     }
     return TDB_OK;
@@ -304,6 +330,56 @@ void occupations(const std::vector<double>& eps, double ne, double kT, std::vect
         double x = (eps[i] - mu) / kT;
         x = std::min(700.0, std::max(-700.0, x));
         f[i] = 2.0 / (1.0 + std::exp(x));
+    }
+}
+
+// Charge-sloshing preconditioner of the SCC residual (the paper names no mixer; the
+// fixed point does not depend on it).  A potential change dv moves the charges by
+// about chi dv; chi is modelled as a constant density of states per atom at the Fermi
+// level, c, on the charge-neutral subspace: chi = -c (1 - 11^T / n).  One Newton step
+// of dq_out = dq_in + chi gamma dq_in is then x = (1 - chi gamma)^-1 resid.  c sums
+// the Fermi-function derivative over the levels at an electronic temperature of at
+// least kPrecondKT, so that a gap at the Fermi level does not switch it off.
+constexpr double kPrecondKT = 0.02;
+
+void scc_precondition(const std::vector<double>& eps, double ne, double kT,
+                      const std::vector<double>& gamma, const std::vector<double>& resid,
+                      std::vector<double>& out) {
+    const int n = (int)resid.size();
+    const double ke = std::max(kT, kPrecondKT);
+    std::vector<double> f;
+    occupations(eps, ne, ke, f);
+    double c = 0.0;
+    for (double fi : f) c += fi * (1.0 - 0.5 * fi) / ke;
+    c /= n;
+    // A = 1 + c (1 - 11^T/n) gamma, solved by Gaussian elimination with partial pivoting
+    std::vector<double> colmean(n, 0.0), A((size_t)n * n);
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b) colmean[b] += gamma[(size_t)a * n + b] / n;
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b)
+            A[(size_t)a * n + b] = (a == b ? 1.0 : 0.0) + c * (gamma[(size_t)a * n + b] - colmean[b]);
+    out = resid;
+    for (int col = 0; col < n; ++col) {
+        int p = col;
+        for (int r = col + 1; r < n; ++r)
+            if (std::fabs(A[(size_t)r * n + col]) > std::fabs(A[(size_t)p * n + col])) p = r;
+        if (p != col) {
+            for (int k = 0; k < n; ++k) std::swap(A[(size_t)p * n + k], A[(size_t)col * n + k]);
+            std::swap(out[p], out[col]);
+        }
+        const double d = A[(size_t)col * n + col];
+        for (int r = col + 1; r < n; ++r) {
+            const double m = A[(size_t)r * n + col] / d;
+            if (m == 0.0) continue;
+            for (int k = col; k < n; ++k) A[(size_t)r * n + k] -= m * A[(size_t)col * n + k];
+            out[r] -= m * out[col];
+        }
+    }
+    for (int r = n - 1; r >= 0; --r) {
+        double v = out[r];
+        for (int k = r + 1; k < n; ++k) v -= A[(size_t)r * n + k] * out[k];
+        out[r] = v / A[(size_t)r * n + r];
     }
 }
 
@@ -412,39 +488,72 @@ tdb_status upload_clock(Ctx& c, long long step, long long n_base, double t_base)
     return TDB_OK;
 }
 
-// After rho_n changes outside a step (ground state, kick, set_state): Mulliken
-// partials of rho_n and the reduced-precision operands.
-tdb_status refresh_derived(Ctx& c) {
-    launch_mulliken_partials(c.N, c.rho_re[c.cur], c.S, c.partial, c.stream);
-    CKL();
-    if (c.prm.precision == TDB_FP32) {
-        const size_t NN = (size_t)c.N * c.N;
-        launch_sub_to_f32(NN, c.rho_re[c.cur], c.rho_ref, c.dre_f, c.stream);
-        launch_sub_to_f32(NN, c.rho_im[c.cur], nullptr, c.dim_f, c.stream);
-        CKL();
+// Operand pieces written from the master by the reduced forms (tensor-core schemes).
+UpdateOperands master_operands(Ctx& c) {
+    UpdateOperands ops;
+    ops.rho_ref = c.rho_ref;
+    ops.scheme = c.scheme;
+    ops.bf16 = piece_bf16(c);
+    const int np = c.npieces;
+    for (int q = 0; q < np; ++q) {
+        ops.re[q] = c.pc_bre[q] + c.Np;
+        ops.im[q] = c.pc_bim[q];
     }
+    ops.ld_re = 2 * c.Np;
+    ops.ld_im = c.Np;
+    ops.scale = c.s_rho;
+    if (head3(c)) ops.dyn = c.dyn;
+    return ops;
+}
+
+// Reduced forms: partials and operands of rho_n from the master.  With `restored`
+// (FP16X6 resuming from a checkpoint of the same form) the scales saved with the state
+// are kept, so that the continuation repeats the original run bit for bit.
+tdb_status derived_from_master(Ctx& c, bool restored = false) {
+    launch_master_partials(c, c.ms[c.cur], c.partial, c.stream);
     if (tensor(c)) {
-        const int N = c.N, b = piece_bf16(c);
-        if (head3(c)) {
-            // exact scale of the current deviation, then its pieces
-            CK(cudaMemsetAsync(&c.dyn->max_drho[c.cur], 0, sizeof(double), c.stream));
-            launch_absmax((size_t)N * N, c.rho_re[c.cur], &c.dyn->max_drho[c.cur], c.stream,
-                          c.rho_ref);
-            launch_absmax((size_t)N * N, c.rho_im[c.cur], &c.dyn->max_drho[c.cur], c.stream);
-            launch_split_rho(c, c.cur, c.rho_re[c.cur], c.rho_im[c.cur], c.stream);
+        UpdateOperands ops = master_operands(c);
+        if (head3(c) && restored) {
+            launch_master_pieces(c, c.ms[c.cur], ops, nullptr, &c.dyn->s_rho, c.stream);
+        } else if (head3(c)) {
+            // exact maxima of both leapfrog levels, then the pieces of the current one
+            for (int l = 0; l < 2; ++l) {
+                CK(cudaMemsetAsync(&c.dyn->max_drho[l], 0, sizeof(double), c.stream));
+                launch_master_absmax(c, c.ms[l], &c.dyn->max_drho[l], c.stream);
+            }
+            launch_master_pieces(c, c.ms[c.cur], ops, &c.dyn->max_drho[c.cur], nullptr, c.stream);
             // the next step's bookkeeping moves max_drho[2] into max_drho[cur]: keep it equal
             CK(cudaMemcpyAsync(&c.dyn->max_drho[2], &c.dyn->max_drho[c.cur], sizeof(double),
                                cudaMemcpyDeviceToDevice, c.stream));
             CK(cudaMemsetAsync(&c.dyn->max_dv, 0, sizeof(double), c.stream));
         } else {
-            uint16_t* re[3] = {c.pc_bre[0] + c.Np, c.pc_bre[1] + c.Np, nullptr};
-            tc::launch_split(c.scheme, N, N, c.rho_re[c.cur], N, c.s_rho, 1, b, re, 2 * c.Np,
-                             c.stream, c.rho_ref);
-            tc::launch_split(c.scheme, N, N, c.rho_im[c.cur], N, c.s_rho, -1, b, c.pc_bim, c.Np,
-                             c.stream);
+            launch_master_pieces(c, c.ms[c.cur], ops, nullptr, nullptr, c.stream);
         }
-        CKL();
     }
+    CKL();
+    return TDB_OK;
+}
+
+// After rho_n changes outside a step (ground state, kick, set_state): Mulliken
+// partials of rho_n and, for the reduced forms, the master and the operands.
+tdb_status refresh_derived(Ctx& c) {
+    if (!mixed(c)) {
+        launch_mulliken_partials(c.N, c.rho_re[c.cur], c.S, c.partial, c.stream);
+        CKL();
+        return TDB_OK;
+    }
+    // the FP64 view is authoritative here: convert both leapfrog levels
+    for (int l = 0; l < 2; ++l) launch_view_to_master(c, c.rho_re[l], c.rho_im[l], c.ms[l], c.stream);
+    c.view_valid = true;
+    return derived_from_master(c);
+}
+
+// Reduced forms: bring the FP64 view up to date with the master.
+tdb_status materialize(Ctx& c) {
+    if (!mixed(c) || c.view_valid) return TDB_OK;
+    for (int l = 0; l < 2; ++l) launch_master_to_view(c, c.ms[l], c.rho_re[l], c.rho_im[l], c.stream);
+    CKL();
+    c.view_valid = true;
     return TDB_OK;
 }
 
@@ -499,7 +608,10 @@ tdb_status setup_tensor(Ctx& c) {
 }
 
 // tile width of the X product (128: measured faster than 64-wide tiles for every scheme)
-int xbn(const Ctx&) { return 128; }
+// Width of the X tiles: 128 x 256 tiles read half as much shared memory per MMA as
+// 128 x 128 ones (the split products re-read each piece several times, and shared-memory
+// bandwidth is what bounds the 128-wide tiles); small systems keep 128.
+int xbn(const Ctx& c) { return c.N >= 512 ? 256 : 128; }
 
 tdb_status build_maps(Ctx& c) {
     CK(tc::prepare());
@@ -551,9 +663,26 @@ tdb_status md_forces(Ctx& c, int cur, bool first, int commit, int* n) {
     launch_charges(c, c.partial, c.q, c.dq, c.stream);
     launch_potential(c, c.gamma, c.dq, c.d_R, c.sc, c.v_orb, c.v_atom, c.gdq, c.hist, c.v_ref,
                      nullptr, c.stream);
-    gemm_f64_ham(c.N, c.Sinv, c.H0, c.S, c.v_orb, c.M, c.stream);            // M = S^-1 H
-    gemm_f64(c.N, c.N, c.N, c.M, c.N, c.rho_re[cur], c.N, c.Xre, c.N, c.stream);
-    gemm_f64(c.N, c.N, c.N, c.M, c.N, c.rho_im[cur], c.N, c.Xim, c.N, c.stream);
+    if (md32(c)) {
+        // M = S^-1 H and X = M rho_n with FP32 operands and FFMA accumulation
+        const int N = c.N;
+        const size_t NN = (size_t)N * N;
+        launch_build_hamiltonian(N, c.H0, c.S, c.v_orb, c.Hs, c.stream);
+        launch_f64_to_f32(NN, c.Sinv, c.md_sinv, c.stream);
+        launch_f64_to_f32(NN, c.Hs, c.md_b, c.stream);
+        launch_f64_to_f32(NN, c.rho_re[cur], c.md_rre, c.stream);
+        launch_f64_to_f32(NN, c.rho_im[cur], c.md_rim, c.stream);
+        gemm_f32(N, N, N, c.md_sinv, N, c.md_b, N, c.md_m, N, c.stream);
+        gemm_f32(N, N, N, c.md_m, N, c.md_rre, N, c.md_xre, N, c.stream);
+        gemm_f32(N, N, N, c.md_m, N, c.md_rim, N, c.md_xim, N, c.stream);
+        launch_f32_to_f64(NN, c.md_xre, c.Xre, c.stream);
+        launch_f32_to_f64(NN, c.md_xim, c.Xim, c.stream);
+        if (n) *n += 7;
+    } else {
+        gemm_f64_ham(c.N, c.Sinv, c.H0, c.S, c.v_orb, c.M, c.stream);        // M = S^-1 H
+        gemm_f64(c.N, c.N, c.N, c.M, c.N, c.rho_re[cur], c.N, c.Xre, c.N, c.stream);
+        gemm_f64(c.N, c.N, c.N, c.M, c.N, c.rho_im[cur], c.N, c.Xim, c.N, c.stream);
+    }
     launch_wre(c.N, c.Xre, c.Wre, c.stream);
     launch_forces(c, c.rho_re[cur], c.Wre, c.d_F, c.stream);
     launch_vel_n(c, c.d_F, first ? 1 : 0, c.stream);
@@ -570,9 +699,22 @@ tdb_status enqueue_step_md(Ctx& c, int cur, bool euler, int* launches) {
     const int prv = cur ^ 1;
     int n = 0;
     TRY(md_forces(c, cur, euler, 1, &n));
-    gemm_f64(c.N, c.N, c.N, c.Sinv, c.N, c.D, c.N, c.M, c.N, c.stream);       // Y = S^-1 D
-    gemm_f64(c.N, c.N, c.N, c.M, c.N, c.rho_re[cur], c.N, c.Zre, c.N, c.stream);
-    gemm_f64(c.N, c.N, c.N, c.M, c.N, c.rho_im[cur], c.N, c.Zim, c.N, c.stream);
+    if (md32(c)) {
+        // Y = S^-1 D and Z = Y rho_n in FP32 (the FP32 copies of S^-1 and rho_n are current)
+        const int N = c.N;
+        const size_t NN = (size_t)N * N;
+        launch_f64_to_f32(NN, c.D, c.md_b, c.stream);
+        gemm_f32(N, N, N, c.md_sinv, N, c.md_b, N, c.md_m, N, c.stream);
+        gemm_f32(N, N, N, c.md_m, N, c.md_rre, N, c.md_xre, N, c.stream);
+        gemm_f32(N, N, N, c.md_m, N, c.md_rim, N, c.md_xim, N, c.stream);
+        launch_f32_to_f64(NN, c.md_xre, c.Zre, c.stream);
+        launch_f32_to_f64(NN, c.md_xim, c.Zim, c.stream);
+        n += 3;
+    } else {
+        gemm_f64(c.N, c.N, c.N, c.Sinv, c.N, c.D, c.N, c.M, c.N, c.stream);   // Y = S^-1 D
+        gemm_f64(c.N, c.N, c.N, c.M, c.N, c.rho_re[cur], c.N, c.Zre, c.N, c.stream);
+        gemm_f64(c.N, c.N, c.N, c.M, c.N, c.rho_im[cur], c.N, c.Zim, c.N, c.stream);
+    }
     const double factor = euler ? c.prm.dt : 2.0 * c.prm.dt;
     const double* bre = euler ? c.rho_re[cur] : c.rho_re[prv];
     const double* bim = euler ? c.rho_im[cur] : c.rho_im[prv];
@@ -612,7 +754,7 @@ tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* t
     int n = 0;
     MARK("charges");
     launch_charges(c, c.partial, c.q, c.dq, c.stream, nullptr, nullptr, head3(c) ? c.dyn : nullptr,
-                   cur);
+                   cur, c.qbase);
     ++n;
     MARK("potential");
     launch_potential(c, c.gamma, c.dq, c.d_R, c.sc, c.v_orb, c.v_atom, c.gdq, c.hist, c.v_ref,
@@ -663,51 +805,49 @@ tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* t
         x.bf16 = b;
         x.err = c.d_err;
         x.max_out = h3 ? c.dyn->max_x : nullptr;
-        int nparts;
-        if (h3) {
-            // X_a = dM rho_ref, X_re = M Re(rho - rho_ref), X_im = M Im(rho): each K = N
-            x.part[0] = {0, 0, N, 0, c.Xa_f, N, 0.f, c.s_ref, &c.dyn->s_dm, nullptr, 0};
-            x.part[1] = {Np, Np, N, 0, c.Xre_f, N, c.s_m, 0.f, nullptr, &c.dyn->s_rho, 0};
-            x.part[2] = {Np, 0, N, 0, c.Xim_f, N, c.s_m, 0.f, nullptr, &c.dyn->s_rho, 1};
-            nparts = 3;
-        } else {
-            // X_re = [dM | M] [rho_ref ; Re(rho - rho_ref)],  X_im = M Im(rho)
-            x.part[0] = {0, 0, Np + N, 0, c.Xre_f, N, c.s_m, c.s_rho, nullptr, nullptr, 0};
-            x.part[1] = {Np, 0, N, 0, c.Xim_f, N, c.s_m, c.s_rho, nullptr, nullptr, 1};
-            nparts = 2;
-        }
+        // parts: X_a = dM rho_ref and X_re = M Re(rho - rho_ref) (the real part of X is their
+        // sum), then X_im = M Im rho; each cut into ns K slices
+        const int ns = x_split(c);
+        const int kc = ((N + ns - 1) / ns + 63) / 64 * 64;
+        int nparts = 0;
+        for (int prod = 0; prod < 3; ++prod)
+            for (int sl = 0; sl < ns; ++sl) {
+                const int off = sl * kc, len = std::min(kc, N - off);
+                tc::GemmPart& P = x.part[nparts];
+                P.k0_a = (prod == 0 ? 0 : Np) + off;
+                P.k0_b = (prod == 1 ? Np : 0) + off;
+                P.K = len;
+                P.mode = 0;
+                P.C = c.xp[nparts];
+                P.ldc = N;
+                P.b_set = prod == 2 ? 1 : 0;
+                if (h3) {
+                    // dM pieces carry s_dm, M pieces s_m; rho_ref pieces s_ref, dRho s_rho
+                    P.sa = c.s_m;
+                    P.sa_dev = prod == 0 ? &c.dyn->s_dm : nullptr;
+                    P.sb = c.s_ref;
+                    P.sb_dev = prod == 0 ? nullptr : &c.dyn->s_rho;
+                } else {
+                    P.sa = c.s_m;
+                    P.sb = c.s_rho;
+                }
+                ++nparts;
+            }
         MARK("tc_gemm_X");
         CK(tc::launch(c.scheme, c.maps_x, x, nparts, c.stream, xbn(c)));
         ++n;
-        UpdateOperands ops;
-        ops.rho_ref = c.rho_ref;
-        ops.scheme = c.scheme;
-        ops.bf16 = b;
+        // the update writes the pieces of rho_{n+1} - rho_ref itself (FP16X6: scaled from a
+        // bound on their size) and tracks their maximum
+        UpdateOperands ops = master_operands(c);
         ops.cur = cur;
-        if (h3) {
-            // the update writes the head pieces of rho_{n+1} - rho_ref itself, scaled from a
-            // bound on their size, and tracks their maximum
-            ops.dyn = c.dyn;
-            ops.base_slot = euler ? cur : prv;
-            ops.Xre2 = c.Xa_f;
-            for (int q = 0; q < 3; ++q) {
-                ops.re[q] = c.pc_bre[q] + Np;
-                ops.im[q] = c.pc_bim[q];
-            }
-            ops.ld_re = 2 * Np;
-            ops.ld_im = Np;
-        } else {
-            ops.re[0] = c.pc_bre[0] + Np;
-            ops.re[1] = c.pc_bre[1] + Np;
-            ops.im[0] = c.pc_bim[0];
-            ops.im[1] = c.pc_bim[1];
-            ops.ld_re = 2 * Np;
-            ops.ld_im = Np;
-            ops.scale = c.s_rho;
-        }
+        ops.base_slot = euler ? cur : prv;
+        ops.nre = 2 * ns;
+        ops.nim = ns;
+        for (int q = 0; q < 2 * ns; ++q) ops.xre[q] = c.xp[q];
+        for (int q = 0; q < ns; ++q) ops.xim[q] = c.xp[2 * ns + q];
         MARK("update");
-        launch_update_f32(c, c.Xre_f, c.Xim_f, bre, bim, c.rho_re[prv], c.rho_im[prv], factor,
-                          c.S, c.partial, c.sc, ops, c.stream);
+        launch_update_df(c, euler ? c.ms[cur] : c.ms[prv], c.ms[prv], factor, c.partial, c.sc, ops,
+                         c.stream);
         ++n;
     } else {
         const int N = c.N;
@@ -718,19 +858,21 @@ tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* t
         MARK("add_M");
         launch_add_f32_strided(N, c.Mgs_f, c.dM_f, 2 * N, c.M_f, 2 * N, c.stream);
         ++n;
-        // X_re = dM rho_ref + M Re(rho - rho_ref);  X_im = M Im rho
+        // X_re = dM rho_ref + M Re(rho - rho_ref);  X_im = M Im rho (master hi parts)
         MARK("gemm_Xre_f32");
-        gemm_f32_add(N, N, 2 * N, c.dM_f, 2 * N, c.rref_f, N, c.Xre_f, N, nullptr, c.stream);
+        gemm_f32_add(N, N, N, c.dM_f, 2 * N, c.rref_f, N, c.Xre_f, N, nullptr, c.stream);
+        gemm_f32_add(N, N, N, c.M_f, 2 * N, c.ms[cur].re_hi, N, c.Xre_f, N, c.Xre_f, c.stream);
         MARK("gemm_Xim_f32");
-        gemm_f32_add(N, N, N, c.M_f, 2 * N, c.dim_f, N, c.Xim_f, N, nullptr, c.stream);
-        n += 2;
+        gemm_f32_add(N, N, N, c.M_f, 2 * N, c.ms[cur].im_hi, N, c.Xim_f, N, nullptr, c.stream);
+        n += 3;
         MARK("update");
         UpdateOperands ops;
-        ops.rho_ref = c.rho_ref;
-        ops.f_re = c.dre_f;
-        ops.f_im = c.dim_f;
-        launch_update_f32(c, c.Xre_f, c.Xim_f, bre, bim, c.rho_re[prv], c.rho_im[prv], factor,
-                          c.S, c.partial, c.sc, ops, c.stream);
+        ops.cur = cur;
+        ops.xre[0] = c.Xre_f;
+        ops.xim[0] = c.Xim_f;
+        ops.nre = ops.nim = 1;
+        launch_update_df(c, euler ? c.ms[cur] : c.ms[prv], c.ms[prv], factor, c.partial, c.sc, ops,
+                         c.stream);
         ++n;
     }
     MARK("end");
@@ -845,7 +987,7 @@ void tdb_default_params(tdb_params* p) {
     p->scc_tol = 1e-12;
     p->scc_max_iter = 400;
     p->kT = 0.0;
-    p->scc_mix = 0.1;
+    p->scc_mix = 0.3;
     p->history_cap = 65536;
     p->cuda_stream = nullptr;
 }
@@ -964,7 +1106,7 @@ tdb_status tdb_create(const tdb_system* sys, const tdb_params* prm, void* worksp
             return fail(TDB_ERR_CUDA);
     }
     if (mixed(*c)) launch_f64_to_f32((size_t)c->N * c->N, c->S, c->S_f, c->stream);
-    if (c->prm.precision == TDB_FP32)
+    if (c->prm.precision == TDB_FP32 && !c->prm.move_nuclei)
         launch_f64_to_f32((size_t)c->N * c->N, c->Sinv, c->Sinv_f, c->stream);
     if (tensor(*c)) {
         s = build_maps(*c);
@@ -999,7 +1141,14 @@ tdb_status tdb_ground_state(tdb_ctx* c, int* iters_out, double* residual_out) {
     double* work = nullptr;
     CK(cudaMalloc(&work, sizeof(double) * std::max(lwork, 1) + 256));
     int* info = reinterpret_cast<int*>(reinterpret_cast<char*>(work) + sizeof(double) * std::max(lwork, 1));
-    std::vector<double> dq_in(nat, 0.0), dq_out(nat), eig(N), occ(N), resid(nat);
+    std::vector<double> dq_in(nat, 0.0), dq_out(nat), eig(N), occ(N), resid(nat), pres(nat);
+    std::vector<double> h_gamma;
+    if (c->prm.scc) {
+        h_gamma.resize((size_t)nat * nat);
+        CK(cudaMemcpyAsync(h_gamma.data(), c->gamma, sizeof(double) * nat * nat,
+                           cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
     Anderson mixer{8, c->prm.scc_mix, {}, {}};
     tdb_status rc = TDB_ERR_SCC_NOCONV;
     double res = 0.0;
@@ -1065,7 +1214,8 @@ tdb_status tdb_ground_state(tdb_ctx* c, int* iters_out, double* residual_out) {
             rc = TDB_OK;
             break;
         }
-        mixer.next(dq_in, resid);
+        scc_precondition(eig, c->n_electrons, c->prm.kT, h_gamma, resid, pres);
+        mixer.next(dq_in, pres);
     }
     cudaFree(work);
     if (iters_out) *iters_out = std::min(it, c->prm.scc_max_iter);
@@ -1097,6 +1247,9 @@ tdb_status tdb_ground_state(tdb_ctx* c, int* iters_out, double* residual_out) {
         gemm_f64_ham(N, c->Sinv, c->H0, c->S, c->v_ref, c->M, c->stream);  // M_gs
         launch_f64_to_f32(NN, c->M, c->Mgs_f, c->stream);
         if (c->prm.precision == TDB_FP32) launch_f64_to_f32(NN, c->rho_ref, c->rref_f, c->stream);
+        // Mulliken populations of rho_ref: the step adds those of rho - rho_ref
+        launch_mulliken_partials(N, c->rho_ref, c->S, c->partial, c->stream);
+        launch_charges(*c, c->partial, c->qbase, c->dq, c->stream);
         CKL();
         if (tensor(*c)) TRY(setup_tensor(*c));
     }
@@ -1113,6 +1266,7 @@ tdb_status tdb_kick(tdb_ctx* c, double strength, const double dir[3]) {
         return TDB_ERR_ARG;
     }
     const int N = c->N, cur = c->cur;
+    TRY(materialize(*c));
     if (c->prm.move_nuclei) TRY(md_model(*c));
     // eq:rhokick: T = e^{iV} rho S e^{-iV} S^-1,  rho(0+) = 1/2 (T + T^dagger)
     gemm_f64(N, N, N, c->rho_re[cur], N, c->S, N, c->Xre, N, c->stream);
@@ -1184,6 +1338,7 @@ tdb_status tdb_step(tdb_ctx* c, long n) {
         c->cur ^= 1;
         c->n += 1;
     }
+    if (mixed(*c) && n > 0) c->view_valid = false;
     c->last_launches = launches;
     return TDB_OK;
 }
@@ -1212,10 +1367,12 @@ tdb_status tdb_observables(tdb_ctx* c, tdb_obs* o, double* charges, double* forc
     if (c->prm.move_nuclei) {
         TRY(md_forces(*c, cur, c->euler_next, 0, nullptr));
     } else {
-        launch_charges(*c, c->partial, c->q, c->dq, c->stream);
+        launch_charges(*c, c->partial, c->q, c->dq, c->stream, nullptr, nullptr, nullptr, 0,
+                       c->qbase);
         launch_potential(*c, c->gamma, c->dq, c->d_R, c->sc, c->v_orb, c->v_atom, c->gdq, c->hist,
                          c->v_ref, nullptr, c->stream);
     }
+    TRY(materialize(*c));
     launch_obs_reduce(c->N, c->rho_re[cur], c->rho_im[cur], c->H0, c->S, c->obs_blocks, kObsBlocks,
                       c->stream);
     launch_obs_finish(kObsBlocks, c->obs_blocks, c->obs_out, c->stream);
@@ -1284,6 +1441,7 @@ tdb_status tdb_dipole_history(tdb_ctx* c, double* out, long cap, long* n_out) {
 
 tdb_status tdb_get_rho(tdb_ctx* c, double* re, double* im, double* prev_re, double* prev_im) {
     TRY(check_ctx(c, true, true));
+    TRY(materialize(*c));
     const size_t b = sizeof(double) * c->N * c->N;
     if (re) CK(cudaMemcpyAsync(re, c->rho_re[c->cur], b, cudaMemcpyDeviceToHost, c->stream));
     if (im) CK(cudaMemcpyAsync(im, c->rho_im[c->cur], b, cudaMemcpyDeviceToHost, c->stream));
@@ -1295,10 +1453,17 @@ tdb_status tdb_get_rho(tdb_ctx* c, double* re, double* im, double* prev_re, doub
     return TDB_OK;
 }
 
+// Reduced forms append their FP32-pair master (both leapfrog levels) and the scale
+// bookkeeping after the FP64 views, so that a resume in the same form is bitwise.
+size_t master_bytes(const tdb_ctx* c) {
+    if (!mixed(*c)) return 0;
+    return 8 * sizeof(float) * (size_t)c->N * c->N + sizeof(tc::DynScales);
+}
+
 size_t tdb_state_bytes(const tdb_ctx* c) {
     if (!c) return 0;
     return sizeof(StateHeader) + 4 * sizeof(double) * (size_t)c->N * c->N +
-           6 * sizeof(double) * c->nat;
+           6 * sizeof(double) * c->nat + master_bytes(c);
 }
 
 tdb_status tdb_get_state(tdb_ctx* c, void* buf, size_t bytes) {
@@ -1307,6 +1472,7 @@ tdb_status tdb_get_state(tdb_ctx* c, void* buf, size_t bytes) {
         set_err("state buffer too small");
         return TDB_ERR_ARG;
     }
+    TRY(materialize(*c));
     DevScalars h{};
     CK(cudaMemcpyAsync(&h, c->sc, sizeof h, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -1338,6 +1504,24 @@ tdb_status tdb_get_state(tdb_ctx* c, void* buf, size_t bytes) {
     p += 4 * b;
     std::memcpy(p, c->R.data(), sizeof(double) * 3 * c->nat);
     std::memcpy(p + sizeof(double) * 3 * c->nat, c->V.data(), sizeof(double) * 3 * c->nat);
+    p += 6 * sizeof(double) * c->nat;
+    if (mixed(*c)) {
+        const size_t fb = sizeof(float) * c->N * c->N;
+        for (int l : {prv, cur}) {
+            const MasterPtrs& m = c->ms[l];
+            for (const float* src : {m.re_hi, m.re_lo, m.im_hi, m.im_lo}) {
+                CK(cudaMemcpyAsync(p, src, fb, cudaMemcpyDeviceToHost, c->stream));
+                p += fb;
+            }
+        }
+        tc::DynScales d{};
+        if (head3(*c)) CK(cudaMemcpyAsync(&d, c->dyn, sizeof d, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        // the maxima of the two levels are stored in (previous, current) order, like the
+        // matrices, so that the blob does not depend on which buffer holds which level
+        if (cur == 0) std::swap(d.max_drho[0], d.max_drho[1]);
+        std::memcpy(p, &d, sizeof d);
+    }
     return TDB_OK;
 }
 
@@ -1384,7 +1568,30 @@ tdb_status tdb_set_state(tdb_ctx* c, const void* buf, size_t bytes) {
     c->euler_next = hd.euler_next != 0;
     c->work = hd.work;
     c->have_gs = true;
-    TRY(refresh_derived(*c));
+    if (mixed(*c) && hd.precision == c->prm.precision) {
+        // same reduced form: the master and the scales continue where they were
+        const char* q = p + 4 * b + 6 * sizeof(double) * c->nat;
+        const size_t fb = sizeof(float) * c->N * c->N;
+        for (int l : {prv, cur}) {
+            const MasterPtrs& m = c->ms[l];
+            for (float* dst : {m.re_hi, m.re_lo, m.im_hi, m.im_lo}) {
+                CK(cudaMemcpyAsync(dst, q, fb, cudaMemcpyHostToDevice, c->stream));
+                q += fb;
+            }
+        }
+        if (head3(*c)) {
+            tc::DynScales d;
+            std::memcpy(&d, q, sizeof d);
+            if (cur == 0) std::swap(d.max_drho[0], d.max_drho[1]);
+            CK(cudaMemcpyAsync(c->dyn, &d, sizeof d, cudaMemcpyHostToDevice, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+        }
+        c->view_valid = true;
+        TRY(derived_from_master(*c, true));
+        CK(cudaStreamSynchronize(c->stream));
+    } else {
+        TRY(refresh_derived(*c));
+    }
     TRY(upload_clock(*c, hd.n, hd.n_base, hd.t_base));
     return TDB_OK;
 }
@@ -1417,7 +1624,14 @@ tdb_status tdb_step_profiled(tdb_ctx* c, double* ms, const char** names, int cap
     }
     StepTimer tm;
     int nl = 0;
-    TRY(enqueue_step(*c, c->cur, c->euler_next, &nl, &tm));
+    if (c->prm.move_nuclei) {
+        // the Ehrenfest step is timed as a whole
+        tm.mark(c->stream, "ehrenfest_step");
+        TRY(enqueue_step_md(*c, c->cur, c->euler_next, &nl));
+        tm.mark(c->stream, "end");
+    } else {
+        TRY(enqueue_step(*c, c->cur, c->euler_next, &nl, &tm));
+    }
     CK(cudaStreamSynchronize(c->stream));
     const int k = std::min<int>(cap, (int)tm.ev.size() - 1);
     for (int i = 0; i < k; ++i) {
@@ -1427,6 +1641,7 @@ tdb_status tdb_step_profiled(tdb_ctx* c, double* ms, const char** names, int cap
         if (names) names[i] = tm.names[i];
     }
     *n_out = k;
+    if (mixed(*c)) c->view_valid = false;
     c->euler_next = false;
     c->cur ^= 1;
     c->n += 1;

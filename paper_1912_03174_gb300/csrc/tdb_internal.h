@@ -53,6 +53,11 @@ struct ModelParams {
     double rep_A, rep_b;
 };
 
+// FP32-pair master of rho - rho_ref (reduced-precision forms), one leapfrog level.
+struct MasterPtrs {
+    float *re_hi, *re_lo, *im_hi, *im_lo;
+};
+
 // A propagation context.  All device pointers point into one workspace.
 struct Ctx {
     int nat = 0, nper = 0, N = 0, nspec = 0, nct = 0;
@@ -88,8 +93,12 @@ struct Ctx {
     float *dv_f = nullptr;                           // [N] v - v_ref per orbital
     float *S_f = nullptr, *Sinv_f = nullptr, *Mgs_f = nullptr, *rref_f = nullptr;
     float *dM_f = nullptr, *M_f = nullptr;           // delta M, M = M_gs + delta M
-    float *dre_f = nullptr, *dim_f = nullptr;        // rho - rho_ref (Re, Im)
     float *Xre_f = nullptr, *Xim_f = nullptr;
+
+    // reduced-precision master (two leapfrog levels) and the FP64 view's state
+    MasterPtrs ms[2] = {};
+    double* qbase = nullptr;     // Mulliken populations of rho_ref (deviation partials add to it)
+    bool view_valid = true;      // FP64 rho_re / rho_im hold the current state
 
     // tensor-core operands (TDB_BF16X3 / TDB_FP16X3 / TDB_FP16X6): 16-bit pieces
     // (2 or 3 per operand), row stride padded to Np = round_up(N, 64)
@@ -99,7 +108,10 @@ struct Ctx {
     uint16_t* pc_am[3] = {};     // N x 2Np    [delta M | M]
     uint16_t* pc_bre[3] = {};    // N x 2Np    [rho_ref | Re(rho - rho_ref)]
     uint16_t* pc_bim[3] = {};    // N x Np     -Im rho
-    float* Xa_f = nullptr;       // delta M rho_ref (FP16X6: its own output block)
+    float* xp[tc::kMaxParts] = {};   // partial products of X (tensor-core forms)
+    // moving nuclei, FP32 form: FP32 copies of S^-1, H or D, rho_n; M or Y; X or Z
+    float *md_sinv = nullptr, *md_b = nullptr, *md_rre = nullptr, *md_rim = nullptr;
+    float *md_m = nullptr, *md_xre = nullptr, *md_xim = nullptr;
     tc::DynScales* dyn = nullptr;
     int* d_err = nullptr;        // bounded-wait time-out / piece overflow flag
     float s_sinv = 1, s_dh = 1, s_m = 1, s_rho = 1, s_ref = 1;   // power-of-two operand scales
@@ -144,7 +156,7 @@ void launch_mulliken_partials(int N, const double* rho_re, const double* S, doub
 // reset0/reset1 (may be null): device doubles zeroed by the kernel
 void launch_charges(const Ctx& c, const double* partial, double* q, double* dq, cudaStream_t st,
                     double* reset0 = nullptr, double* reset1 = nullptr,
-                    tc::DynScales* dyn = nullptr, int cur = 0);
+                    tc::DynScales* dyn = nullptr, int cur = 0, const double* qbase = nullptr);
 // max_dv (may be null): atomicMax of |v - v_ref| over atoms
 void launch_potential(const Ctx& c, const double* gamma, const double* dq, const double* R,
                       DevScalars* sc, double* v_orb, double* v_atom, double* gdq, double* hist,
@@ -152,8 +164,7 @@ void launch_potential(const Ctx& c, const double* gamma, const double* dq, const
                       double* max_dv = nullptr);
 void launch_build_hamiltonian(int N, const double* H0, const double* S, const double* v_orb,
                               double* H, cudaStream_t st);
-// charges + potential of a frozen-nuclei step in one launch (dyn: FP16X6 bookkeeping or null)
-void launch_charges_potential(const Ctx& c, tc::DynScales* dyn, int cur, cudaStream_t st);
+// FP64 leapfrog / Euler update (zre, zim: NAC term of moving nuclei, or null)
 void launch_update(const Ctx& c, const double* Xre, const double* Xim, const double* base_re,
                    const double* base_im, double* out_re, double* out_im, double factor,
                    const double* S, double* partial, DevScalars* sc, cudaStream_t st,
@@ -161,7 +172,6 @@ void launch_update(const Ctx& c, const double* Xre, const double* Xim, const dou
 // Operands written by the update for the next step's products.
 struct UpdateOperands {
     const double* rho_ref = nullptr;   // deviations are taken from this (real) matrix
-    float *f_re = nullptr, *f_im = nullptr;                 // FP32: Re(rho - rho_ref), Im rho
     int scheme = 0;                                         // tc::kHiLo / tc::kHead3 pieces
     uint16_t* re[3] = {};                                   // pieces of s (Re rho - rho_ref)
     uint16_t* im[3] = {};                                   // pieces of -s Im rho
@@ -170,15 +180,11 @@ struct UpdateOperands {
     int bf16 = 0;
     tc::DynScales* dyn = nullptr;      // kHead3: s = pscale(max_drho[cur]); tracks the new max
     int cur = 0;
-    const float* Xre2 = nullptr;       // added to X_re when set
-    const double* zre = nullptr;       // NAC term Z = S^-1 D rho (moving nuclei, FP64 form)
-    const double* zim = nullptr;
+    const float* xre[4] = {};          // X = S^-1 H rho: partial products of Re X ...
+    const float* xim[2] = {};          // ... and of Im X, summed in this order
+    int nre = 0, nim = 0;
     int base_slot = 0;                 // FP16X6: buffer whose max bounds the update's base
 };
-void launch_update_f32(const Ctx& c, const float* Xre, const float* Xim, const double* base_re,
-                       const double* base_im, double* out_re, double* out_im, double factor,
-                       const double* S, double* partial, DevScalars* sc,
-                       const UpdateOperands& ops, cudaStream_t st);
 void launch_kick_phase(int N, int n_per, const double* R, double strength, const double* dir,
                        const double* Pre, const double* Pim, double* Cre, double* Cim,
                        cudaStream_t st);
@@ -196,9 +202,18 @@ void launch_power(const Ctx& c, const double* xre, const double* D, double* part
                   int commit, cudaStream_t st);
 void launch_vel_n(const Ctx& c, const double* F, int first, cudaStream_t st);
 void launch_vv(const Ctx& c, const double* F, cudaStream_t st);
+// reduced-precision master (kern_step.cu)
+void launch_update_df(const Ctx& c, const MasterPtrs& base, const MasterPtrs& out, double factor,
+                      double* partial, DevScalars* sc, const UpdateOperands& ops, cudaStream_t st);
+void launch_view_to_master(const Ctx& c, const double* rre, const double* rim, const MasterPtrs& m,
+                           cudaStream_t st);
+void launch_master_to_view(const Ctx& c, const MasterPtrs& m, double* rre, double* rim,
+                           cudaStream_t st);
+void launch_master_partials(const Ctx& c, const MasterPtrs& m, double* partial, cudaStream_t st);
+void launch_master_absmax(const Ctx& c, const MasterPtrs& m, double* out, cudaStream_t st);
+void launch_master_pieces(const Ctx& c, const MasterPtrs& m, const UpdateOperands& ops,
+                          const double* mx_exact, const float* dev_scale, cudaStream_t st);
 // FP16X6: head pieces of rho - rho_ref (scale from c.dyn->max_drho[slot]) into the B operands
-void launch_split_rho(const Ctx& c, int slot, const double* rre, const double* rim, cudaStream_t st);
-
 // GEMM: C[M x Ncol] = A[M x K] * B[K x Ncol], row-major, FP64 SIMT.
 enum class BKind { Dense = 0, Hamiltonian = 1 };
 void gemm_f64(int M, int Ncol, int K, const double* A, int lda, const double* B, int ldb,

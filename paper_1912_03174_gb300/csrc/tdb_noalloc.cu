@@ -111,7 +111,8 @@ __global__ void k_f32_to_f64(size_t n, const float* __restrict__ in, double* __r
 
 extern "C" tdb_status tdb_split_gemm_noalloc(int M, int N, int K, const double* A, const double* B,
                                              int fmt, double* C, void* stream) {
-    if (M < 1 || N < 1 || K < 1 || !A || !B || !C || fmt < 0 || fmt > 2) {
+    if (M < 1 || N < 1 || K < 1 || !A || !B || !C || fmt < 0 || fmt > 2 ||
+        (fmt == 2 && K > 3 * tdb::tc::kHeadK)) {
         tdb::set_last_error("tdb_split_gemm_noalloc: invalid sizes, pointers or format");
         return TDB_ERR_ARG;
     }

@@ -12,10 +12,12 @@ namespace tc {
 // Piece schemes of an operand x (already multiplied by its power-of-two scale s):
 //  kHiLo  (2 pieces): hi = r16(x), lo = r16(x - hi); products hh + hl + lh, one accumulator.
 //  kHead3 (3 pieces): head = clamp(rint(x), -127, 127) (an integer), r = x - head,
-//          rh = fp16(r), rl = fp16(r - rh); the head*head products (integers) go to an
-//          accumulator whose sums stay exact below 2^24 (K <= 1024), the five products
-//          head*rh, rh*head, rh*rh, head*rl, rl*head to a second one.
+//          rh = fp16(r), rl = fp16(r - rh); the head*head products (integers) go to one
+//          accumulator per 1024-deep slice of K, whose sums stay exact below 2^24, the five
+//          products head*rh, rh*head, rh*rh, head*rl, rl*head to a further one.
 enum Scheme { kHiLo = 3, kHead3 = 6 };
+constexpr int kHeadK = 1024;    // K depth of one exact head accumulator (1040 * 127^2 < 2^24)
+constexpr int kMaxParts = 6;    // output blocks of one launch (grid z)
 
 // One output block of the GEMM: C[M x N] = sum_k A[:, k0_a + k] Bt[:, k0_b + k], k < K,
 // times 1 / (scale_a scale_b); a scale is sa_dev[0] when sa_dev is set, else sa.
@@ -32,7 +34,7 @@ struct GemmPart {
 
 struct GemmParams {
     int M, N;
-    GemmPart part[3];
+    GemmPart part[kMaxParts];
     double* max_out;   // mode 0: atomicMax of |C| per part into max_out[part] (may be null)
     uint32_t idesc;
     int bf16;
@@ -54,7 +56,7 @@ struct Maps {
 };
 
 // Tensor map of a rows x cols row-major 16-bit matrix (row stride ld elements):
-// box 64 (K) x box_rows rows, 128-byte swizzle, zero fill out of bounds.  A operands
+// box 32 (K) x box_rows rows, 64-byte swizzle, zero fill out of bounds.  A operands
 // use 128-row boxes; B operands use boxes of the tile width bn of the launch.
 bool make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int bf16,
               int box_rows = 128);
@@ -62,7 +64,9 @@ uint32_t idesc_f16(int bf16, int bn = 128);
 size_t smem_bytes(int scheme);
 // Once per process and device before the first launch (and outside stream capture).
 cudaError_t prepare();
-// Output tiles of 128 x bn (bn = 64 or 128; the B maps must have bn-row boxes).
+// Output tiles of 128 x bn (bn = 64, 128 or 256; the B maps must have bn-row boxes); nparts <=
+// kMaxParts.  kHead3 needs (ceil(K / kHeadK) + 1) bn <= 512 TMEM columns for every part
+// (cudaErrorInvalidValue otherwise).
 cudaError_t launch(int scheme, const Maps& m, const GemmParams& p, int nparts, cudaStream_t st,
                    int bn = 128);
 
@@ -78,7 +82,7 @@ struct DynScales {
     double max_dv;        // max |v - v_ref| of this step (atomicMax on the bit pattern)
     double max_drho[3];   // max |rho - rho_ref| per density buffer; [2]: the one being written
     double sinv_norm;     // ||S^-1||_inf
-    double max_x[3];      // max |X| of the product outputs of this step (parts 0..2)
+    double max_x[kMaxParts];   // max |X| of each product output of this step
     float s_dh, s_dm, s_rho;
     int pad;
 };
@@ -87,7 +91,7 @@ void launch_split_dham(int scheme, int N, const float* S, const float* dv, float
                        int* err);
 
 // Power-of-two scale mapping a magnitude bound m into (63.5, 127]: the integer heads then
-// use their full 7-bit range and K <= 1040 head products (<= 127^2 each) sum exactly in FP32.
+// use their full 7-bit range and up to 1040 head products (<= 127^2 each) sum exactly in FP32.
 // Every caller passes a rigorous bound (an exact maximum or a norm bound), so no value
 // exceeds the head range.
 __host__ __device__ inline float pscale(double m) {

@@ -20,7 +20,7 @@ float pow2_scale(const std::vector<double>& x, double target) {
 extern "C" tdb_status tdb_split_gemm(int M, int N, int K, const double* A, const double* B, int fmt,
                                      double* C, double* ms) {
     if (M < 1 || N < 1 || K < 1 || !A || !B || !C || fmt < 0 || fmt > 2 || M > 32768 ||
-        N > 32768 || K > 65536)
+        N > 32768 || K > 65536 || (fmt == 2 && K > 3 * tdb::tc::kHeadK))
         return TDB_ERR_ARG;
     const int ldk = (K + 63) / 64 * 64;
     std::vector<double> a(A, A + static_cast<size_t>(M) * K), bt(static_cast<size_t>(N) * K);

@@ -162,6 +162,10 @@ def test_error_paths(B):
     with pytest.raises(B.TdbError) as e:
         B.tdb_create(s2, B.make_params(run))
     assert e.value.status == 1
+    md = I.Run(dt=0.2, n_steps=0, scc=True, move_nuclei=True)
+    with pytest.raises(B.TdbError) as e:      # moving nuclei: FP64 and FP32 forms only
+        B.tdb_create(I.small_cluster(6, seed=1), B.make_params(md, "fp16x6"))
+    assert e.value.status == 10
 
 
 def test_invariant_monitor_flags_a_corrupted_state(B):
@@ -201,9 +205,10 @@ REDUCED = [("fp32", 1e-6, 1e-6), ("fp16x6", 1e-6, 1e-6), ("fp16x3", 1e-5, 1e-5),
 
 
 @pytest.mark.parametrize("form,tol_mu,tol_rho", REDUCED)
-@pytest.mark.parametrize("n_atoms", [10, 33, 64])
+@pytest.mark.parametrize("n_atoms", [10, 33, 64, 130])
 def test_reduced_precision_forms_match_oracle(B, n_atoms, form, tol_mu, tol_rho):
-    # N = 40, 132, 256: one tile, ragged tails (132 is not a multiple of 64), several tiles
+    # N = 40, 132, 256, 520: one tile, ragged tails (132 is not a multiple of 64), several
+    # tiles, 256-wide X tiles with a ragged tail (520 = 2 x 256 + 8)
     sysm = I.small_flake(n_atoms, seed=8)
     run = I.Run(dt=0.2, n_steps=0, scc=True, kick=1e-3, kT=I.SCC_KT)
     n = 500
@@ -215,6 +220,40 @@ def test_reduced_precision_forms_match_oracle(B, n_atoms, form, tol_mu, tol_rho)
     assert np.max(np.abs(g["rho"] - tr.rho)) < tol_rho
     assert abs(g["obs"]["trace_re"] - sysm.n_electrons) / sysm.n_electrons < 1e-8
     assert g["obs"]["herm_err"] == 0.0
+
+
+@pytest.mark.parametrize("form", ["fp32", "fp16x6", "bf16x3"])
+def test_reduced_form_checkpoint_resume_is_bitwise(B, form):
+    # the state of a reduced form carries its FP32-pair master and scale bookkeeping
+    sysm = I.small_flake(33, seed=6)
+    run = I.Run(dt=0.2, n_steps=0, scc=True, kick=1e-3, kT=I.SCC_KT)
+    with B.Propagator(sysm, run, form) as a, B.Propagator(sysm, run, form) as b:
+        a.setup()
+        b.setup()
+        a.step(37)
+        B.tdb_set_state(b.ctx, B.tdb_get_state(a.ctx))
+        a.step(50)
+        b.step(50)
+        assert B.tdb_get_state(a.ctx) == B.tdb_get_state(b.ctx)
+        oa, ob = a.observables(), b.observables()
+        assert np.array_equal(oa["dipole"], ob["dipole"]) and oa["step"] == ob["step"] == 87
+
+
+@pytest.mark.parametrize("form,tol", [("fp16x6", 5e-7), ("fp16x3", 5e-5)])
+def test_reduced_forms_at_n2048_track_the_fp64_form(B, form, tol):
+    # N = 2048 (512-atom flake): the X products run as two K slices of 1024 and delta M
+    # keeps two exact head accumulators; the FP64 form is the reference (it matches the
+    # oracle at N = 1024 and below)
+    sysm = I.small_flake(512, seed=12)
+    run = I.Run(dt=0.2, n_steps=0, scc=True, kick=1e-3, kT=I.SCC_KT)
+    n = 300
+    ref = _gpu_run(B, sysm, run, n, "fp64")
+    g = _gpu_run(B, sysm, run, n, form)
+    err = np.max(np.abs(g["hist"] - ref["hist"]))
+    assert err < tol, err
+    assert np.max(np.abs(g["rho"] - ref["rho"])) < 10 * tol
+    assert g["obs"]["herm_err"] == 0.0
+    assert abs(g["obs"]["trace_re"] - sysm.n_electrons) / sysm.n_electrons < 1e-8
 
 
 def test_exact_head_form_beats_the_hi_lo_forms(B):
@@ -236,8 +275,8 @@ def test_exact_head_form_beats_the_hi_lo_forms(B):
 # moving nuclei (Ehrenfest, eq:forces, eq:nac, velocity Verlet)
 # ---------------------------------------------------------------------------
 
-def _md_gpu(B, sysm, run, n):
-    with B.Propagator(sysm, run, "fp64") as p:
+def _md_gpu(B, sysm, run, n, precision="fp64"):
+    with B.Propagator(sysm, run, precision) as p:
         p.setup()
         p.step(n)
         hist = B.tdb_dipole_history(p.ctx, n)
@@ -270,6 +309,24 @@ def test_ehrenfest_matches_oracle(B, n_atoms, seed, laser):
     assert abs(g["obs"]["E_total"] - tr.energy[-1]) < 1e-9
     assert abs(g["obs"]["work"] - tr.work[-1]) < 1e-10
     assert abs(g["obs"]["trace_re"] - tr.trace[-1].real) < 1e-10
+    assert g["obs"]["herm_err"] == 0.0
+
+
+def test_ehrenfest_fp32_form_tracks_the_oracle(B):
+    # FP32 products (M = S^-1 H, X = M rho, Y = S^-1 D, Z = Y rho) with the FP64
+    # density, forces and update
+    sysm = I.small_cluster(33, seed=7, T=3000.0)
+    run = I.Run(dt=0.2, n_steps=0, scc=True, move_nuclei=True, kick=1e-2, kT=I.SCC_KT)
+    n = 200
+    g = _md_gpu(B, sysm, run, n, "fp32")
+    rho0, gs, S, Sinv = O.setup(sysm, run)
+    tr = O.propagate(sysm, run, rho0, n, keep_forces=True)
+    mu = np.vstack([g["hist"], g["obs"]["dipole"][None, :]])
+    err = dict(mu=np.max(np.abs(mu - tr.dipole)), R=np.max(np.abs(g["R"] - tr.R)),
+               F=np.max(np.abs(g["obs"]["forces"] - tr.forces[-1])),
+               rho=np.max(np.abs(g["rho"] - tr.rho)))
+    assert err["mu"] < 1e-5 and err["R"] < 1e-7 and err["F"] < 1e-4 and err["rho"] < 1e-5, err
+    assert abs(g["obs"]["trace_re"] - tr.trace[-1].real) < 1e-6, err
     assert g["obs"]["herm_err"] == 0.0
 
 

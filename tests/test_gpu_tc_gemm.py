@@ -63,8 +63,10 @@ def test_exact_small_integers(B):
         assert np.array_equal(C, A @ Bm)
 
 
-@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (130, 200, 300), (256, 384, 1024)])
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (130, 200, 300), (256, 384, 1024),
+                                   (200, 136, 2048), (128, 256, 3000)])
 def test_head_scheme_matches_fp64(B, M, N, K):
+    # K > 1024: one exact head accumulator per 1024-deep slice of K
     rng = np.random.default_rng(M + N + K)
     A = rng.normal(size=(M, K)) * np.exp(rng.uniform(-6, 0, size=(M, K)))
     Bm = rng.normal(size=(K, N)) * np.exp(rng.uniform(-6, 0, size=(K, N)))
@@ -75,12 +77,12 @@ def test_head_scheme_matches_fp64(B, M, N, K):
     assert rel < 2.0 ** -20 + 16 * 2.0 ** -24 * np.sqrt(K), rel
 
 
-def test_head_scheme_removes_the_accumulation_bias(B):
+@pytest.mark.parametrize("K", [1024, 2048])
+def test_head_scheme_removes_the_accumulation_bias(B, K):
     # all products positive: the FP32 tensor-core accumulation truncates, so the
     # hi/lo scheme comes out systematically low by ~K 2^-25; the integer heads sum
     # exactly, leaving only the tails' share (~2^-7 of it)
     rng = np.random.default_rng(11)
-    K = 1024
     A = rng.uniform(0, 1, (256, K))
     Bm = rng.uniform(0, 1, (K, 256))
     ref = A @ Bm
@@ -90,3 +92,10 @@ def test_head_scheme_removes_the_accumulation_bias(B):
         bias[fmt] = float(np.mean((C - ref) / ref))
     assert bias[0] < -1e-6, bias              # measured ~ -7e-6 on GB300
     assert abs(bias[2]) < abs(bias[0]) / 20, bias
+
+
+def test_head_scheme_rejects_k_beyond_three_slices(B):
+    A = np.ones((128, 3073))
+    with pytest.raises(B.TdbError) as e:
+        B.tdb_split_gemm(A, A.T.copy(), fmt=2)
+    assert e.value.status == 1
