@@ -162,8 +162,8 @@ def model_pair_gradients(sysm, R):
 
 
 # ---------------------------------------------------------------------------
-# gamma (eq:coul).  The paper leaves the short-range function zeta(R) to
-# "ab initio calculations"; the reading taken here is the standard DFTB form:
+# gamma (eq:coul).  The paper defers the short-range function zeta(R) to
+# first-principles fits; the reading taken here is the standard DFTB form:
 # the Coulomb interaction of two normalised exponential densities
 # n(r) = tau^3/(8 pi) exp(-tau r) with tau = 16 U / 5, so that gamma_AA = U_A.
 # ---------------------------------------------------------------------------
