@@ -216,6 +216,7 @@ __global__ void k_charges(int nat, int nper, int nct, const double* __restrict__
     if (A >= nat) return;
     const double* p = partial + (size_t)A * nper * nct;
     double s = 0.0;
+#pragma unroll 4
     for (int i = lane; i < nper * nct; i += 32) s += p[i];
     s = warp_sum(s);
     if (lane == 0) {
@@ -237,13 +238,21 @@ __global__ void k_potential(int nat, int nper, int scc, const double* __restrict
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarp = blockDim.x >> 5;
     const long long n = sc->step;
-    const double t = sc->t_base + (double)(n - sc->n_base) * sc->dt;
-    double E[3];
-    field_at(sc->field, t, E);
+    // the field at t_n, evaluated once per block
+    __shared__ double E_sh[3];
+    if (threadIdx.x == 0) {
+        const double t = sc->t_base + (double)(n - sc->n_base) * sc->dt;
+        field_at(sc->field, t, E_sh);
+    }
+    __syncthreads();
+    const double E[3] = {E_sh[0], E_sh[1], E_sh[2]};
     for (int A = blockIdx.x * nwarp + warp; A < nat; A += gridDim.x * nwarp) {
         double s = 0.0;
-        if (scc)
-            for (int B = lane; B < nat; B += 32) s += gamma[(size_t)A * nat + B] * dq[B];
+        if (scc) {
+            const double* g = gamma + (size_t)A * nat;
+#pragma unroll 8
+            for (int B = lane; B < nat; B += 32) s += g[B] * dq[B];
+        }
         s = warp_sum(s);
         const double vA = s + R[3 * A] * E[0] + R[3 * A + 1] * E[1] + R[3 * A + 2] * E[2];
         if (lane < nper) {

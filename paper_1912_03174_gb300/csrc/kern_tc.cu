@@ -474,13 +474,18 @@ __global__ void k_split_dham(int N, const float* __restrict__ S, const float* __
         __syncthreads();
         s = s_sh;
     }
-    if (r >= N || c >= N) return;
-    uint16_t q[3];
-    const bool ok = split_value<SCHEME>(0.5f * S[static_cast<size_t>(r) * N + c] * (dv[r] + dv[c]) * s,
-                                        bf16, q);
-    const size_t o = static_cast<size_t>(r) * ld_out + c;
+    if (c >= N) return;
+    // rows r, r + gridDim.y blockDim.y, ...: the scale prologue is paid once per block
+    const float dvc = dv[c];
+    bool ok = true;
+    for (int row = r; row < N; row += gridDim.y * blockDim.y) {
+        uint16_t q[3];
+        ok &= split_value<SCHEME>(0.5f * S[static_cast<size_t>(row) * N + c] * (dv[row] + dvc) * s,
+                                  bf16, q);
+        const size_t o = static_cast<size_t>(row) * ld_out + c;
 #pragma unroll
-    for (int t = 0; t < Cfg<SCHEME>::PIECES; ++t) out.p[t][o] = q[t];
+        for (int t = 0; t < Cfg<SCHEME>::PIECES; ++t) out.p[t][o] = q[t];
+    }
     if (!ok && err) atomicCAS(err, 0, 4);
 }
 
@@ -585,7 +590,8 @@ void launch_split_dham(int scheme, int N, const float* S, const float* dv, float
                        uint16_t* const* pieces, int ld_out, DynScales* dyn, cudaStream_t st,
                        int* err) {
     dim3 b(32, 8);
-    dim3 g((N + 31) / 32, (N + 7) / 8);
+    // about 8 rows per thread
+    dim3 g((N + 31) / 32, (N + 63) / 64);
     Pieces o{{pieces[0], pieces[1], scheme == kHead3 ? pieces[2] : nullptr}};
     if (scheme == kHiLo)
         k_split_dham<kHiLo><<<g, b, 0, st>>>(N, S, dv, scale, bf16, o, ld_out, nullptr, err);
