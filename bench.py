@@ -194,7 +194,7 @@ def n2048_runs(B, torch, flush, stream, reduced_steps):
     out = {"frozen": {"workload": "SCC frozen-nuclei hexagonal flake, 512 atoms (N=2048), "
                                   "kick 1e-3 a.u. along x, dt=0.2 a.u.", "forms": {}}}
     res = {}
-    for f, k in (("fp64", 20), ("fp16x3", reduced_steps), ("fp16x6", reduced_steps)):
+    for f, k in (("fp64", 20), ("fp64s", 60), ("fp16x3", reduced_steps), ("fp16x6", reduced_steps)):
         res[f] = run_form(B, torch, sysm, run, f, k, 3, flush, stream)
     n64 = len(res["fp64"]["hist"])
     for f, r in res.items():
@@ -203,15 +203,15 @@ def n2048_runs(B, torch, flush, stream, reduced_steps):
             "max_dipole_err_vs_fp64_au": float(np.max(np.abs(r["hist"][:n64] - res["fp64"]["hist"]))),
             "compared_steps": n64}
     sysm3, run3 = I.cluster_c3()
-    r3 = {f: run_form(B, torch, sysm3, run3, f, 5, 3, flush, stream) for f in ("fp64", "fp32")}
+    r3 = {f: run_form(B, torch, sysm3, run3, f, 5, 3, flush, stream) for f in ("fp64", "fp64s", "fp32")}
     out["ehrenfest_c3"] = {
         "workload": "Ehrenfest cluster, 512 atoms (N=2048), 300 K, Gaussian laser E0=0.01 "
                     "omega=0.1, dt=0.2 a.u.",
         "forms": {f: {"steps_per_s": 1000.0 / float(np.mean(r["ms"])), "timed_steps": len(r["ms"]),
                       "max_dipole_err_vs_fp64_au": float(np.max(np.abs(r["hist"] - r3["fp64"]["hist"])))}
                   for f, r in r3.items()},
-        "note": "moving nuclei run in the FP64 form and the FP32 form (FP32 products, FP64 "
-                "density, forces and update)"}
+        "note": "moving nuclei run in the FP64, FP64-sliced (integer-slice tensor-core products) "
+                "and FP32 forms; density, forces and update in FP64"}
     return out
 
 
@@ -274,7 +274,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--forms", default="fp64,fp32,bf16x3,fp16x3,fp16x6")
+    ap.add_argument("--forms", default="fp64,fp64s,fp32,bf16x3,fp16x3,fp16x6")
     ap.add_argument("--atoms", type=int, default=256)
     ap.add_argument("--cpu-steps", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -366,8 +366,8 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "bf16x3",
-                                       "fp16x3": "fp16x3", "fp16x6": "fp16x6"}[head],
+        "vs_baseline": None, "dtype": {"fp64": "f64", "fp64s": "f64 (int7x6 slices)", "fp32": "f32",
+                                       "bf16x3": "bf16x3", "fp16x3": "fp16x3", "fp16x6": "fp16x6"}[head],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": N, "precision": head, "parallelism": "replicas",
                    "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)",

@@ -65,10 +65,14 @@ typedef enum {
     TDB_FP16X3 = 3,   /* tcgen05 tensor cores, power-of-two scaled FP16 hi/lo pieces
                          (~22 bits), 3 products, FP32 accumulate, on rho - rho_gs.
                          Requires |v - v_gs| < 16 Ha for every atom potential. */
-    TDB_FP16X6 = 4    /* tcgen05 tensor cores, each operand = 7-bit integer head + two FP16
+    TDB_FP16X6 = 4,   /* tcgen05 tensor cores, each operand = 7-bit integer head + two FP16
                          tails (~29 bits) under per-step power-of-two scales; the head
                          products accumulate exactly (integer sums below 2^24), the five
                          tail products in a second FP32 accumulator; on rho - rho_gs */
+    TDB_FP64_SLICED = 5 /* FP64-accurate products on the tcgen05 tensor cores: rows of A and
+                         columns of B cut into six 7-bit integer slices under power-of-two
+                         scales, every slice product summed exactly (see tdb_slice_gemm);
+                         FP64 density and update; frozen or moving nuclei; N <= 4096 */
 } tdb_precision;
 
 /* The system (geometry and synthetic two-centre model).  Radial integrals:
@@ -211,6 +215,19 @@ tdb_status tdb_step_profiled(tdb_ctx* ctx, double* ms, const char** names, int c
  * ms (may be NULL): kernel time.
  * TDB_ERR_TIMEOUT if a bounded device wait expired. */
 tdb_status tdb_split_gemm(int M, int N, int K, const double* A, const double* B, int fmt, double* C,
+                          double* ms);
+
+/* C = A B with FP64-accurate integer-slice products on the tensor cores (the
+ * TDB_FP64_SLICED form; no context needed, allocates and frees its own device
+ * buffers).  A: M x K, B: K x N, C: M x N, row-major host doubles, K <= 4096.
+ * Each row of A (column of B) is scaled by a power of two into (-1, 1) and cut
+ * into six signed 7-bit integer slices (FP16 values); the 21 slice pairs with
+ * s + t < 6 are multiplied on the FP16 tensor cores, pairs of equal weight summed
+ * exactly over 512-deep K chunks (integers below 2^24 in FP32), chunks and weights
+ * combined exactly in 64-bit integers.  Error below about 7 2^-42 K max_k|A_ik|
+ * max_k|B_kj|.  ms (may be NULL): kernel time.  TDB_ERR_ARG for bad sizes;
+ * TDB_ERR_TIMEOUT if a bounded device wait expired. */
+tdb_status tdb_slice_gemm(int M, int N, int K, const double* A, const double* B, double* C,
                           double* ms);
 
 /* The same product as tdb_split_gemm, for callers that cannot allocate device

@@ -15,9 +15,9 @@ import numpy as np
 
 from . import build as _build
 
-TDB_FP64, TDB_FP32, TDB_BF16X3, TDB_FP16X3, TDB_FP16X6 = 0, 1, 2, 3, 4
+TDB_FP64, TDB_FP32, TDB_BF16X3, TDB_FP16X3, TDB_FP16X6, TDB_FP64_SLICED = 0, 1, 2, 3, 4, 5
 PRECISIONS = {"fp64": TDB_FP64, "fp32": TDB_FP32, "bf16x3": TDB_BF16X3, "fp16x3": TDB_FP16X3,
-              "fp16x6": TDB_FP16X6}
+              "fp16x6": TDB_FP16X6, "fp64s": TDB_FP64_SLICED}
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -78,6 +78,7 @@ SIGNATURES = {
     "tdb_step_profiled": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_char_p), ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int)]),
     "tdb_split_gemm": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_int, _dp, _dp]),
+    "tdb_slice_gemm": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]),
     "tdb_split_gemm_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "tdb_destroy": (None, [ctypes.c_void_p]),
@@ -309,6 +310,19 @@ def tdb_split_gemm(A, B, fmt=0):
     C = np.zeros((M, N))
     ms = ctypes.c_double()
     _check("tdb_split_gemm", load().tdb_split_gemm(M, N, K, _ptr(A), _ptr(B), int(fmt), _ptr(C), ctypes.byref(ms)))
+    return C, ms.value
+
+
+def tdb_slice_gemm(A, B):
+    """C = A @ B with FP64-accurate integer-slice tensor-core products; returns (C, kernel ms)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2
+    C = np.zeros((M, N))
+    ms = ctypes.c_double()
+    _check("tdb_slice_gemm", load().tdb_slice_gemm(M, N, K, _ptr(A), _ptr(B), _ptr(C), ctypes.byref(ms)))
     return C, ms.value
 
 

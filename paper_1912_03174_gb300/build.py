@@ -43,7 +43,7 @@ def _sources():
 def _stamp(srcs) -> str:
     h = hashlib.sha256()
     for p in srcs + [os.path.join(INCLUDE, "tdb.h")] + sorted(
-            os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")):
+            os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))):
         with open(p, "rb") as fh:
             h.update(p.encode() + fh.read())
     h.update(" ".join(NVCC_FLAGS).encode())

@@ -99,14 +99,18 @@ struct Carver {
     }
 };
 
-// Frozen-nuclei reduced forms (FP32-pair master of rho - rho_ref).
-bool mixed(const Ctx& c) { return c.prm.precision != TDB_FP64 && !c.prm.move_nuclei; }
-// Moving nuclei with FP32 products (FP64 density, forces and update).
-bool md32(const Ctx& c) { return c.prm.move_nuclei && c.prm.precision == TDB_FP32; }
 bool tensor(const Ctx& c) {
     return c.prm.precision == TDB_BF16X3 || c.prm.precision == TDB_FP16X3 ||
            c.prm.precision == TDB_FP16X6;
 }
+// Frozen-nuclei reduced forms (FP32-pair master of rho - rho_ref).
+bool mixed(const Ctx& c) {
+    return (c.prm.precision == TDB_FP32 || tensor(c)) && !c.prm.move_nuclei;
+}
+// Moving nuclei with FP32 products (FP64 density, forces and update).
+bool md32(const Ctx& c) { return c.prm.move_nuclei && c.prm.precision == TDB_FP32; }
+// FP64-accurate integer-slice products (FP64 density and update), any nuclei.
+bool sliced(const Ctx& c) { return c.prm.precision == TDB_FP64_SLICED; }
 bool head3(const Ctx& c) { return c.prm.precision == TDB_FP16X6; }
 // The tensor-core X products (dM rho_ref, M Re(rho - rho_ref), M Im rho) are cut into
 // this many K slices with their own FP32 outputs, so that a slice of K <= 1024 keeps one
@@ -168,6 +172,11 @@ size_t carve(Ctx& c, char* base) {
     if (mixed(c)) {
         c.dv_f = k.take<float>(N);
         c.S_f = k.take<float>(NN);
+    }
+    if (sliced(c)) {
+        // slices of S^-1 (A), H or D (B), M or Y (A), Re rho and Im rho (B)
+        for (int q = 0; q < 5; ++q) c.oz_raw[q] = k.take<char>(oz::sliced_bytes(N, N));
+        c.oz_colmax = k.take<double>(N);
     }
     if (md32(c)) {
         c.md_sinv = k.take<float>(NN);
@@ -241,12 +250,17 @@ tdb_status validate(const tdb_system* s, const tdb_params* p) {
         }
     if (!(std::isfinite(p->dt)) || p->dt == 0.0 || p->window < 1 || p->history_cap < 1 ||
         p->scc_max_iter < 1 || !(p->scc_mix > 0 && p->scc_mix <= 1) || p->kT < 0 ||
-        p->precision < 0 || p->precision > 4) {
+        p->precision < 0 || p->precision > 5) {
         set_err("invalid params");
         return TDB_ERR_ARG;
     }
-    if (p->move_nuclei && p->precision != TDB_FP64 && p->precision != TDB_FP32) {
-        set_err("moving nuclei run in the FP64 and FP32 forms only in this build");
+    if (p->move_nuclei && p->precision != TDB_FP64 && p->precision != TDB_FP32 &&
+        p->precision != TDB_FP64_SLICED) {
+        set_err("moving nuclei run in the FP64, FP64_SLICED and FP32 forms only in this build");
+        return TDB_ERR_UNSUPPORTED;
+    }
+    if (p->precision == TDB_FP64_SLICED && N > oz::kMaxK) {
+        set_err("TDB_FP64_SLICED supports N <= 4096 in this build");
         return TDB_ERR_UNSUPPORTED;
     }
     if (p->precision == TDB_FP16X6 && N > 2048) {
@@ -654,6 +668,29 @@ tdb_status md_model(Ctx& c) {
     return enqueue_inverse(c);
 }
 
+// Sliced-form products: out = A B with A, B given through their slices (0: S^-1,
+// 1: H or D, 2: M or Y, 3: Re rho, 4: Im rho).
+tdb_status oz_product(Ctx& c, int a, int b, double* out) {
+    oz::Part part;
+    part.b = &c.oz[b];
+    part.C = out;
+    part.ldc = c.N;
+    CK(oz::gemm(c.oz[a], &part, 1, c.d_err, c.stream));
+    return TDB_OK;
+}
+// re = A Re rho, im = A Im rho in one launch
+tdb_status oz_product_rho(Ctx& c, int a, double* re, double* im) {
+    oz::Part parts[2];
+    parts[0].b = &c.oz[3];
+    parts[0].C = re;
+    parts[0].ldc = c.N;
+    parts[1].b = &c.oz[4];
+    parts[1].C = im;
+    parts[1].ldc = c.N;
+    CK(oz::gemm(c.oz[a], parts, 2, c.d_err, c.stream));
+    return TDB_OK;
+}
+
 // Everything of a moving-nuclei step up to the work rate, for rho_n in buffer cur
 // (Sec. 2.3 with the ordering: S_n, S^-1_n; q(rho_n), H_n; X_n; F_n; V_n; D_n; P_n).
 // commit = 1 inside a step (the work integral advances), 0 for observables.
@@ -663,7 +700,19 @@ tdb_status md_forces(Ctx& c, int cur, bool first, int commit, int* n) {
     launch_charges(c, c.partial, c.q, c.dq, c.stream);
     launch_potential(c, c.gamma, c.dq, c.d_R, c.sc, c.v_orb, c.v_atom, c.gdq, c.hist, c.v_ref,
                      nullptr, c.stream);
-    if (md32(c)) {
+    if (sliced(c)) {
+        // M = S^-1 H and X = M rho_n with integer-slice products (S^-1 sliced per step)
+        const int N = c.N;
+        launch_build_hamiltonian(N, c.H0, c.S, c.v_orb, c.Hs, c.stream);
+        oz::slice_rows(c.Sinv, N, 1.0, c.oz[0], c.stream);
+        oz::slice_rows(c.Hs, N, 1.0, c.oz[1], c.stream);          // H symmetric
+        TRY(oz_product(c, 0, 1, c.M));
+        oz::slice_rows(c.M, N, 1.0, c.oz[2], c.stream);
+        oz::slice_rows(c.rho_re[cur], N, 1.0, c.oz[3], c.stream);  // Re rho symmetric
+        oz::slice_rows(c.rho_im[cur], N, -1.0, c.oz[4], c.stream); // (Im rho)^T = -Im rho
+        TRY(oz_product_rho(c, 2, c.Xre, c.Xim));
+        if (n) *n += 5;
+    } else if (md32(c)) {
         // M = S^-1 H and X = M rho_n with FP32 operands and FFMA accumulation
         const int N = c.N;
         const size_t NN = (size_t)N * N;
@@ -699,7 +748,14 @@ tdb_status enqueue_step_md(Ctx& c, int cur, bool euler, int* launches) {
     const int prv = cur ^ 1;
     int n = 0;
     TRY(md_forces(c, cur, euler, 1, &n));
-    if (md32(c)) {
+    if (sliced(c)) {
+        // Y = S^-1 D (D is not symmetric: column slices) and Z = Y rho_n
+        oz::slice_cols(c.D, c.N, c.oz[1], c.oz_colmax, c.stream);
+        TRY(oz_product(c, 0, 1, c.M));
+        oz::slice_rows(c.M, c.N, 1.0, c.oz[2], c.stream);
+        TRY(oz_product_rho(c, 2, c.Zre, c.Zim));
+        n += 2;
+    } else if (md32(c)) {
         // Y = S^-1 D and Z = Y rho_n in FP32 (the FP32 copies of S^-1 and rho_n are current)
         const int N = c.N;
         const size_t NN = (size_t)N * N;
@@ -760,7 +816,25 @@ tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* t
     launch_potential(c, c.gamma, c.dq, c.d_R, c.sc, c.v_orb, c.v_atom, c.gdq, c.hist, c.v_ref,
                      mixed(c) ? c.dv_f : nullptr, c.stream, head3(c) ? &c.dyn->max_dv : nullptr);
     ++n;
-    if (c.prm.precision == TDB_FP64) {
+    if (sliced(c)) {
+        const int N = c.N;
+        MARK("slice_H");
+        launch_build_hamiltonian(N, c.H0, c.S, c.v_orb, c.Hs, c.stream);
+        oz::slice_rows(c.Hs, N, 1.0, c.oz[1], c.stream);
+        MARK("oz_gemm_M");
+        TRY(oz_product(c, 0, 1, c.M));                          // M = S^-1 H
+        MARK("slice_M_rho");
+        oz::slice_rows(c.M, N, 1.0, c.oz[2], c.stream);
+        oz::slice_rows(c.rho_re[cur], N, 1.0, c.oz[3], c.stream);
+        oz::slice_rows(c.rho_im[cur], N, -1.0, c.oz[4], c.stream);
+        MARK("oz_gemm_X");
+        TRY(oz_product_rho(c, 2, c.Xre, c.Xim));                // X = M rho
+        n += 7;
+        MARK("update");
+        launch_update(c, c.Xre, c.Xim, bre, bim, c.rho_re[prv], c.rho_im[prv], factor, c.S,
+                      c.partial, c.sc, c.stream);
+        ++n;
+    } else if (c.prm.precision == TDB_FP64) {
         MARK("gemm_M_f64");
         gemm_f64_ham(c.N, c.Sinv, c.H0, c.S, c.v_orb, c.M, c.stream);  // M = S^-1 H
         MARK("gemm_Xre_f64");
@@ -1111,6 +1185,18 @@ tdb_status tdb_create(const tdb_system* sys, const tdb_params* prm, void* worksp
     if (tensor(*c)) {
         s = build_maps(*c);
         if (s != TDB_OK) return fail(s);
+    }
+    if (sliced(*c)) {
+        const int N = c->N;
+        bool ok = oz::prepare() == cudaSuccess;
+        for (int q = 0; q < 5 && ok; ++q)
+            ok = oz::sliced_init(c->oz[q], c->oz_raw[q], N, N, q == 0 || q == 2 ? 128 : 64);
+        if (!ok) {
+            set_err("integer-slice GEMM setup failed");
+            return fail(TDB_ERR_CUDA);
+        }
+        // frozen nuclei: S^-1 is sliced once
+        if (!c->prm.move_nuclei) oz::slice_rows(c->Sinv, N, 1.0, c->oz[0], c->stream);
     }
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
         set_err("setup failed: %s", cudaGetErrorString(cudaGetLastError()));

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "tdb.h"
+#include "tdb_oz.h"
 #include "tdb_tc.h"
 
 namespace tdb {
@@ -109,6 +110,10 @@ struct Ctx {
     uint16_t* pc_bre[3] = {};    // N x 2Np    [rho_ref | Re(rho - rho_ref)]
     uint16_t* pc_bim[3] = {};    // N x Np     -Im rho
     float* xp[tc::kMaxParts] = {};   // partial products of X (tensor-core forms)
+    // FP64_SLICED form: slices of S^-1, H or D, M or Y, Re rho, Im rho
+    oz::Sliced oz[5];
+    char* oz_raw[5] = {};
+    double* oz_colmax = nullptr;
     // moving nuclei, FP32 form: FP32 copies of S^-1, H or D, rho_n; M or Y; X or Z
     float *md_sinv = nullptr, *md_b = nullptr, *md_rre = nullptr, *md_rim = nullptr;
     float *md_m = nullptr, *md_xre = nullptr, *md_xim = nullptr;

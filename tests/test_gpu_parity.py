@@ -163,7 +163,7 @@ def test_error_paths(B):
         B.tdb_create(s2, B.make_params(run))
     assert e.value.status == 1
     md = I.Run(dt=0.2, n_steps=0, scc=True, move_nuclei=True)
-    with pytest.raises(B.TdbError) as e:      # moving nuclei: FP64 and FP32 forms only
+    with pytest.raises(B.TdbError) as e:      # moving nuclei: FP64, FP64_SLICED and FP32 only
         B.tdb_create(I.small_cluster(6, seed=1), B.make_params(md, "fp16x6"))
     assert e.value.status == 10
 
@@ -200,8 +200,10 @@ def test_c2_flake_full_size_prefix_fp64(B):
 
 
 # reduced-precision forms: (form, dipole tolerance in a.u., rho tolerance)
+# fp64s: integer-slice products carry ~7 2^-42 K max|M| max|rho| per product, which over
+# 500 steps reaches a few 1e-9 in the dipole (the FP64 form stays at ~1e-12)
 REDUCED = [("fp32", 1e-6, 1e-6), ("fp16x6", 1e-6, 1e-6), ("fp16x3", 1e-5, 1e-5),
-           ("bf16x3", 2e-5, 2e-5)]
+           ("bf16x3", 2e-5, 2e-5), ("fp64s", 2e-8, 2e-8)]
 
 
 @pytest.mark.parametrize("form,tol_mu,tol_rho", REDUCED)
@@ -309,6 +311,26 @@ def test_ehrenfest_matches_oracle(B, n_atoms, seed, laser):
     assert abs(g["obs"]["E_total"] - tr.energy[-1]) < 1e-9
     assert abs(g["obs"]["work"] - tr.work[-1]) < 1e-10
     assert abs(g["obs"]["trace_re"] - tr.trace[-1].real) < 1e-10
+    assert g["obs"]["herm_err"] == 0.0
+
+
+@pytest.mark.parametrize("n_atoms,seed,laser", [(12, 5, True), (33, 7, False)])
+def test_ehrenfest_fp64_sliced_form_matches_oracle(B, n_atoms, seed, laser):
+    # integer-slice products (S^-1 H, M rho, S^-1 D, Y rho), FP64 everything else
+    sysm = I.small_cluster(n_atoms, seed=seed, T=3000.0)
+    fld = I.Field(E0=0.01, omega=0.1, phase=0.2, t_center=20.0, fwhm=20.0, envelope=1) if laser else None
+    run = I.Run(dt=0.2, n_steps=0, scc=True, move_nuclei=True, kick=1e-2 if not laser else 0.0,
+                field=fld, kT=I.SCC_KT)
+    n = 200
+    g = _md_gpu(B, sysm, run, n, "fp64s")
+    rho0, gs, S, Sinv = O.setup(sysm, run)
+    tr = O.propagate(sysm, run, rho0, n, keep_forces=True)
+    mu = np.vstack([g["hist"], g["obs"]["dipole"][None, :]])
+    err = dict(mu=np.max(np.abs(mu - tr.dipole)), R=np.max(np.abs(g["R"] - tr.R)),
+               F=np.max(np.abs(g["obs"]["forces"] - tr.forces[-1])),
+               rho=np.max(np.abs(g["rho"] - tr.rho)))
+    assert err["mu"] < 1e-8 and err["R"] < 1e-9 and err["F"] < 1e-8 and err["rho"] < 1e-8, err
+    assert abs(g["obs"]["work"] - tr.work[-1]) < 1e-9, err
     assert g["obs"]["herm_err"] == 0.0
 
 

@@ -99,3 +99,49 @@ def test_head_scheme_rejects_k_beyond_three_slices(B):
     with pytest.raises(B.TdbError) as e:
         B.tdb_split_gemm(A, A.T.copy(), fmt=2)
     assert e.value.status == 1
+
+
+# ---------------------------------------------------------------------------
+# integer-slice product (TDB_FP64_SLICED): six 7-bit slices, exact accumulation
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("M,N,K", [(128, 64, 32), (130, 200, 300), (256, 384, 1024),
+                                   (200, 136, 2048), (64, 100, 4096)])
+def test_slice_gemm_is_fp64_accurate(B, M, N, K):
+    rng = np.random.default_rng(3 * M + 5 * N + K)
+    A = rng.normal(size=(M, K)) * np.exp(rng.uniform(-6, 0, size=(M, K)))
+    Bm = rng.normal(size=(K, N)) * np.exp(rng.uniform(-6, 0, size=(K, N)))
+    C, _ = B.tdb_slice_gemm(A, Bm)
+    ref = A @ Bm
+    # the slices keep 42 bits of each entry relative to its row (A) or column (B)
+    # maximum; the kept pairs leave out terms below 7 2^-42 of those maxima
+    bound = K * np.max(np.abs(A), axis=1)[:, None] * np.max(np.abs(Bm), axis=0)[None, :]
+    assert np.all(np.abs(C - ref) <= 2.0 ** -38 * bound), np.max(np.abs(C - ref) / bound)
+    rel = np.max(np.abs(C - ref) / (np.abs(A) @ np.abs(Bm)))
+    assert rel < 1e-9, rel
+
+
+def test_slice_gemm_is_exact_on_integers_and_powers_of_two(B):
+    rng = np.random.default_rng(5)
+    A = rng.integers(-64, 65, size=(150, 520)).astype(float)
+    Bm = rng.integers(-64, 65, size=(520, 90)).astype(float) * 2.0 ** -20
+    C, _ = B.tdb_slice_gemm(A, Bm)
+    assert np.array_equal(C, A @ Bm)
+
+
+def test_slice_gemm_has_no_accumulation_bias(B):
+    # the all-positive product whose FP32 tensor-core accumulation comes out low
+    rng = np.random.default_rng(11)
+    A = rng.uniform(0, 1, (256, 2048))
+    Bm = rng.uniform(0, 1, (2048, 256))
+    C, _ = B.tdb_slice_gemm(A, Bm)
+    ref = A @ Bm
+    assert np.max(np.abs(C - ref) / ref) < 1e-11
+    assert abs(float(np.mean((C - ref) / ref))) < 1e-13
+
+
+def test_slice_gemm_rejects_k_beyond_4096(B):
+    A = np.ones((64, 4097))
+    with pytest.raises(B.TdbError) as e:
+        B.tdb_slice_gemm(A, A.T.copy())
+    assert e.value.status == 1
