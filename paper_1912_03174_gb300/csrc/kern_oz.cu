@@ -183,15 +183,40 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-// Slices of one value already scaled into (-64, 64): rint digits in base 128.  y - rint(y)
-// and the multiplication by 128 are exact, so the digits reproduce y to 2^(6 - 7 kSlices).
-__device__ __forceinline__ void put_slices(double y, uint16_t* const* s, size_t o) {
-#pragma unroll
-    for (int q = 0; q < kSlices; ++q) {
-        const double d = rint(y);
-        s[q][o] = __half_as_ushort(__double2half(d));
-        y = (y - d) * 128.0;
+// frexp exponent of a normal m > 0 (m = f 2^e, f in [0.5, 1)) from its bits
+__device__ __forceinline__ int exponent_of(double m) {
+    return static_cast<int>((__double_as_longlong(m) >> 52) & 0x7ff) - 1022;
+}
+// 2^k for -1022 <= k <= 1023 from its bits
+__device__ __forceinline__ double pow2(int k) {
+    return __longlong_as_double(static_cast<long long>(k + 1023) << 52);
+}
+// Exponent e of a row (column) maximum m and the scale 2^(41 - e) that maps the row onto
+// 41-bit integers; maxima below 2^-900 count as zero rows (all slices 0).
+__device__ __forceinline__ void row_scale(double m, int& e, double& scale41) {
+    if (m < 0x1p-900) {
+        e = 0;
+        scale41 = 0.0;
+    } else {
+        e = exponent_of(m);
+        scale41 = pow2(41 - e);
     }
+}
+
+// Slices of x: v = round(x 2^(41 - e)) (|v| <= 2^41, one rounding), written in balanced
+// base-128 digits from the bottom (|d| <= 64 each; the top one is <= 64 because
+// |x| 2^-e < 1).  Integer arithmetic only, so the FP64 pipe does one multiply and one
+// conversion per value.
+__device__ __forceinline__ void put_slices(double x, double scale41, uint16_t* const* s,
+                                           size_t o) {
+    long long v = __double2ll_rn(x * scale41);
+#pragma unroll
+    for (int q = kSlices - 1; q > 0; --q) {
+        const long long r = ((v + 64) & 127) - 64;
+        s[q][o] = __half_as_ushort(__int2half_rn(static_cast<int>(r)));
+        v = (v - r) >> 7;
+    }
+    s[0][o] = __half_as_ushort(__int2half_rn(static_cast<int>(v)));
 }
 
 struct SlicePtrs {
@@ -209,21 +234,22 @@ __global__ void k_slice_rows(const double* __restrict__ A, int lda, int K, doubl
     for (int k = threadIdx.x; k < K; k += blockDim.x) m = fmax(m, fabs(a[k]));
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     __shared__ double red[32];
-    __shared__ int e_sh;
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
     __syncthreads();
+    __shared__ double sc_sh;
     if (threadIdx.x == 0) {
         double mm = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmax(mm, red[w]);
-        int e = 0;
-        if (mm > 0.0) frexp(mm, &e);   // mm = f 2^e, f in [0.5, 1): |x| 2^-e < 1
-        e_sh = e;
+        int e;
+        double sc;
+        row_scale(mm, e, sc);
+        sc_sh = sign * sc;
         out.e[row] = e;
     }
     __syncthreads();
-    const int sh = 6 - e_sh;
+    const double sc = sc_sh;
     for (int k = threadIdx.x; k < K; k += blockDim.x)
-        put_slices(ldexp(sign * a[k], sh), out.s, static_cast<size_t>(row) * out.ld + k);
+        put_slices(a[k], sc, out.s, static_cast<size_t>(row) * out.ld + k);
 }
 
 // Column maxima |B| (colmax starts at zero): 32 columns x 8 row groups per block.
@@ -260,11 +286,11 @@ __global__ void k_slice_cols(const double* __restrict__ B, int ldb, int K, int c
     for (int i = 0; i < 4; ++i) {
         const int n = c0 + threadIdx.y + 8 * i, k = k0 + threadIdx.x;
         if (n >= cols || k >= K) continue;
-        int e = 0;
-        const double m = colmax[n];
-        if (m > 0.0) frexp(m, &e);
+        int e;
+        double sc;
+        row_scale(colmax[n], e, sc);
         if (k == 0) out.e[n] = e;
-        put_slices(ldexp(t[threadIdx.x][threadIdx.y + 8 * i], 6 - e), out.s,
+        put_slices(t[threadIdx.x][threadIdx.y + 8 * i], sc, out.s,
                    static_cast<size_t>(n) * out.ld + k);
     }
 }
