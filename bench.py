@@ -208,7 +208,8 @@ def n2048_runs(B, torch, flush, stream, reduced_steps):
         "workload": "Ehrenfest cluster, 512 atoms (N=2048), 300 K, Gaussian laser E0=0.01 "
                     "omega=0.1, dt=0.2 a.u.",
         "forms": {f: {"steps_per_s": 1000.0 / float(np.mean(r["ms"])), "timed_steps": len(r["ms"]),
-                      "max_dipole_err_vs_fp64_au": float(np.max(np.abs(r["hist"] - r3["fp64"]["hist"])))}
+                      "max_dipole_err_vs_fp64_au": float(np.max(np.abs(r["hist"] - r3["fp64"]["hist"]))),
+                      "phase_ms": r["prof"]}
                   for f, r in r3.items()},
         "note": "moving nuclei run in the FP64, FP64-sliced (integer-slice tensor-core products) "
                 "and FP32 forms; density, forces and update in FP64"}

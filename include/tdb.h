@@ -200,7 +200,9 @@ long tdb_last_launch_count(const tdb_ctx* ctx);
  * CUDA event recorded on the context stream before each kernel; synchronises.
  * ms[i] = device time of kernel i (milliseconds), names[i] = a static string
  * naming it (names may be NULL); *n_out = kernels timed (<= cap).  With moving
- * nuclei the whole Ehrenfest step is one entry ("ehrenfest_step"). */
+ * nuclei the entries are the phases of the Ehrenfest step (model and S^-1, charges
+ * and potential, products X, forces, NAC and power, products Z, update and velocity
+ * Verlet). */
 tdb_status tdb_step_profiled(tdb_ctx* ctx, double* ms, const char** names, int cap, int* n_out);
 
 /* C = A B through the tensor-core split-precision GEMM on its own, for

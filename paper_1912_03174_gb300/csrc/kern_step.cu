@@ -638,6 +638,16 @@ __global__ void k_f64_to_f32(size_t n, const double* __restrict__ in, float* __r
         out[i] = (float)in[i];
 }
 
+// Newton-Schulz step for the inverse of S: X <- 2 X - 1/2 (Q + Q^T) with Q = X S X and X
+// symmetric (the symmetric part keeps the iterate exactly symmetric).
+__global__ void k_ns_update(int N, double* __restrict__ X, const double* __restrict__ Q) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    if (r >= N || c >= N) return;
+    const size_t i = (size_t)r * N + c, j = (size_t)c * N + r;
+    X[i] = 2.0 * X[i] - 0.5 * (Q[i] + Q[j]);
+}
+
 __global__ void k_f32_to_f64(size_t n, const float* __restrict__ in, double* __restrict__ out) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x)
@@ -713,6 +723,11 @@ __global__ void k_absmax(size_t n, const double* __restrict__ x, const double* _
 
 void launch_absmax(size_t n, const double* x, double* out, cudaStream_t st, const double* sub) {
     k_absmax<<<608, 256, 0, st>>>(n, x, sub, out);
+}
+
+void launch_ns_update(int N, double* X, const double* Q, cudaStream_t st) {
+    dim3 b(32, 8);
+    k_ns_update<<<grid2(N, N, b), b, 0, st>>>(N, X, Q);
 }
 
 void launch_f32_to_f64(size_t n, const float* in, double* out, cudaStream_t st) {

@@ -18,6 +18,7 @@ void gemm_f32_add(int M, int Ncol, int K, const float* A, int lda, const float* 
                   float* C, int ldc, const float* Cadd, cudaStream_t st);
 void launch_f64_to_f32(size_t n, const double* in, float* out, cudaStream_t st);
 void launch_f32_to_f64(size_t n, const float* in, double* out, cudaStream_t st);
+void launch_ns_update(int N, double* X, const double* Q, cudaStream_t st);
 void gemm_f32(int M, int Ncol, int K, const float* A, int lda, const float* B, int ldb, float* C,
               int ldc, cudaStream_t st);
 void launch_add_f32_strided(int N, const float* a, const float* b, int ldb, float* out, int ldo,
@@ -660,13 +661,56 @@ tdb_status enqueue_inverse(Ctx& c) {
     return TDB_OK;
 }
 
-// S, H0, gamma and S^-1 at the current device geometry (moving nuclei).
-tdb_status md_model(Ctx& c) {
+tdb_status oz_product(Ctx& c, int a, int b, double* out);
+
+// S^-1 at a new geometry from the inverse at the previous one (FP64_SLICED form):
+// Newton-Schulz steps X <- 2 X - X S X with integer-slice products.  They converge
+// quadratically while ||1 - S X|| < 1; between two steps the nuclei move by ~1e-4 bohr,
+// so the start is within ~1e-5 and two steps reach the products' precision.
+tdb_status ns_inverse(Ctx& c) {
+    const int N = c.N;
+    oz::slice_rows(c.S, N, 1.0, c.oz[2], c.stream);                 // A = S
+    for (int it = 0; it < 2; ++it) {
+        oz::slice_rows(c.Sinv, N, 1.0, c.oz[1], c.stream);          // B = X (symmetric)
+        TRY(oz_product(c, 2, 1, c.M));                              // P = S X
+        oz::slice_rows(c.Sinv, N, 1.0, c.oz[0], c.stream);          // A = X
+        oz::slice_cols(c.M, N, c.oz[1], c.oz_colmax, c.stream);     // B = P
+        TRY(oz_product(c, 0, 1, c.Hs));                             // Q = X P
+        launch_ns_update(N, c.Sinv, c.Hs, c.stream);
+    }
+    CKL();
+    return TDB_OK;
+}
+
+// S, H0, gamma and S^-1 at the current device geometry (moving nuclei).  Inside a step
+// of the FP64_SLICED form S^-1 follows from the previous one (ns_inverse); otherwise
+// (and after a ground state, kick or checkpoint load) it is factorised anew.
+tdb_status md_model(Ctx& c, bool in_step = false) {
     launch_build_model(c, c.d_R, c.S, c.H0, c.stream);
     launch_build_gamma(c, c.d_R, c.gamma, c.stream);
     CKL();
+    if (in_step && sliced(c)) return ns_inverse(c);
     return enqueue_inverse(c);
 }
+
+// Optional per-kernel timing of an enqueued step: an event before each launch.
+struct StepTimer {
+    std::vector<cudaEvent_t> ev;
+    std::vector<const char*> names;
+    void mark(cudaStream_t st, const char* name) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        cudaEventRecord(e, st);
+        ev.push_back(e);
+        names.push_back(name);
+    }
+    ~StepTimer() {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
+};
+
+#define MARK(name) \
+    if (tm) tm->mark(c.stream, name)
 
 // Sliced-form products: out = A B with A, B given through their slices (0: S^-1,
 // 1: H or D, 2: M or Y, 3: Re rho, 4: Im rho).
@@ -694,12 +738,15 @@ tdb_status oz_product_rho(Ctx& c, int a, double* re, double* im) {
 // Everything of a moving-nuclei step up to the work rate, for rho_n in buffer cur
 // (Sec. 2.3 with the ordering: S_n, S^-1_n; q(rho_n), H_n; X_n; F_n; V_n; D_n; P_n).
 // commit = 1 inside a step (the work integral advances), 0 for observables.
-tdb_status md_forces(Ctx& c, int cur, bool first, int commit, int* n) {
-    TRY(md_model(c));
+tdb_status md_forces(Ctx& c, int cur, bool first, int commit, int* n, StepTimer* tm = nullptr) {
+    MARK("md_model_inverse");
+    TRY(md_model(c, true));
+    MARK("md_charges_potential");
     launch_mulliken_partials(c.N, c.rho_re[cur], c.S, c.partial, c.stream);
     launch_charges(c, c.partial, c.q, c.dq, c.stream);
     launch_potential(c, c.gamma, c.dq, c.d_R, c.sc, c.v_orb, c.v_atom, c.gdq, c.hist, c.v_ref,
                      nullptr, c.stream);
+    MARK("md_products_X");
     if (sliced(c)) {
         // M = S^-1 H and X = M rho_n with integer-slice products (S^-1 sliced per step)
         const int N = c.N;
@@ -732,9 +779,11 @@ tdb_status md_forces(Ctx& c, int cur, bool first, int commit, int* n) {
         gemm_f64(c.N, c.N, c.N, c.M, c.N, c.rho_re[cur], c.N, c.Xre, c.N, c.stream);
         gemm_f64(c.N, c.N, c.N, c.M, c.N, c.rho_im[cur], c.N, c.Xim, c.N, c.stream);
     }
+    MARK("md_forces");
     launch_wre(c.N, c.Xre, c.Wre, c.stream);
     launch_forces(c, c.rho_re[cur], c.Wre, c.d_F, c.stream);
     launch_vel_n(c, c.d_F, first ? 1 : 0, c.stream);
+    MARK("md_nac_power");
     launch_build_nac(c, c.d_Vn, c.D, c.stream);
     launch_power(c, c.Xre, c.D, c.pw_part, kObsBlocks, first ? 1 : 0, commit, c.stream);
     CKL();
@@ -744,10 +793,11 @@ tdb_status md_forces(Ctx& c, int cur, bool first, int commit, int* n) {
 
 // One moving-nuclei step: forces as above, then Z = S^-1 D rho, the update with the
 // NAC term, and velocity Verlet for the nuclei.
-tdb_status enqueue_step_md(Ctx& c, int cur, bool euler, int* launches) {
+tdb_status enqueue_step_md(Ctx& c, int cur, bool euler, int* launches, StepTimer* tm = nullptr) {
     const int prv = cur ^ 1;
     int n = 0;
-    TRY(md_forces(c, cur, euler, 1, &n));
+    TRY(md_forces(c, cur, euler, 1, &n, tm));
+    MARK("md_products_Z");
     if (sliced(c)) {
         // Y = S^-1 D (D is not symmetric: column slices) and Z = Y rho_n
         oz::slice_cols(c.D, c.N, c.oz[1], c.oz_colmax, c.stream);
@@ -774,32 +824,15 @@ tdb_status enqueue_step_md(Ctx& c, int cur, bool euler, int* launches) {
     const double factor = euler ? c.prm.dt : 2.0 * c.prm.dt;
     const double* bre = euler ? c.rho_re[cur] : c.rho_re[prv];
     const double* bim = euler ? c.rho_im[cur] : c.rho_im[prv];
+    MARK("md_update_verlet");
     launch_update(c, c.Xre, c.Xim, bre, bim, c.rho_re[prv], c.rho_im[prv], factor, c.S, c.partial,
                   c.sc, c.stream, c.Zre, c.Zim);
     launch_vv(c, c.d_F, c.stream);
+    MARK("end");
     CKL();
     if (launches) *launches = n + 5;
     return TDB_OK;
 }
-
-// Optional per-kernel timing of an enqueued step: an event before each launch.
-struct StepTimer {
-    std::vector<cudaEvent_t> ev;
-    std::vector<const char*> names;
-    void mark(cudaStream_t st, const char* name) {
-        cudaEvent_t e;
-        cudaEventCreate(&e);
-        cudaEventRecord(e, st);
-        ev.push_back(e);
-        names.push_back(name);
-    }
-    ~StepTimer() {
-        for (auto e : ev) cudaEventDestroy(e);
-    }
-};
-
-#define MARK(name) \
-    if (tm) tm->mark(c.stream, name)
 
 // Enqueue one propagation step for rho_n in buffer `cur` (eq:leapfrog, eq:eomrho).
 tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* tm = nullptr) {
@@ -1711,10 +1744,7 @@ tdb_status tdb_step_profiled(tdb_ctx* c, double* ms, const char** names, int cap
     StepTimer tm;
     int nl = 0;
     if (c->prm.move_nuclei) {
-        // the Ehrenfest step is timed as a whole
-        tm.mark(c->stream, "ehrenfest_step");
-        TRY(enqueue_step_md(*c, c->cur, c->euler_next, &nl));
-        tm.mark(c->stream, "end");
+        TRY(enqueue_step_md(*c, c->cur, c->euler_next, &nl, &tm));
     } else {
         TRY(enqueue_step(*c, c->cur, c->euler_next, &nl, &tm));
     }
