@@ -84,12 +84,13 @@ __global__ void k_forces(int nat, int nper, int scc, const double* __restrict__ 
                          const double* __restrict__ v_atom, const double* __restrict__ dq,
                          const double* __restrict__ U, ModelParams mp,
                          const DevScalars* __restrict__ sc, double* __restrict__ F) {
-    const int lane = threadIdx.x & 31;
-    const int A = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (A >= nat) return;
+    // one block per atom A, its threads over the partners B (FP64 throughout: enough
+    // blocks and threads to keep the FP64 pipes of all SMs busy)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int A = blockIdx.x;
     const int N = nat * nper;
     double f[3] = {0.0, 0.0, 0.0};
-    for (int B = lane; B < nat; B += 32) {
+    for (int B = threadIdx.x; B < nat; B += blockDim.x) {
         if (B == A) continue;
         const double d[3] = {R[3 * B] - R[3 * A], R[3 * B + 1] - R[3 * A + 1],
                              R[3 * B + 2] - R[3 * A + 2]};
@@ -121,8 +122,17 @@ __global__ void k_forces(int nat, int nper, int scc, const double* __restrict__ 
         }
     }
     for (int q = 0; q < 3; ++q) f[q] = warp_sum_d(f[q]);
+    __shared__ double red[3][32];
     if (lane == 0)
-        for (int q = 0; q < 3; ++q) F[3 * A + q] = f[q] - dq[A] * sc->E[q];
+        for (int q = 0; q < 3; ++q) red[q][warp] = f[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 3; ++q) {
+            double t = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[q][w];
+            F[3 * A + q] = t - dq[A] * sc->E[q];
+        }
+    }
 }
 
 // Re W = 1/2 (Re X + Re X^T) through a shared-memory tile transpose.
@@ -228,8 +238,8 @@ __global__ void k_vv(int nat, const double* __restrict__ Vn, const double* __res
 }  // namespace
 
 void launch_forces(const Ctx& c, const double* rre, const double* wre, double* F, cudaStream_t st) {
-    k_forces<<<(c.nat + 7) / 8, 256, 0, st>>>(c.nat, c.nper, c.prm.scc, c.d_R, rre, wre, c.v_atom,
-                                              c.dq, c.d_U, c.mp, c.sc, F);
+    k_forces<<<c.nat, 128, 0, st>>>(c.nat, c.nper, c.prm.scc, c.d_R, rre, wre, c.v_atom, c.dq,
+                                    c.d_U, c.mp, c.sc, F);
 }
 
 void launch_wre(int N, const double* xre, double* wre, cudaStream_t st) {
