@@ -39,9 +39,12 @@ KERNEL_FLOPS = {
     "gemm_dM_f32": lambda N: 2 * N ** 3,
     "gemm_Xre_f32": lambda N: 4 * N ** 3,
     "gemm_Xim_f32": lambda N: 2 * N ** 3,
-    # tensor-core split GEMMs: algorithmic flops (the three split products execute 3x this)
+    # tensor-core split GEMMs: algorithmic flops (the split products execute 3x or 6x this)
     "tc_gemm_dM": lambda N: 2 * N ** 3,
     "tc_gemm_X": lambda N: 6 * N ** 3,
+    # integer-slice products (21 slice products each)
+    "oz_gemm_M": lambda N: 2 * N ** 3,
+    "oz_gemm_X": lambda N: 4 * N ** 3,
 }
 # algorithmic bytes per launch of the O(N^2) kernels
 KERNEL_BYTES = {
@@ -64,11 +67,17 @@ KERNEL_BYTES = {
 # one ncu capture of the bench workload (summaries under profiles/).  An entry holds while
 # the kernel's source file is byte-identical to the one captured (sha256); otherwise the
 # bench reports traffic as null.
-PROFILED_TRAFFIC: dict = {}
+PROFILED_TRAFFIC: dict = {
+    # profiles/fp16x6_step_N1024_traffic.md (ncu, c2 N = 1024, mean of two launches)
+    ("tc_gemm_X", "fp16x6"): {"bytes": 31529728, "source": "paper_1912_03174_gb300/csrc/kern_tc.cu",
+                  "sha256": "538667eeb27d567d18bd01c5216799484ef5496d5e3d2774687f9a9799a0379b"},
+    ("update", "fp16x6"): {"bytes": 33608576, "source": "paper_1912_03174_gb300/csrc/kern_step.cu",
+               "sha256": "93c3c3c6bea09cf6594b9ecf821b197aa5f4a6a823fc60d644a4bdcebfa7a9eb"},
+}
 
 
-def _traffic(name: str):
-    e = PROFILED_TRAFFIC.get(name)
+def _traffic(name: str, form: str):
+    e = PROFILED_TRAFFIC.get((name, form))
     if not e:
         return None
     import hashlib
@@ -216,6 +225,62 @@ def n2048_runs(B, torch, flush, stream, reduced_steps):
     return out
 
 
+def c4_runs(B, torch, n_traj, post_steps, form="fp16x6"):
+    """Batched pump-probe scan (probe runs branched from pump runs, Sec. 3.2): four
+    flakes (N = 128..1024), each probe a clone of its size's pump run at its delay tau
+    (rounded to the step grid), kicked 1e-3 a.u. along x.  Pump runs, branching and
+    graph capture are untimed; timed: every probe advancing post_steps steps, batched
+    across the probes' streams (tdb_step_batch) and, for comparison, one probe after
+    another (tdb_step).  Both are bracketed by device-wide synchronisation (the probes
+    run on many streams) and timed by the host clock."""
+    import dataclasses
+    from paper_1912_03174_gb300 import inputs as I
+    systems, run, which, tau = I.pump_probe_c4(n_traj=n_traj)
+    pump_run = dataclasses.replace(run, kick=0.0)
+    probes = []
+    pump_steps = 0
+    for s_idx, sysm in enumerate(systems):
+        idx = np.where(which == s_idx)[0]
+        if len(idx) == 0:
+            continue
+        steps = np.rint(tau[idx] / run.dt).astype(np.int64)
+        with B.Propagator(sysm, pump_run, form) as p:
+            p.setup()
+            at = 0
+            for st in np.sort(steps):
+                B.tdb_step(p.ctx, int(st - at))
+                at = int(st)
+                c = B.tdb_clone(p.ctx)
+                B.tdb_kick(c, run.kick, run.kick_dir)
+                probes.append(c)
+            pump_steps += at
+    try:
+        B.tdb_step_batch(probes, 2)                     # Euler step + graph capture
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.tdb_step_batch(probes, post_steps)
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for c in probes:
+            B.tdb_step(c, post_steps)
+            torch.cuda.synchronize()
+        t_seq = time.perf_counter() - t0
+    finally:
+        for c in probes:
+            B.tdb_destroy(c)
+    units = len(probes) * post_steps
+    return {"workload": f"pump-probe scan: {len(probes)} probe runs over flakes of "
+                        f"{'/'.join(str(s.n_atoms) for s in systems)} atoms (N = 128..1024), "
+                        f"laser pump E0=0.01 omega=0.1, probe kick 1e-3 at tau ~ U(0, 200 fs), "
+                        f"dt=0.2, {post_steps} post-kick steps timed per probe",
+            "precision": form, "probes": len(probes), "pump_steps_untimed": int(pump_steps),
+            "trajectory_steps_per_s_batched": units / t_batch,
+            "trajectory_steps_per_s_one_by_one": units / t_seq,
+            "batch_speedup": t_seq / t_batch,
+            "timing": "host clock between device-wide synchronisations"}
+
+
 def e2e_run(B, sysm, run, precision, steps, warmup):
     """End to end through the public API: per step the field is set from the host
     (H2D), one step runs, and the observables with charges are read back (D2H)."""
@@ -281,6 +346,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-n2048", action="store_true")
+    ap.add_argument("--c4-probes", type=int, default=64, help="pump-probe scan size (0: skip)")
+    ap.add_argument("--c4-steps", type=int, default=200, help="timed post-kick steps per probe")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -317,6 +384,9 @@ def main():
         n2048 = None
         if not args.no_n2048:
             n2048 = n2048_runs(B, torch, flush, stream, min(args.steps, 200))
+        c4 = None
+        if args.c4_probes > 0:
+            c4 = c4_runs(B, torch, args.c4_probes, args.c4_steps)
         if dist:
             dist.barrier()
     clocks = clk.summary()
@@ -339,12 +409,12 @@ def main():
     peaks, src = _peaks()
     N = sysm.n_orb
     sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
-    if name.startswith("tc_gemm"):
+    if name.startswith(("tc_gemm", "oz_gemm")):
         ach = KERNEL_FLOPS[name](N) / (t_ms * 1e-3) / 1e12
         peak = peaks["bf16_tflops"]
-        products = {"bf16x3": 3, "fp16x3": 3, "fp16x6": 6}.get(head, 3)
+        products = {"bf16x3": 3, "fp16x3": 3, "fp16x6": 6, "fp64s": 21}.get(head, 3)
         roof = {"kernel": name, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": _traffic(name),
+                "frac": ach / peak, "traffic": _traffic(name, head),
                 "peak_source": f"{src} dense bf16 burst (fp16 runs at the same rate)",
                 "executed_tflops": products * ach, "executed_frac": products * ach / peak,
                 "note": f"achieved counts algorithmic flops; the split form executes {products} "
@@ -363,7 +433,7 @@ def main():
             key = "split_dH_fp16x6" if head == "fp16x6" else "split_dH"
         ach = KERNEL_BYTES[key](N) / (t_ms * 1e-3) / 1e9
         roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": _traffic(name), "peak_source": src}
+                "frac": ach / peaks["hbm_gbs"], "traffic": _traffic(name, head), "peak_source": src}
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -380,7 +450,8 @@ def main():
                                                                if "fp64" in res else None)}
                              for f in forms},
                    "kernel_ms": {f: res[f]["prof"] for f in forms},
-                   "n2048": n2048},
+                   "n2048": n2048,
+                   "pump_probe_c4": c4},
         "roofline": roof,
         "gpu_launches": int(r["launches"]),
         "clocks": clocks,

@@ -169,6 +169,26 @@ tdb_status tdb_set_field(tdb_ctx* ctx, const tdb_field* field);
 /* Advance n >= 0 leapfrog steps (asynchronous on the context stream). */
 tdb_status tdb_step(tdb_ctx* ctx, long n);
 
+/* A new context in the state of src (after its ground state): same system,
+ * parameters and precision form, its own device workspace (workspace as in
+ * tdb_create, or NULL) and stream (cuda_stream, or NULL for a new one); the
+ * device state is copied device to device, so a branch costs no ground state and
+ * no host round trip.  Stepping the clone reproduces stepping src bit for bit.
+ * This is how a probe run branches from a pump run at delay tau (Sec. 3.2):
+ * step the pump to tau, clone, kick the clone. */
+tdb_status tdb_clone(tdb_ctx* src, void* cuda_stream, void* workspace, size_t workspace_bytes,
+                     tdb_ctx** out);
+
+/* Advance each of count independent contexts (trajectories) by n >= 0 steps,
+ * enqueued step by step across them so that their streams run side by side on the
+ * GPU: the probe runs of a pump-probe scan (Sec. 3.2) branch from pump snapshots
+ * (tdb_set_state + tdb_kick) and are independent of one another.  Each context
+ * should have a stream of its own (params.cuda_stream NULL, or distinct streams);
+ * contexts that share a stream are stepped correctly but one after another.
+ * Asynchronous like tdb_step.  On an error in context i at step k the contexts
+ * before i have made k + 1 steps, the others k; the message names i and k. */
+tdb_status tdb_step_batch(tdb_ctx* const* ctxs, int count, long n);
+
 /* Observables of the current rho_n (synchronises).  charges: [n_atoms] Mulliken
  * populations q_A or NULL; forces: [n_atoms][3] Ehrenfest forces (eq:forces,
  * velocity terms dropped) or NULL. */

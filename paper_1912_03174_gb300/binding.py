@@ -67,6 +67,9 @@ SIGNATURES = {
     "tdb_kick": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, _dp]),
     "tdb_set_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(TdbField)]),
     "tdb_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_long]),
+    "tdb_clone": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                  ctypes.POINTER(ctypes.c_void_p)]),
+    "tdb_step_batch": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_long]),
     "tdb_observables": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(TdbObs), _dp, _dp]),
     "tdb_dipole_history": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.c_long, ctypes.POINTER(ctypes.c_long)]),
     "tdb_get_rho": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp, _dp, _dp]),
@@ -233,6 +236,20 @@ def tdb_set_field(ctx: Context, fld):
 
 def tdb_step(ctx: Context, n: int):
     _check("tdb_step", load().tdb_step(ctx.handle, int(n)))
+
+
+def tdb_clone(ctx: Context, stream=None) -> Context:
+    """A new context in ctx's current state (device-to-device copy), with its own stream."""
+    h = ctypes.c_void_p()
+    _check("tdb_clone", load().tdb_clone(ctx.handle, stream, None, 0, ctypes.byref(h)))
+    return Context(handle=h, n_atoms=ctx.n_atoms, n_orb=ctx.n_orb)
+
+
+def tdb_step_batch(ctxs, n: int):
+    """Advance independent contexts by n steps each, interleaved across their streams."""
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.handle.value if isinstance(c.handle, ctypes.c_void_p)
+                                          else c.handle for c in ctxs])
+    _check("tdb_step_batch", load().tdb_step_batch(arr, len(ctxs), int(n)))
 
 
 def tdb_observables(ctx: Context, charges=True, forces=False):

@@ -1,12 +1,13 @@
 // Integer-slice GEMM on the tcgen05 tensor cores (see tdb_oz.h for the arithmetic).
 //
 // Data path per 128 x 64 output tile: TMA loads the kSlices slices of A and of B^T for
-// a 32-deep K block into a 3-stage shared-memory ring; one thread issues the 21 MMAs
-// (pairs s + t < kSlices) of each 16-deep step into kSlices TMEM accumulators, one per
-// weight w = s + t; after every kChunk of K the eight drain warps move the (exact,
-// integer-valued) accumulators into 64-bit integer sums in registers and hand the TMEM
-// back; the last drain writes FP64 C with the row and column scales.  All waits are
-// bounded; a time-out records an error code and the kernel frees its TMEM and returns.
+// a 32-deep K block into a 3-stage shared-memory ring; one thread issues the 21 slice
+// products (pairs s + t < kSlices) of each 16-deep step as 8 MMAs of N <= 256 into
+// kSlices TMEM accumulators, one per weight w = s + t; after every kChunk of K the
+// eight drain warps move the (exact, integer-valued) accumulators into 64-bit integer
+// sums in registers and hand the TMEM back; the last drain writes FP64 C with the row
+// and column scales.  All waits are bounded; a time-out records an error code and the
+// kernel frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_fp16.h>
 
@@ -48,7 +49,7 @@ struct Params {
     double* C[2];
     int ldc[2];
     int* err;
-    uint32_t idesc;
+    uint32_t idesc[5];   // [nb]: instruction descriptor of an N = 64 nb product
 };
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -123,14 +124,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                         a[q] = sdesc(st + q * A_TILE + k * 32);
                         b[q] = sdesc(st + kSlices * A_TILE + q * B_TILE + k * 32);
                     }
-                    // pair (sa, tb) into the accumulator of weight sa + tb; the sa = 0 pairs of
-                    // a chunk's first step start every accumulator afresh
+                    // pair (sa, tb) into the accumulator of weight sa + tb.  The B slices lie
+                    // one after another in shared memory and the accumulators by weight in
+                    // TMEM, so one MMA of N = 64 nb takes the pairs (sa, tb .. tb + nb - 1)
+                    // into the accumulators sa + tb .. sa + tb + nb - 1: 8 MMAs (N <= 256)
+                    // instead of 21.  The sa = 0 products of a chunk's first step cover every
+                    // accumulator and start them afresh.
 #pragma unroll
                     for (int sa = 0; sa < kSlices; ++sa)
 #pragma unroll
-                        for (int tb = 0; sa + tb < kSlices; ++tb)
+                        for (int tb = 0; sa + tb < kSlices; tb += 4) {
+                            const int nb = kSlices - sa - tb < 4 ? kSlices - sa - tb : 4;
                             mma_f16(tmem + static_cast<uint32_t>((sa + tb) * BN), a[sa], b[tb],
-                                    p.idesc, (first && k == 0 && sa == 0) ? 0u : 1u);
+                                    p.idesc[nb], (first && k == 0 && sa == 0) ? 0u : 1u);
+                        }
                 }
                 mma_commit(empty0 + 8 * s);
                 if ((kb % kChunkKB) == kChunkKB - 1 || kb == nkb - 1) mma_commit(cfull);
@@ -362,7 +369,7 @@ cudaError_t gemm(const Sliced& a, const Part* parts, int nparts, int* err, cudaS
     p.K = a.K;
     p.ea = a.e;
     p.err = err;
-    p.idesc = tc::idesc_f16(0, BN);
+    for (int nb = 1; nb <= 4; ++nb) p.idesc[nb] = tc::idesc_f16(0, nb * BN);
     dim3 grid((N + BN - 1) / BN, (a.rows + BM - 1) / BM, nparts);
     k_oz_gemm<<<grid, kThreads, SMEM, st>>>(m, p);
     return cudaGetLastError();

@@ -1118,6 +1118,7 @@ tdb_status tdb_create(const tdb_system* sys, const tdb_params* prm, void* worksp
     if (!c) return TDB_ERR_NOMEM;
     fill_host(*c, sys, prm);
     const size_t need = carve(*c, nullptr);
+    c->ws_need = need;
     auto fail = [&](tdb_status s) {
         tdb_destroy(c);
         return s;
@@ -1419,46 +1420,147 @@ tdb_status tdb_set_field(tdb_ctx* c, const tdb_field* f) {
     return TDB_OK;
 }
 
-tdb_status tdb_step(tdb_ctx* c, long n) {
+}  // extern "C"
+
+namespace {
+
+// State and stability checks before a context steps.
+tdb_status step_checks(tdb_ctx* c) {
     TRY(check_ctx(c, true, false));
-    if (n < 0) {
-        set_err("negative step count");
-        return TDB_ERR_ARG;
-    }
     if (std::fabs(c->prm.dt) * c->spectral_width >= 0.9) {
         set_err("dt * spectral width = %.3f >= 0.9: leapfrog unstable",
                 std::fabs(c->prm.dt) * c->spectral_width);
         return TDB_ERR_UNSTABLE;
     }
-    long launches = 0;
+    return TDB_OK;
+}
+
+// Enqueue one step of c on its stream: the captured graph of its leapfrog parity, or
+// the kernels themselves for an Euler step and for moving nuclei.
+tdb_status step_one(tdb_ctx* c, long* launches) {
+    int nl = 0;
     if (c->prm.move_nuclei) {
-        for (long k = 0; k < n; ++k) {
-            int nl = 0;
-            TRY(enqueue_step_md(*c, c->cur, c->euler_next, &nl));
-            launches += nl;
-            c->euler_next = false;
-            c->cur ^= 1;
-            c->n += 1;
-        }
-        c->last_launches = launches;
-        return TDB_OK;
+        TRY(enqueue_step_md(*c, c->cur, c->euler_next, &nl));
+    } else if (c->euler_next) {
+        TRY(enqueue_step(*c, c->cur, true, &nl));
+    } else {
+        TRY(ensure_graph(*c, c->cur));
+        CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
+        nl = c->graph_launches;
     }
-    for (long k = 0; k < n; ++k) {
-        if (c->euler_next) {
-            int nl = 0;
-            TRY(enqueue_step(*c, c->cur, true, &nl));
-            launches += nl;
-            c->euler_next = false;
-        } else {
-            TRY(ensure_graph(*c, c->cur));
-            CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
-            launches += c->graph_launches;
-        }
-        c->cur ^= 1;
-        c->n += 1;
+    *launches += nl;
+    c->euler_next = false;
+    c->cur ^= 1;
+    c->n += 1;
+    if (mixed(*c)) c->view_valid = false;
+    return TDB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tdb_status tdb_step(tdb_ctx* c, long n) {
+    TRY(step_checks(c));
+    if (n < 0) {
+        set_err("negative step count");
+        return TDB_ERR_ARG;
     }
-    if (mixed(*c) && n > 0) c->view_valid = false;
+    long launches = 0;
+    for (long k = 0; k < n; ++k) TRY(step_one(c, &launches));
     c->last_launches = launches;
+    return TDB_OK;
+}
+
+tdb_status tdb_clone(tdb_ctx* src, void* cuda_stream, void* workspace, size_t workspace_bytes,
+                     tdb_ctx** out) {
+    TRY(check_ctx(src, true, false));
+    if (!out) {
+        set_err("NULL out");
+        return TDB_ERR_ARG;
+    }
+    *out = nullptr;
+    // the same system and parameters, from the host copies the source keeps
+    tdb_system sys{};
+    sys.n_atoms = src->nat;
+    sys.orbs_per_atom = src->nper;
+    sys.n_species = src->nspec;
+    sys.species = src->species.data();
+    sys.R = src->R.data();
+    sys.V = src->V.data();
+    sys.eps_s = src->eps_s.data();
+    sys.eps_p = src->eps_p.data();
+    sys.hubbard_U = src->U.data();
+    sys.mass = src->mass.data();
+    sys.t0 = src->mp.t0;
+    sys.lam_H = src->mp.lam_H;
+    sys.s0 = src->mp.s0;
+    sys.lam_S = src->mp.lam_S;
+    for (int k = 0; k < 4; ++k) sys.eta[k] = src->mp.eta[k];
+    sys.rep_A = src->mp.rep_A;
+    sys.rep_b = src->mp.rep_b;
+    sys.n_electrons = src->n_electrons;
+    tdb_params prm = src->prm;
+    prm.cuda_stream = cuda_stream;
+    TRY(tdb_create(&sys, &prm, workspace, workspace_bytes, out));
+    tdb_ctx* c = *out;
+    // the device state is the workspace (same layout: no device pointers inside it)
+    tdb_status rc = TDB_OK;
+    if (c->ws_need != src->ws_need || cudaStreamSynchronize(src->stream) != cudaSuccess ||
+        cudaMemcpyAsync(c->ws, src->ws, src->ws_need, cudaMemcpyDeviceToDevice, c->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        set_err("tdb_clone: copy of the device state failed");
+        rc = TDB_ERR_CUDA;
+    }
+    if (rc != TDB_OK) {
+        tdb_destroy(c);
+        *out = nullptr;
+        return rc;
+    }
+    // host-side state
+    c->R = src->R;
+    c->V = src->V;
+    c->s_sinv = src->s_sinv;
+    c->s_dh = src->s_dh;
+    c->s_m = src->s_m;
+    c->s_rho = src->s_rho;
+    c->s_ref = src->s_ref;
+    c->view_valid = src->view_valid;
+    c->cur = src->cur;
+    c->have_gs = src->have_gs;
+    c->euler_next = src->euler_next;
+    c->n = src->n;
+    c->spectral_width = src->spectral_width;
+    c->work = src->work;
+    c->field = src->field;
+    c->field_on = src->field_on;
+    return TDB_OK;
+}
+
+tdb_status tdb_step_batch(tdb_ctx* const* ctxs, int count, long n) {
+    if (!ctxs || count < 1 || n < 0) {
+        set_err("tdb_step_batch: need count >= 1 contexts and n >= 0");
+        return TDB_ERR_ARG;
+    }
+    for (int i = 0; i < count; ++i) {
+        const tdb_status st = step_checks(ctxs[i]);
+        if (st != TDB_OK) {
+            set_err("tdb_step_batch: context %d: %s", i, g_err.c_str());
+            return st;
+        }
+    }
+    std::vector<long> launches(count, 0);
+    // step by step across the contexts, so that their streams run side by side
+    for (long k = 0; k < n; ++k)
+        for (int i = 0; i < count; ++i) {
+            const tdb_status st = step_one(ctxs[i], &launches[i]);
+            if (st != TDB_OK) {
+                set_err("tdb_step_batch: context %d, step %ld: %s", i, k, g_err.c_str());
+                return st;
+            }
+        }
+    for (int i = 0; i < count; ++i) ctxs[i]->last_launches = launches[i];
     return TDB_OK;
 }
 

@@ -72,6 +72,7 @@ struct Ctx {
     bool own_stream = false;
     void* ws = nullptr;
     size_t ws_bytes = 0;
+    size_t ws_need = 0;          // bytes of ws the layout uses
     bool own_ws = false;
 
     // device arrays (FP64)

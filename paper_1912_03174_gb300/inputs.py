@@ -229,6 +229,29 @@ def cluster_c3(seed: int = 1003, n_atoms: int = 512):
     return sysm, run
 
 
+def pump_probe_c4(seed: int = 1004, n_traj: int = 256, sizes=(32, 64, 128, 256)):
+    """Batched pump-probe scan: four flakes by the flake rule (32/64/128/256 atoms,
+    N = 128..1024), SCC, frozen nuclei, dt = 0.2; the pump is the c3 laser (Gaussian,
+    E0 = 0.01, omega = 0.1 Ha, FWHM 10 fs centred at 20 fs, along x), the probe a
+    1e-3 a.u. kick along x at delay tau; each of n_traj trajectories draws a size
+    uniformly and tau ~ U(0, 200 fs); 5000 post-kick steps.  Returns (systems, run,
+    size index per trajectory, tau in a.u. per trajectory); run.kick is the probe
+    strength (applied at tau, not at t = 0)."""
+    rng = np.random.default_rng(seed)
+    systems = []
+    for k, n in enumerate(sizes):
+        R = hex_flake(n, 2.68, 0.02, rng)
+        eps_s, eps_p, U, mass = _species_params(rng, 1, scc=True)
+        systems.append(System(f"flake{n}", R, np.zeros(n, np.int32), eps_s, eps_p, U, mass,
+                              n_electrons=4.0 * n))
+    fwhm = 10.0 * FS
+    fld = Field(E0=0.01, omega=0.1, phase=0.0, t_center=2.0 * fwhm, fwhm=fwhm, envelope=1)
+    run = Run(dt=0.2, n_steps=5000, scc=True, kick=1e-3, field=fld, kT=SCC_KT)
+    which = rng.integers(0, len(sizes), n_traj)
+    tau = rng.uniform(0.0, 200.0 * FS, n_traj)
+    return systems, run, which, tau
+
+
 def small_flake(n_atoms: int, seed: int, scc: bool = True, jitter: float = 0.02, n_species: int = 1):
     """A flake built by the flake rule at any size (tests: several tiles plus a ragged tail)."""
     rng = np.random.default_rng(seed)
