@@ -52,12 +52,18 @@ struct Cfg<kHead3> {
 };
 
 // Accumulators of a K-deep product: kHead3 one exact head accumulator per kHeadK slice
-// plus the tail accumulator; kHiLo one.
+// plus the tail accumulators; kHiLo one.  With 64-wide kHead3 tiles the five tail
+// products get one accumulator each (n_tails = 5), so that products sharing an A piece
+// run as one MMA over two adjacent B pieces (N = 128) into adjacent accumulators: four
+// MMAs per 16-deep step instead of six.
 __host__ __device__ inline int n_heads(int scheme, int K) {
     return scheme == kHead3 ? (K + kHeadK - 1) / kHeadK : 0;
 }
+__host__ __device__ constexpr int n_tails(int scheme, int bn) {
+    return scheme == kHead3 && bn == 64 ? 5 : 1;
+}
 __host__ __device__ inline uint32_t tmem_cols(int scheme, int K, int bn) {
-    const uint32_t need = static_cast<uint32_t>((n_heads(scheme, K) + 1) * bn);
+    const uint32_t need = static_cast<uint32_t>((n_heads(scheme, K) + n_tails(scheme, bn)) * bn);
     uint32_t cols = 32;
     while (cols < need) cols <<= 1;
     return cols;
@@ -191,11 +197,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // exact integer sums, a fresh accumulator every kHeadK of K
                     const uint32_t head = tmem + static_cast<uint32_t>((kb / kHeadKB) * BN);
                     mma_f16(head, a[0], b[0], p.idesc, ((kb % kHeadKB) | k) != 0);
-                    mma_f16(tail, a[0], b[1], p.idesc, accum);
-                    mma_f16(tail, a[1], b[0], p.idesc, 1);
-                    mma_f16(tail, a[1], b[1], p.idesc, 1);
-                    mma_f16(tail, a[0], b[PIECES - 1], p.idesc, 1);
-                    mma_f16(tail, a[PIECES - 1], b[0], p.idesc, 1);
+                    if (n_tails(SCHEME, BN) == 5) {
+                        // tails [a0 b1 | a0 b2 | a1 b0 | a1 b1 | a2 b0], B pieces adjacent
+                        const uint32_t idw = (p.idesc & ~(0x3Fu << 17)) |
+                                             (static_cast<uint32_t>(2 * BN >> 3) << 17);
+                        mma_f16(tail, a[0], b[1], idw, accum);
+                        mma_f16(tail + static_cast<uint32_t>(2 * BN), a[1], b[0], idw, accum);
+                        mma_f16(tail + static_cast<uint32_t>(4 * BN), a[2], b[0], p.idesc, accum);
+                    } else {
+                        mma_f16(tail, a[0], b[1], p.idesc, accum);
+                        mma_f16(tail, a[1], b[0], p.idesc, 1);
+                        mma_f16(tail, a[1], b[1], p.idesc, 1);
+                        mma_f16(tail, a[0], b[PIECES - 1], p.idesc, 1);
+                        mma_f16(tail, a[PIECES - 1], b[0], p.idesc, 1);
+                    }
                 }
             }
             mma_commit(empty0 + 8 * s);
@@ -230,6 +245,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tmem_wait_ld();
 #pragma unroll
                     for (int j = 0; j < 32; ++j) v[j] += __uint_as_float(r[j]);
+                }
+                // separate tail accumulators summed in a fixed order
+                for (int t = 1; t < n_tails(SCHEME, BN); ++t) {
+                    tmem_ld32(tmem + static_cast<uint32_t>((nheads + t) * BN) + lane_off + c * 32, r);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        r1[j] = __float_as_uint(__uint_as_float(r1[j]) + __uint_as_float(r[j]));
                 }
 #pragma unroll
                 for (int j = 0; j < 32; ++j) v[j] = (v[j] + __uint_as_float(r1[j])) * inv;
