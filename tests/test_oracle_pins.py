@@ -392,3 +392,25 @@ def test_leapfrog_second_order_against_fine_rk4():
         tr = O.propagate(s, run, rho0, int(round(T / dt)), dt=dt)
         errs.append(np.max(np.abs(tr.rho - ref)))
     assert 3.0 < errs[0] / errs[1] < 5.0, errs
+
+
+def test_scc_ground_state_is_a_fixed_point_of_the_charge_cycle():
+    # Sec. 2.1: the ground state reproduces itself: its charges give the Hamiltonian whose
+    # occupied generalized eigenvectors rebuild the same density.  Checked by one plain
+    # diagonalisation (scipy), independent of the preconditioned mixer that found it, on a
+    # 3-D cluster (the case the preconditioner exists for) and a flake.
+    for sysm in (I.small_cluster(40, seed=13, T=300.0), I.small_flake(20, seed=3)):
+        run = I.Run(dt=0.2, n_steps=0, scc=True, kT=I.SCC_KT)
+        R = np.asarray(sysm.R, dtype=np.float64)
+        S, H0 = O.model_matrices(sysm, R)
+        gamma = O.gamma_matrix(sysm, R)
+        gs = O.ground_state(sysm, S, H0, gamma, R, True, kT=run.kT)
+        v = gamma @ gs.dq
+        vo = np.repeat(v, sysm.orbs_per_atom)
+        H = H0 + 0.5 * S * (vo[:, None] + vo[None, :])
+        eps, C = sla.eigh(H, S)
+        f = O.fermi_occupations(eps, sysm.n_electrons, run.kT)
+        rho = (C * f) @ C.T
+        assert np.max(np.abs(rho - gs.rho)) < 1e-10
+        q = np.array([np.trace((rho @ S)[4 * a:4 * a + 4, 4 * a:4 * a + 4]) for a in range(sysm.n_atoms)])
+        assert np.max(np.abs(q - sysm.n_electrons / sysm.n_atoms - gs.dq)) < 1e-11
