@@ -192,6 +192,18 @@ def run_form(B, torch, sysm, run, precision, steps, warmup, flush, stream):
                 launches=launches)
 
 
+def replica_timing(ms_step: float, world: int, dist=None):
+    """Replicas only: every rank propagates its own copy of the workload, with no
+    data-path collective.  The slowest rank's time per step sets the pace (a max over
+    ranks on the host, gloo) and the whole-job value is world x its steps/s."""
+    if dist is not None:
+        import torch
+        t = torch.tensor([ms_step], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    return ms_step, world * 1000.0 / ms_step
+
+
 def n2048_runs(B, torch, flush, stream, reduced_steps):
     """The N = 2048 points of the metric, reported beside the N = 1024 headline:
     a 512-atom flake with frozen nuclei in every form (dipole error of each form
@@ -394,12 +406,7 @@ def main():
     head = forms[-1]
     r = res[head]
     ms_step = float(np.mean(r["ms"]))
-    # max over ranks of the time per step (replicas run the same workload)
-    if dist:
-        t = torch.tensor([ms_step], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = world * 1000.0 / ms_step
+    ms_step, value = replica_timing(ms_step, world, dist)
     ms64 = float(np.mean(res["fp64"]["ms"])) if "fp64" in res else None
     err = None
     if "fp64" in res and head != "fp64":

@@ -239,8 +239,9 @@ tdb_status tdb_step_profiled(tdb_ctx* ctx, double* ms, const char** names, int c
 tdb_status tdb_split_gemm(int M, int N, int K, const double* A, const double* B, int fmt, double* C,
                           double* ms);
 
-/* C = A B with FP64-accurate integer-slice products on the tensor cores (the
- * TDB_FP64_SLICED form; no context needed, allocates and frees its own device
+/* C = A B with FP64-accurate integer-slice products on the tensor cores: the
+ * products S^-1 H and (S^-1 H) rho of eq:eomrho (Sec. 2.1) in the TDB_FP64_SLICED
+ * form, here on their own (no context needed; allocates and frees its own device
  * buffers).  A: M x K, B: K x N, C: M x N, row-major host doubles, K <= 4096.
  * Each row of A (column of B) is scaled by a power of two into (-1, 1) and cut
  * into six signed 7-bit integer slices (FP16 values); the 21 slice pairs with
