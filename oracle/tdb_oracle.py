@@ -24,6 +24,8 @@ eigensolver) as the only library steps:
 * Sec. 2.3, eq:leapfrog              leapfrog with an Euler first step
 * Sec. 2.3                           velocity Verlet for the nuclei
 * Sec. 3.1, eq:pumpf                 laser pulse
+* (learned form)                     closed-form leapfrog windows with a frozen
+                                      Hamiltonian; the per-atom shift network
 
 Parity pins: every function here is pinned by a test in
 ``tests/test_oracle_pins.py`` against something other than itself (closed
@@ -634,3 +636,85 @@ def run_trajectory(sysm, run, n_steps=None, keep_forces=False):
     rho, gs, S, Sinv = setup(sysm, run)
     n = run.n_steps if n_steps is None else n_steps
     return propagate(sysm, run, rho, n, keep_forces=keep_forces), gs
+
+
+# ---------------------------------------------------------------------------
+# Windowed propagation with a frozen Hamiltonian, and the per-atom shift network
+# (the learned form: a network predicts the window-averaged SCC shift, the window is
+# then propagated in closed form)
+# ---------------------------------------------------------------------------
+
+def window_propagate(rho_prev, rho, S, H_bar, dt, k):
+    """k leapfrog steps of eq:eomrho (eq:leapfrog) with the Hamiltonian frozen at H_bar,
+    in closed form.  In the generalised eigenbasis H_bar C = S C eps (C^T S C = 1) the
+    leapfrog acts element by element, x_{m+1} = x_{m-1} - 2 i dt w x_m with
+    w = eps_a - eps_b, solved by x_m = A l+^m + B l-^m, l+- = -i theta +- sqrt(1 - theta^2),
+    theta = w dt (the leapfrog's own modes, not exp(-i w m dt)).  With P = S C,
+    rho~ = P^T rho P and rho = C rho~ C^T.  Returns (rho_{n-1+k}, rho_{n+k}) from
+    (rho_{n-1}, rho_n)."""
+    eps, C = sla.eigh(H_bar, S)
+    P = S @ C
+    x0 = P.T @ np.asarray(rho_prev, dtype=np.complex128) @ P
+    x1 = P.T @ np.asarray(rho, dtype=np.complex128) @ P
+    theta = (eps[:, None] - eps[None, :]) * dt
+    c = np.sqrt(1.0 - theta ** 2)
+    lp = -1j * theta + c
+    lm = -1j * theta - c
+    A = (x1 - lm * x0) / (lp - lm)
+    B = x0 - A
+    xk = A * lp ** k + B * lm ** k
+    xk1 = A * lp ** (k + 1) + B * lm ** (k + 1)
+    return C @ xk @ C.T, C @ xk1 @ C.T
+
+
+def bf16_round(x):
+    """Round to the nearest bfloat16 (ties to even), returned as float64."""
+    a = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    a = (a + 0x7FFF + ((a >> 16) & 1)) & 0xFFFF0000
+    return a.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def shiftnet_unpack(params, F, H):
+    """Packed parameters: W1 (F x H), b1 (H), W2 (H x H), b2 (H), w3 (H), b3 (1)."""
+    p = np.asarray(params, dtype=np.float64)
+    o = 0
+    W1 = p[o:o + F * H].reshape(F, H); o += F * H
+    b1 = p[o:o + H]; o += H
+    W2 = p[o:o + H * H].reshape(H, H); o += H * H
+    b2 = p[o:o + H]; o += H
+    w3 = p[o:o + H]; o += H
+    b3 = p[o]
+    return W1, b1, W2, b2, w3, b3
+
+
+def shiftnet_forward(params, X, F, H, bf16=True):
+    """Per-atom network y = w3 . tanh(W2^T tanh(W1^T x + b1) + b2) + b3; the weight
+    matrices enter rounded to bfloat16 when bf16 is set (biases and activations are
+    not rounded).  Returns y and the hidden activations."""
+    W1, b1, W2, b2, w3, b3 = shiftnet_unpack(params, F, H)
+    if bf16:
+        W1, W2, w3 = bf16_round(W1), bf16_round(W2), bf16_round(w3)
+    X = np.asarray(X, dtype=np.float64)
+    h1 = np.tanh(X @ W1 + b1)
+    h2 = np.tanh(h1 @ W2 + b2)
+    return h2 @ w3 + b3, (X, h1, h2, W2, w3)
+
+
+def shiftnet_loss_grad(params, X, Y, F, H, bf16=True):
+    """Mean squared error and its gradient with respect to the packed parameters (the
+    gradient through the bfloat16 rounding is taken as that of the rounded weights)."""
+    y, (X, h1, h2, W2, w3) = shiftnet_forward(params, X, F, H, bf16)
+    n = X.shape[0]
+    r = y - np.asarray(Y, dtype=np.float64)
+    loss = float(np.mean(r * r))
+    dy = 2.0 * r / n
+    dw3 = h2.T @ dy
+    db3 = np.sum(dy)
+    dz2 = np.outer(dy, w3) * (1.0 - h2 * h2)
+    dW2 = h1.T @ dz2
+    db2 = dz2.sum(axis=0)
+    dz1 = (dz2 @ W2.T) * (1.0 - h1 * h1)
+    dW1 = X.T @ dz1
+    db1 = dz1.sum(axis=0)
+    g = np.concatenate([dW1.ravel(), db1, dW2.ravel(), db2, dw3, [db3]])
+    return loss, g

@@ -414,3 +414,46 @@ def test_scc_ground_state_is_a_fixed_point_of_the_charge_cycle():
         assert np.max(np.abs(rho - gs.rho)) < 1e-10
         q = np.array([np.trace((rho @ S)[4 * a:4 * a + 4, 4 * a:4 * a + 4]) for a in range(sysm.n_atoms)])
         assert np.max(np.abs(q - sysm.n_electrons / sysm.n_atoms - gs.dq)) < 1e-11
+
+
+def test_window_propagation_equals_leapfrog_with_a_frozen_hamiltonian():
+    # non-SCC and field-free, so the plain leapfrog's Hamiltonian is frozen at H0: the
+    # closed-form window must reproduce k of its steps
+    sysm = I.small_flake(12, seed=21, scc=False)
+    run = I.Run(dt=0.2, n_steps=0, scc=False, kick=1e-2)
+    rho0, gs, S, Sinv = O.setup(sysm, run)
+    S, H0 = O.model_matrices(sysm, np.asarray(sysm.R, dtype=np.float64))
+    k = 37
+    tr1 = O.propagate(sysm, run, rho0, 1)                 # Euler: rho_0, rho_1
+    trk = O.propagate(sysm, run, tr1.rho, k, rho_prev=tr1.rho_prev)
+    a, b = O.window_propagate(tr1.rho_prev, tr1.rho, S, H0, run.dt, k)
+    assert np.max(np.abs(a - trk.rho_prev)) < 1e-11
+    assert np.max(np.abs(b - trk.rho)) < 1e-11
+    a0, b0 = O.window_propagate(tr1.rho_prev, tr1.rho, S, H0, run.dt, 0)
+    assert np.max(np.abs(a0 - tr1.rho_prev)) < 1e-12 and np.max(np.abs(b0 - tr1.rho)) < 1e-12
+
+
+def test_bf16_rounding():
+    x = np.array([1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -3.3, 1e-3])
+    r = O.bf16_round(x)
+    assert r[0] == 1.0 and r[1] == 1.0                      # tie to even
+    assert r[2] == 1.0 + 2.0 ** -6                          # tie to even (up)
+    assert np.all(np.abs(r - x) <= np.abs(x) * 2.0 ** -8)
+
+
+def test_shiftnet_gradient_matches_central_differences():
+    rng = np.random.default_rng(5)
+    F, H, n = 7, 9, 40
+    npar = F * H + H + H * H + H + H + 1
+    p = rng.normal(size=npar) * 0.4
+    X = rng.normal(size=(n, F))
+    Y = rng.normal(size=n)
+    loss, g = O.shiftnet_loss_grad(p, X, Y, F, H, bf16=False)
+    h = 1e-6
+    fd = np.empty(npar)
+    for i in range(npar):
+        e = np.zeros(npar)
+        e[i] = h
+        fd[i] = (O.shiftnet_loss_grad(p + e, X, Y, F, H, bf16=False)[0]
+                 - O.shiftnet_loss_grad(p - e, X, Y, F, H, bf16=False)[0]) / (2 * h)
+    assert np.max(np.abs(g - fd)) < 1e-7 * max(1.0, np.max(np.abs(g)))
