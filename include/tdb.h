@@ -179,6 +179,48 @@ tdb_status tdb_step(tdb_ctx* ctx, long n);
 tdb_status tdb_clone(tdb_ctx* src, void* cuda_stream, void* workspace, size_t workspace_bytes,
                      tdb_ctx** out);
 
+/* Per-atom SCC shift sum_B gamma_AB dq_B (eq:hscc) of the current rho_n (Mulliken
+ * charges of rho_n, Sec. 2.2): out[n_atoms] host doubles.  Frozen nuclei
+ * (TDB_ERR_UNSUPPORTED otherwise).  The learned form takes its history at window
+ * ends as network input. */
+tdb_status tdb_scc_shift(tdb_ctx* ctx, double* out);
+
+/* k leapfrog steps (eq:leapfrog, eq:eomrho) with the Hamiltonian frozen at
+ * H_bar = H0 + 1/2 S (v_bar_A + v_bar_B) (eq:hscc with the per-atom potential v_bar,
+ * n_atoms values: the SCC shift plus any external potential, averaged over the
+ * window), taken in closed form: in the generalised eigenbasis H_bar C = S C eps the
+ * leapfrog acts element by element through its own two modes.  One FP64 generalised
+ * eigensolve and 17 N^3 products replace k steps of products; charges come only at
+ * the window's end, and the dipole history is not written inside a window.  FP64 or
+ * FP64_SLICED form, frozen nuclei and no laser field (TDB_ERR_UNSUPPORTED), not right
+ * after a ground state, kick or state load (take one tdb_step first: TDB_ERR_STATE).
+ * Requires |(eps_a - eps_b) dt| < 1. */
+tdb_status tdb_step_window(tdb_ctx* ctx, const double* v_bar, int k);
+
+/* The per-atom shift network of the learned form (this library's own GPU kernels;
+ * the paper has no network, it is the learned part built around its propagator):
+ * y = w3 . tanh(W2^T tanh(W1^T x + b1) + b2) + b3 for each sample x (n_features
+ * values), weights used in bfloat16 with FP32 accumulation, FP32 master parameters
+ * packed as W1 (n_features x hidden, row-major), b1, W2 (hidden x hidden), b2, w3,
+ * b3.  Trained with Adam on the mean squared error.  n_features <= 32, hidden <= 64.
+ * X: n x n_features row-major host floats; Y: n host floats. */
+typedef struct tdb_shiftnet tdb_shiftnet;
+tdb_status tdb_shiftnet_create(int n_features, int hidden, unsigned long long seed,
+                               tdb_shiftnet** out);
+long tdb_shiftnet_param_count(const tdb_shiftnet* net);
+tdb_status tdb_shiftnet_get_params(tdb_shiftnet* net, float* params);
+tdb_status tdb_shiftnet_set_params(tdb_shiftnet* net, const float* params);
+tdb_status tdb_shiftnet_predict(tdb_shiftnet* net, const float* X, long n, float* Y);
+/* grad = d(mean squared error)/d(params) over the n samples (FP32 sums in an
+ * unspecified order); *loss = the mean squared error. */
+tdb_status tdb_shiftnet_gradient(tdb_shiftnet* net, const float* X, const float* Y, long n,
+                                 float* grad, double* loss);
+/* epochs passes over the samples in mini-batches of batch (in order), one Adam step
+ * (learning rate lr) per batch; *loss_out = mean squared error over the last epoch. */
+tdb_status tdb_shiftnet_train(tdb_shiftnet* net, const float* X, const float* Y, long n,
+                              int epochs, long batch, float lr, double* loss_out);
+void tdb_shiftnet_destroy(tdb_shiftnet* net);
+
 /* Advance each of count independent contexts (trajectories) by n >= 0 steps,
  * enqueued step by step across them so that their streams run side by side on the
  * GPU: the probe runs of a pump-probe scan (Sec. 3.2) branch from pump snapshots

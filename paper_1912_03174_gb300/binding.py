@@ -20,6 +20,7 @@ PRECISIONS = {"fp64": TDB_FP64, "fp32": TDB_FP32, "bf16x3": TDB_BF16X3, "fp16x3"
               "fp16x6": TDB_FP16X6, "fp64s": TDB_FP64_SLICED}
 
 _dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
 _ip = ctypes.POINTER(ctypes.c_int)
 
 
@@ -67,6 +68,18 @@ SIGNATURES = {
     "tdb_kick": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, _dp]),
     "tdb_set_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(TdbField)]),
     "tdb_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_long]),
+    "tdb_scc_shift": (ctypes.c_int, [ctypes.c_void_p, _dp]),
+    "tdb_step_window": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.c_int]),
+    "tdb_shiftnet_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong,
+                                           ctypes.POINTER(ctypes.c_void_p)]),
+    "tdb_shiftnet_param_count": (ctypes.c_long, [ctypes.c_void_p]),
+    "tdb_shiftnet_get_params": (ctypes.c_int, [ctypes.c_void_p, _fp]),
+    "tdb_shiftnet_set_params": (ctypes.c_int, [ctypes.c_void_p, _fp]),
+    "tdb_shiftnet_predict": (ctypes.c_int, [ctypes.c_void_p, _fp, ctypes.c_long, _fp]),
+    "tdb_shiftnet_gradient": (ctypes.c_int, [ctypes.c_void_p, _fp, _fp, ctypes.c_long, _fp, _dp]),
+    "tdb_shiftnet_train": (ctypes.c_int, [ctypes.c_void_p, _fp, _fp, ctypes.c_long, ctypes.c_int,
+                                          ctypes.c_long, ctypes.c_float, _dp]),
+    "tdb_shiftnet_destroy": (None, [ctypes.c_void_p]),
     "tdb_clone": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                   ctypes.POINTER(ctypes.c_void_p)]),
     "tdb_step_batch": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_long]),
@@ -236,6 +249,78 @@ def tdb_set_field(ctx: Context, fld):
 
 def tdb_step(ctx: Context, n: int):
     _check("tdb_step", load().tdb_step(ctx.handle, int(n)))
+
+
+def tdb_scc_shift(ctx: Context) -> np.ndarray:
+    out = np.zeros(ctx.n_atoms)
+    _check("tdb_scc_shift", load().tdb_scc_shift(ctx.handle, _ptr(out)))
+    return out
+
+
+def tdb_step_window(ctx: Context, v_bar, k: int):
+    v = np.ascontiguousarray(v_bar, dtype=np.float64)
+    assert v.shape == (ctx.n_atoms,)
+    _check("tdb_step_window", load().tdb_step_window(ctx.handle, _ptr(v), int(k)))
+
+
+def _fptr(a):
+    return a.ctypes.data_as(_fp)
+
+
+class ShiftNet:
+    """The per-atom shift network on the GPU (tdb_shiftnet_*)."""
+
+    def __init__(self, n_features: int, hidden: int = 64, seed: int = 0):
+        self.F, self.H = int(n_features), int(hidden)
+        self.handle = ctypes.c_void_p()
+        _check("tdb_shiftnet_create", load().tdb_shiftnet_create(self.F, self.H, int(seed),
+                                                                 ctypes.byref(self.handle)))
+        self.n_params = int(load().tdb_shiftnet_param_count(self.handle))
+
+    def params(self) -> np.ndarray:
+        p = np.zeros(self.n_params, dtype=np.float32)
+        _check("tdb_shiftnet_get_params", load().tdb_shiftnet_get_params(self.handle, _fptr(p)))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.shape == (self.n_params,)
+        _check("tdb_shiftnet_set_params", load().tdb_shiftnet_set_params(self.handle, _fptr(p)))
+
+    def predict(self, X) -> np.ndarray:
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.zeros(X.shape[0], dtype=np.float32)
+        _check("tdb_shiftnet_predict", load().tdb_shiftnet_predict(self.handle, _fptr(X), X.shape[0], _fptr(Y)))
+        return Y
+
+    def gradient(self, X, Y):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.ascontiguousarray(Y, dtype=np.float32)
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = ctypes.c_double()
+        _check("tdb_shiftnet_gradient", load().tdb_shiftnet_gradient(
+            self.handle, _fptr(X), _fptr(Y), X.shape[0], _fptr(g), ctypes.byref(loss)))
+        return loss.value, g
+
+    def train(self, X, Y, epochs: int, batch: int, lr: float) -> float:
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.ascontiguousarray(Y, dtype=np.float32)
+        loss = ctypes.c_double()
+        _check("tdb_shiftnet_train", load().tdb_shiftnet_train(
+            self.handle, _fptr(X), _fptr(Y), X.shape[0], int(epochs), int(batch), float(lr),
+            ctypes.byref(loss)))
+        return loss.value
+
+    def close(self):
+        if self.handle:
+            load().tdb_shiftnet_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def tdb_clone(ctx: Context, stream=None) -> Context:

@@ -19,6 +19,11 @@ void gemm_f32_add(int M, int Ncol, int K, const float* A, int lda, const float* 
 void launch_f64_to_f32(size_t n, const double* in, float* out, cudaStream_t st);
 void launch_f32_to_f64(size_t n, const float* in, double* out, cudaStream_t st);
 void launch_ns_update(int N, double* X, const double* Q, cudaStream_t st);
+namespace learn {
+void launch_window(int N, const double* eps, double dt, int k, double* x0re, double* x0im,
+                   double* x1re, double* x1im, cudaStream_t st);
+void launch_add_step(DevScalars* sc, int k, cudaStream_t st);
+}  // namespace learn
 void gemm_f32(int M, int Ncol, int K, const float* A, int lda, const float* B, int ldb, float* C,
               int ldc, cudaStream_t st);
 void launch_add_f32_strided(int N, const float* a, const float* b, int ldb, float* out, int ldo,
@@ -1123,7 +1128,7 @@ tdb_status tdb_create(const tdb_system* sys, const tdb_params* prm, void* worksp
         tdb_destroy(c);
         return s;
     };
-    c->h_pinned_bytes = 4096 + sizeof(double) * (size_t)c->nat;
+    c->h_pinned_bytes = 4096 + sizeof(double) * (size_t)c->N;   // charges, or N doubles for a window
     if (cudaMallocHost(reinterpret_cast<void**>(&c->h_pinned), c->h_pinned_bytes) != cudaSuccess) {
         cudaGetLastError();
         set_err("cudaMallocHost failed");
@@ -1538,6 +1543,126 @@ tdb_status tdb_clone(tdb_ctx* src, void* cuda_stream, void* workspace, size_t wo
     return TDB_OK;
 }
 
+tdb_status tdb_scc_shift(tdb_ctx* c, double* out) {
+    TRY(check_ctx(c, true, true));
+    if (!out) {
+        set_err("NULL out");
+        return TDB_ERR_ARG;
+    }
+    if (c->prm.move_nuclei) {
+        set_err("tdb_scc_shift: frozen nuclei");
+        return TDB_ERR_UNSUPPORTED;
+    }
+    // charges and potential of the current rho_n, as tdb_observables takes them
+    launch_charges(*c, c->partial, c->q, c->dq, c->stream, nullptr, nullptr, nullptr, 0, c->qbase);
+    launch_potential(*c, c->gamma, c->dq, c->d_R, c->sc, c->v_orb, c->v_atom, c->gdq, c->hist,
+                     c->v_ref, nullptr, c->stream);
+    CKL();
+    CK(cudaMemcpyAsync(out, c->gdq, sizeof(double) * c->nat, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return TDB_OK;
+}
+
+tdb_status tdb_step_window(tdb_ctx* c, const double* v_bar, int k) {
+    TRY(step_checks(c));
+    if (!v_bar || k < 1) {
+        set_err("tdb_step_window: need v_bar and k >= 1");
+        return TDB_ERR_ARG;
+    }
+    if (c->prm.move_nuclei || (c->prm.precision != TDB_FP64 && c->prm.precision != TDB_FP64_SLICED)) {
+        set_err("tdb_step_window: frozen nuclei and an FP64 density (FP64 or FP64_SLICED form)");
+        return TDB_ERR_UNSUPPORTED;
+    }
+    if (c->field_on) {
+        set_err("tdb_step_window: no laser field (the window freezes the Hamiltonian)");
+        return TDB_ERR_UNSUPPORTED;
+    }
+    if (c->euler_next) {
+        set_err("tdb_step_window: take one tdb_step after a ground state, kick or state load");
+        return TDB_ERR_STATE;
+    }
+    const int N = c->N, cur = c->cur, prv = cur ^ 1;
+    double* d_eig = c->obs_out + 16;
+    if (!c->win_tmp) {
+        int lwork = 0;
+        CKS(cusolverDnDsygvd_bufferSize(c->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR,
+                                        CUBLAS_FILL_MODE_LOWER, N, c->Hs, N, c->M, N, d_eig, &lwork));
+        c->win_lwork = std::max(lwork, 1);
+        if (cudaMalloc(&c->win_work, sizeof(double) * c->win_lwork + 256) != cudaSuccess ||
+            cudaMalloc(&c->win_tmp, sizeof(double) * N * N) != cudaSuccess) {
+            cudaGetLastError();
+            set_err("tdb_step_window: workspace allocation failed");
+            return TDB_ERR_NOMEM;
+        }
+        c->win_info = reinterpret_cast<int*>(reinterpret_cast<char*>(c->win_work) +
+                                             sizeof(double) * c->win_lwork);
+    }
+    // H_bar = H0 + 1/2 S (v_bar_mu + v_bar_nu), v_bar per atom repeated over its orbitals
+    double* hv = reinterpret_cast<double*>(c->h_pinned + 4096);
+    if (c->h_pinned_bytes < 4096 + sizeof(double) * (size_t)N) {
+        set_err("tdb_step_window: staging buffer too small");
+        return TDB_ERR_STATE;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    for (int a = 0; a < c->nat; ++a)
+        for (int o = 0; o < c->nper; ++o) hv[a * c->nper + o] = v_bar[a];
+    CK(cudaMemcpyAsync(c->v_orb, hv, sizeof(double) * N, cudaMemcpyHostToDevice, c->stream));
+    launch_build_hamiltonian(N, c->H0, c->S, c->v_orb, c->Hs, c->stream);
+    CK(cudaMemcpyAsync(c->M, c->S, sizeof(double) * N * N, cudaMemcpyDeviceToDevice, c->stream));
+    CKS(cusolverDnDsygvd(c->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR,
+                         CUBLAS_FILL_MODE_LOWER, N, c->Hs, N, c->M, N, d_eig, c->win_work,
+                         c->win_lwork, c->win_info));
+    {
+        // the generalised eigensolve must succeed and the leapfrog's own modes need
+        // |(eps_a - eps_b) dt| < 1 (beyond it the leapfrog itself is unstable)
+        int* hinfo = reinterpret_cast<int*>(c->h_pinned + 192);
+        CK(cudaMemcpyAsync(hinfo, c->win_info, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(hv, d_eig, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        if (*hinfo != 0) {
+            set_err("tdb_step_window: generalised eigensolve failed (info %d)", *hinfo);
+            return TDB_ERR_CUDA;
+        }
+        const double spread = (hv[N - 1] - hv[0]) * std::fabs(c->prm.dt);
+        if (!(spread < 1.0)) {
+            set_err("tdb_step_window: (eps_max - eps_min) |dt| = %g, needs < 1", spread);
+            return TDB_ERR_UNSUPPORTED;
+        }
+    }
+    // Hs read row-major is Z = C^T (columns of C are the eigenvectors, C^T S C = 1)
+    double* Z = c->Hs;
+    double* Cm = c->M;          // C
+    double* Pt = c->Xre;        // P^T = C^T S = Z S
+    double* P = c->Xim;         // P = S C
+    launch_transpose(N, Z, Cm, c->stream);
+    gemm_f64(N, N, N, Z, N, c->S, N, Pt, N, c->stream);
+    launch_transpose(N, Pt, P, c->stream);
+    double* lev[4] = {c->rho_re[prv], c->rho_im[prv], c->rho_re[cur], c->rho_im[cur]};
+    for (double* x : lev) {   // rho~ = P^T rho P
+        gemm_f64(N, N, N, Pt, N, x, N, c->win_tmp, N, c->stream);
+        gemm_f64(N, N, N, c->win_tmp, N, P, N, x, N, c->stream);
+    }
+    learn::launch_window(N, d_eig, c->prm.dt, k, lev[0], lev[1], lev[2], lev[3], c->stream);
+    for (double* x : lev) {   // rho = C rho~ C^T
+        gemm_f64(N, N, N, Cm, N, x, N, c->win_tmp, N, c->stream);
+        gemm_f64(N, N, N, c->win_tmp, N, Z, N, x, N, c->stream);
+    }
+    // exactly Hermitian levels, then the Mulliken partials of the new rho_n
+    for (int l : {prv, cur}) {
+        launch_hermitian_half(N, c->rho_re[l], c->rho_im[l], c->Xre, c->Xim, c->stream);
+        CK(cudaMemcpyAsync(c->rho_re[l], c->Xre, sizeof(double) * N * N, cudaMemcpyDeviceToDevice,
+                           c->stream));
+        CK(cudaMemcpyAsync(c->rho_im[l], c->Xim, sizeof(double) * N * N, cudaMemcpyDeviceToDevice,
+                           c->stream));
+    }
+    launch_mulliken_partials(N, c->rho_re[cur], c->S, c->partial, c->stream);
+    learn::launch_add_step(c->sc, k, c->stream);
+    CKL();
+    c->n += k;
+    c->last_launches = 0;
+    return TDB_OK;
+}
+
 tdb_status tdb_step_batch(tdb_ctx* const* ctxs, int count, long n) {
     if (!ctxs || count < 1 || n < 0) {
         set_err("tdb_step_batch: need count >= 1 contexts and n >= 0");
@@ -1875,6 +2000,8 @@ void tdb_destroy(tdb_ctx* c) {
     if (c->solver) cusolverDnDestroy(c->solver);
     if (c->own_ws && c->ws) cudaFree(c->ws);
     if (c->inv_work) cudaFree(c->inv_work);
+    if (c->win_work) cudaFree(c->win_work);
+    if (c->win_tmp) cudaFree(c->win_tmp);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     delete c;

@@ -147,6 +147,12 @@ struct Ctx {
     int inv_lwork = 0;
     int* inv_info = nullptr;
 
+    // closed-form windows (learned form): generalised eigensolver workspace and a scratch
+    double* win_work = nullptr;
+    int win_lwork = 0;
+    int* win_info = nullptr;
+    double* win_tmp = nullptr;
+
     cusolverDnHandle_t solver = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int graph_launches = 0;      // kernels per captured step
