@@ -293,6 +293,118 @@ def c4_runs(B, torch, n_traj, post_steps, form="fp16x6"):
             "timing": "host clock between device-wide synchronisations"}
 
 
+def c5_runs(B, torch, k=16, L=8, hidden=64, n_train=4, train_steps=1200, windows=12,
+            epochs=20, form="fp64s"):
+    """The learned form on the 256-atom flake (N = 1024): shift and charge records of
+    n_train plain runs (kicks of seeded strength 1e-3..3e-3 a.u. along seeded directions)
+    train the per-atom network (L shift and L charge samples at window ends, two hidden
+    layers of `hidden`, BF16 weights) on the GPU; a held-out run (the flake's own kick, 1e-3 a.u. along x)
+    then advances in windows of k steps with the network's shift, with the shift frozen
+    at the window's start, and in plain steps.  Reported: data and training time, time
+    per window against k plain steps, and the charge and dipole errors at window ends
+    against the plain run."""
+    import dataclasses
+    from paper_1912_03174_gb300 import inputs as I, learned as Lrn
+    sysm, run = I.flake_c2()
+    rng = np.random.default_rng(1005)
+    Xs, Ys = [], []
+    t0 = time.perf_counter()
+    for _ in range(n_train):
+        d = rng.normal(size=3)
+        r = dataclasses.replace(run, kick=float(rng.uniform(1e-3, 3e-3)), kick_dir=d / np.linalg.norm(d))
+        with B.Propagator(sysm, r, form) as p:
+            p.setup()
+            p.step(1)
+            X, Y = Lrn.training_set(Lrn.record(p.ctx, train_steps), k, L)
+            Xs.append(X)
+            Ys.append(Y)
+    t_data = time.perf_counter() - t0
+    X, Y = np.concatenate(Xs), np.concatenate(Ys)
+    model = Lrn.ShiftModel(k=k, L=L, hidden=hidden, seed=5)
+    t0 = time.perf_counter()
+    model.fit(X, Y, epochs=epochs, batch=512, lr=2e-3)
+    t_train = time.perf_counter() - t0
+
+    def start():
+        p = B.Propagator(sysm, run, form)
+        p.setup()
+        p.step(1)
+        return p
+
+    out = {}
+    # plain reference: warm-up windows, then `windows` windows of k plain steps
+    p = start()
+    try:
+        p.step(L * k)
+        q_ref, mu_ref, t_plain = [], [], []
+        for _ in range(windows):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            B.tdb_step(p.ctx, k)
+            torch.cuda.synchronize()
+            t_plain.append(time.perf_counter() - t0)
+            o = p.observables()
+            q_ref.append(o["charges"])
+            mu_ref.append(o["dipole"])
+    finally:
+        p.close()
+    q_ref, mu_ref = np.array(q_ref), np.array(mu_ref)
+    for mode in ("frozen", "net"):
+        p = start()
+        try:
+            lp = Lrn.LearnedPropagator(p.ctx, model, mode=mode)
+            lp.warm_up()
+            q, mu, t_win = [], [], []
+            for _ in range(windows):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                lp.run(1)
+                torch.cuda.synchronize()
+                t_win.append(time.perf_counter() - t0)
+                o = p.observables()
+                q.append(o["charges"])
+                mu.append(o["dipole"])
+        finally:
+            p.close()
+        eq = np.max(np.abs(np.array(q) - q_ref), axis=1)
+        emu = np.max(np.abs(np.array(mu) - mu_ref), axis=1)
+        out[mode] = {"max_charge_err": float(eq.max()), "final_charge_err": float(eq[-1]),
+                     "max_dipole_err_au": float(emu.max()), "final_dipole_err_au": float(emu[-1]),
+                     "ms_per_window": 1000.0 * float(np.median(t_win[1:]))}
+    # the judge at the stated dipole bound, every fourth window
+    p = start()
+    try:
+        lp = Lrn.LearnedPropagator(p.ctx, model, mode="net", judge_every=4, bound=float("inf"),
+                                   dipole_bound=1e-5)
+        lp.warm_up()
+        lp.run(windows)
+        st = lp.stats
+        judge = {"dipole_bound_au": 1e-5, "judge_every": 4, "windows_run": st.windows,
+                 "judged": st.judged, "taken_over": st.taken_over,
+                 "plain_steps_after_warm_up": st.plain_steps - L * k,
+                 "judge_dipole_err_au": st.judge_dipole_err, "judge_charge_err": st.judge_err}
+    finally:
+        p.close()
+    model.close()
+    ms_plain = 1000.0 * float(np.median(t_plain))
+    ms_win = out["net"]["ms_per_window"]
+    return {"workload": f"learned form on the SCC flake, 256 atoms (N=1024), form {form}: "
+                        f"{n_train} training runs x {train_steps} steps, held-out kick 1e-3 a.u. along x, "
+                        f"windows of k={k} steps (dt=0.2), {windows} windows after {L} plain warm-up windows",
+            "training": {"samples": int(len(Y)), "epochs": epochs, "data_s": t_data, "train_s": t_train,
+                         "samples_per_s": epochs * len(Y) / t_train,
+                         "final_loss_scaled": float(model.losses[-1])},
+            "ms_k_plain_steps": ms_plain, "ms_per_window": ms_win,
+            "effective_steps_per_s_window": 1000.0 * k / ms_win,
+            "steps_per_s_plain": 1000.0 * k / ms_plain,
+            "window_vs_plain_speedup": ms_plain / ms_win,
+            "errors_vs_plain": out,
+            "judge": judge,
+            "gain_charge_err_frozen_over_net": out["frozen"]["max_charge_err"] / max(out["net"]["max_charge_err"], 1e-300),
+            "timing": "host clock between device synchronisations (window: shift readback, "
+                      "network inference, eigensolve and products)"}
+
+
 def e2e_run(B, sysm, run, precision, steps, warmup):
     """End to end through the public API: per step the field is set from the host
     (H2D), one step runs, and the observables with charges are read back (D2H)."""
@@ -360,6 +472,7 @@ def main():
     ap.add_argument("--no-n2048", action="store_true")
     ap.add_argument("--c4-probes", type=int, default=64, help="pump-probe scan size (0: skip)")
     ap.add_argument("--c4-steps", type=int, default=200, help="timed post-kick steps per probe")
+    ap.add_argument("--no-c5", action="store_true", help="skip the learned-form section")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -399,6 +512,7 @@ def main():
         c4 = None
         if args.c4_probes > 0:
             c4 = c4_runs(B, torch, args.c4_probes, args.c4_steps)
+        c5 = None if args.no_c5 else c5_runs(B, torch)
         if dist:
             dist.barrier()
     clocks = clk.summary()
@@ -458,7 +572,8 @@ def main():
                              for f in forms},
                    "kernel_ms": {f: res[f]["prof"] for f in forms},
                    "n2048": n2048,
-                   "pump_probe_c4": c4},
+                   "pump_probe_c4": c4,
+                   "learned_c5": c5},
         "roofline": roof,
         "gpu_launches": int(r["launches"]),
         "clocks": clocks,

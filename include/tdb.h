@@ -179,11 +179,12 @@ tdb_status tdb_step(tdb_ctx* ctx, long n);
 tdb_status tdb_clone(tdb_ctx* src, void* cuda_stream, void* workspace, size_t workspace_bytes,
                      tdb_ctx** out);
 
-/* Per-atom SCC shift sum_B gamma_AB dq_B (eq:hscc) of the current rho_n (Mulliken
- * charges of rho_n, Sec. 2.2): out[n_atoms] host doubles.  Frozen nuclei
- * (TDB_ERR_UNSUPPORTED otherwise).  The learned form takes its history at window
+/* Per-atom SCC shift sum_B gamma_AB dq_B (eq:hscc) of the current rho_n into out, and
+ * when dq is non-NULL the charge fluctuations dq_A = q_A - q0_A themselves (Mulliken
+ * charges of rho_n, eq:qmulik): n_atoms host doubles each.  Frozen nuclei
+ * (TDB_ERR_UNSUPPORTED otherwise).  The learned form takes their history at window
  * ends as network input. */
-tdb_status tdb_scc_shift(tdb_ctx* ctx, double* out);
+tdb_status tdb_scc_shift(tdb_ctx* ctx, double* out, double* dq);
 
 /* k leapfrog steps (eq:leapfrog, eq:eomrho) with the Hamiltonian frozen at
  * H_bar = H0 + 1/2 S (v_bar_A + v_bar_B) (eq:hscc with the per-atom potential v_bar,

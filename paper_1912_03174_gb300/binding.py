@@ -68,7 +68,7 @@ SIGNATURES = {
     "tdb_kick": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, _dp]),
     "tdb_set_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(TdbField)]),
     "tdb_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_long]),
-    "tdb_scc_shift": (ctypes.c_int, [ctypes.c_void_p, _dp]),
+    "tdb_scc_shift": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
     "tdb_step_window": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.c_int]),
     "tdb_shiftnet_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong,
                                            ctypes.POINTER(ctypes.c_void_p)]),
@@ -251,10 +251,12 @@ def tdb_step(ctx: Context, n: int):
     _check("tdb_step", load().tdb_step(ctx.handle, int(n)))
 
 
-def tdb_scc_shift(ctx: Context) -> np.ndarray:
+def tdb_scc_shift(ctx: Context, charges=False):
+    """The SCC shift of rho_n per atom; with charges=True also dq: (shift, dq)."""
     out = np.zeros(ctx.n_atoms)
-    _check("tdb_scc_shift", load().tdb_scc_shift(ctx.handle, _ptr(out)))
-    return out
+    dq = np.zeros(ctx.n_atoms) if charges else None
+    _check("tdb_scc_shift", load().tdb_scc_shift(ctx.handle, _ptr(out), _ptr(dq) if charges else None))
+    return (out, dq) if charges else out
 
 
 def tdb_step_window(ctx: Context, v_bar, k: int):

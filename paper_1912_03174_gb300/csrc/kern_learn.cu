@@ -4,7 +4,7 @@
 // Network: y = w3 . tanh(W2^T tanh(W1^T x + b1) + b2) + b3 per sample, weights used in
 // bfloat16 (rounded from FP32 masters when staged into shared memory), FP32
 // accumulation.  Training minimises the mean squared error with Adam; the backward pass
-// stages a block of 128 samples' activations in shared memory and forms the weight
+// keeps a block of 128 samples' activations in shared memory and forms the weight
 // gradients as block-level sums (X^T dz1, h1^T dz2) added to the global gradient.
 #include <cuda_bf16.h>
 
@@ -72,90 +72,124 @@ __global__ void k_net_forward(int F, int H, const float* __restrict__ params,
 }
 
 // Gradient of the mean squared error over n samples (scale = 1 / n), added to grad;
-// the sum of squared residuals is added to *sse.
+// the sum of squared residuals is added to *sse.  One block takes 128 samples and works
+// layer by layer, all threads on each layer's 128 x H outputs (one sample's row is read
+// as a broadcast, the weights along consecutive columns); W2 is staged with rows padded
+// to H + 1 so that its transposed use in the backward pass is conflict-free too.  The
+// weight and bias gradients are the block's column sums, one global atomic per element.
+// Rows past n carry x = 0 and dy = 0, so they add nothing.
 __global__ void __launch_bounds__(256)
     k_net_grad(int F, int H, const float* __restrict__ params, const float* __restrict__ X,
                const float* __restrict__ Y, long n, float scale, float* __restrict__ grad,
                double* __restrict__ sse) {
     extern __shared__ float sm[];
     const Layout L = layout(F, H);
-    // per-sample rows padded by one float against bank conflicts
-    const int FS = F + 1, HS = H + 1;
-    float* sp = sm;                                   // parameters
-    float* sx = sp + ((L.n + 31) & ~31);              // X block   [128][F + 1]
-    float* sh1 = sx + kBlockSamples * FS;             // h1        [128][H + 1]
-    float* sd1 = sh1 + kBlockSamples * HS;            // dz1       [128][H + 1]
-    float* sd2 = sd1 + kBlockSamples * HS;            // dz2       [128][H + 1]
-    float* sb = sd2 + kBlockSamples * HS;             // b1, b2, w3 grads, b3, sse [3H + 2]
-    stage(L, params, sp);
-    for (int i = threadIdx.x; i < 3 * H + 2; i += blockDim.x) sb[i] = 0.f;
-    __syncthreads();
-    const long s0 = static_cast<long>(blockIdx.x) * kBlockSamples;
-    const int t = threadIdx.x;
-    if (t < kBlockSamples) {
-        const long s = s0 + t;
-        float* xs = sx + t * FS;
-        float* h1 = sh1 + t * HS;
-        float* d1 = sd1 + t * HS;
-        float* d2 = sd2 + t * HS;
-        if (s < n) {
-            for (int f = 0; f < F; ++f) xs[f] = X[s * F + f];
-            for (int j = 0; j < H; ++j) {
-                float z = sp[L.ob1 + j];
-                for (int f = 0; f < F; ++f) z = fmaf(xs[f], sp[L.oW1 + f * H + j], z);
-                h1[j] = tanhf(z);
-            }
-            // h2 is kept in d2 until dz2 replaces it
-            float y = sp[L.ob3];
-            for (int j = 0; j < H; ++j) {
-                float z = sp[L.ob2 + j];
-                for (int i = 0; i < H; ++i) z = fmaf(h1[i], sp[L.oW2 + i * H + j], z);
-                d2[j] = tanhf(z);
-                y = fmaf(d2[j], sp[L.ow3 + j], y);
-            }
-            const float r = y - Y[s];
-            const float dy = 2.f * r * scale;
-            atomicAdd(&sb[3 * H], dy);                 // b3
-            atomicAdd(&sb[3 * H + 1], r * r);          // squared residual
-            for (int j = 0; j < H; ++j) {
-                const float h2 = d2[j];
-                atomicAdd(&sb[2 * H + j], h2 * dy);    // w3
-                d2[j] = dy * sp[L.ow3 + j] * (1.f - h2 * h2);
-                atomicAdd(&sb[H + j], d2[j]);          // b2
-            }
-            for (int i = 0; i < H; ++i) {
-                float g = 0.f;
-                for (int j = 0; j < H; ++j) g = fmaf(d2[j], sp[L.oW2 + i * H + j], g);
-                d1[i] = g * (1.f - h1[i] * h1[i]);
-                atomicAdd(&sb[i], d1[i]);              // b1
-            }
-        } else {
-            for (int f = 0; f < F; ++f) xs[f] = 0.f;
-            for (int j = 0; j < H; ++j) h1[j] = d1[j] = d2[j] = 0.f;
-        }
+    const int FS = F + 1, HS = H + 1, t = threadIdx.x, nt = blockDim.x;
+    constexpr int S = kBlockSamples;
+    float* sW1 = sm;                        // F x H
+    float* sb1 = sW1 + F * H;               // H
+    float* sW2 = sb1 + H;                   // H x (H + 1)
+    float* sb2 = sW2 + H * HS;              // H
+    float* sw3 = sb2 + H;                   // H
+    float* sx = sw3 + H + 1;                // [S][F + 1]   (b3 sits at sw3[H])
+    float* sh1 = sx + S * FS;               // [S][H + 1]
+    float* sh2 = sh1 + S * HS;              // [S][H + 1]
+    float* sd1 = sh2 + S * HS;              // [S][H + 1]
+    float* sd2 = sd1 + S * HS;              // [S][H + 1]
+    float* sdy = sd2 + S * HS;              // [S]
+    float* sr2 = sdy + S;                   // [S] squared residuals
+    for (int i = t; i < F * H; i += nt) sW1[i] = bf(params[L.oW1 + i]);
+    for (int i = t; i < H * H; i += nt) sW2[(i / H) * HS + i % H] = bf(params[L.oW2 + i]);
+    for (int i = t; i < H; i += nt) {
+        sb1[i] = params[L.ob1 + i];
+        sb2[i] = params[L.ob2 + i];
+        sw3[i] = bf(params[L.ow3 + i]);
+    }
+    if (t == 0) sw3[H] = params[L.ob3];
+    const long s0 = static_cast<long>(blockIdx.x) * S;
+    for (int e = t; e < S * F; e += nt) {
+        const int q = e / F, f = e % F;
+        sx[q * FS + f] = s0 + q < n ? X[(s0 + q) * F + f] : 0.f;
     }
     __syncthreads();
-    // W1 = X^T dz1 and W2 = h1^T dz2 over the block's samples
-    for (int e = t; e < F * H + H * H; e += blockDim.x) {
+    // h1 = tanh(x W1 + b1)
+    for (int e = t; e < S * H; e += nt) {
+        const int q = e / H, j = e % H;
+        float z = sb1[j];
+        for (int f = 0; f < F; ++f) z = fmaf(sx[q * FS + f], sW1[f * H + j], z);
+        sh1[q * HS + j] = tanhf(z);
+    }
+    __syncthreads();
+    // h2 = tanh(h1 W2 + b2)
+    for (int e = t; e < S * H; e += nt) {
+        const int q = e / H, j = e % H;
+        float z = sb2[j];
+        for (int i = 0; i < H; ++i) z = fmaf(sh1[q * HS + i], sW2[i * HS + j], z);
+        sh2[q * HS + j] = tanhf(z);
+    }
+    __syncthreads();
+    // y = h2 w3 + b3, dy = 2 (y - Y) / n
+    for (int q = t; q < S; q += nt) {
+        float y = sw3[H];
+        for (int j = 0; j < H; ++j) y = fmaf(sh2[q * HS + j], sw3[j], y);
+        const bool ok = s0 + q < n;
+        const float r = ok ? y - Y[s0 + q] : 0.f;
+        sdy[q] = 2.f * r * scale;
+        sr2[q] = r * r;
+    }
+    __syncthreads();
+    // dz2 = dy w3 (1 - h2^2)
+    for (int e = t; e < S * H; e += nt) {
+        const int q = e / H, j = e % H;
+        const float h2 = sh2[q * HS + j];
+        sd2[q * HS + j] = sdy[q] * sw3[j] * (1.f - h2 * h2);
+    }
+    __syncthreads();
+    // dz1 = (dz2 W2^T) (1 - h1^2)
+    for (int e = t; e < S * H; e += nt) {
+        const int q = e / H, i = e % H;
         float g = 0.f;
-        if (e < F * H) {
+        for (int j = 0; j < H; ++j) g = fmaf(sd2[q * HS + j], sW2[i * HS + j], g);
+        const float h1 = sh1[q * HS + i];
+        sd1[q * HS + i] = g * (1.f - h1 * h1);
+    }
+    __syncthreads();
+    // column sums over the block's samples
+    const int nW1 = F * H, nW2 = H * H;
+    for (int e = t; e < nW1 + nW2 + 3 * H + 1; e += nt) {
+        float g = 0.f;
+        int dst;
+        if (e < nW1) {
             const int f = e / H, j = e % H;
-            for (int q = 0; q < kBlockSamples; ++q) g = fmaf(sx[q * FS + f], sd1[q * HS + j], g);
-            atomicAdd(&grad[L.oW1 + e], g);
+            for (int q = 0; q < S; ++q) g = fmaf(sx[q * FS + f], sd1[q * HS + j], g);
+            dst = L.oW1 + e;
+        } else if (e < nW1 + nW2) {
+            const int e2 = e - nW1, i = e2 / H, j = e2 % H;
+            for (int q = 0; q < S; ++q) g = fmaf(sh1[q * HS + i], sd2[q * HS + j], g);
+            dst = L.oW2 + e2;
         } else {
-            const int e2 = e - F * H, i = e2 / H, j = e2 % H;
-            for (int q = 0; q < kBlockSamples; ++q) g = fmaf(sh1[q * HS + i], sd2[q * HS + j], g);
-            atomicAdd(&grad[L.oW2 + e2], g);
+            const int e3 = e - nW1 - nW2, j = e3 % H;
+            if (e3 < H) {                       // b1
+                for (int q = 0; q < S; ++q) g += sd1[q * HS + j];
+                dst = L.ob1 + j;
+            } else if (e3 < 2 * H) {            // b2
+                for (int q = 0; q < S; ++q) g += sd2[q * HS + j];
+                dst = L.ob2 + j;
+            } else if (e3 < 3 * H) {            // w3
+                for (int q = 0; q < S; ++q) g = fmaf(sh2[q * HS + j], sdy[q], g);
+                dst = L.ow3 + j;
+            } else {                            // b3
+                for (int q = 0; q < S; ++q) g += sdy[q];
+                dst = L.ob3;
+            }
         }
+        atomicAdd(&grad[dst], g);
     }
-    for (int j = t; j < H; j += blockDim.x) {
-        atomicAdd(&grad[L.ob1 + j], sb[j]);
-        atomicAdd(&grad[L.ob2 + j], sb[H + j]);
-        atomicAdd(&grad[L.ow3 + j], sb[2 * H + j]);
-    }
-    if (t == 0) {
-        atomicAdd(&grad[L.ob3], sb[3 * H]);
-        atomicAdd(sse, static_cast<double>(sb[3 * H + 1]));
+    if (t < 32) {
+        float r2 = 0.f;
+        for (int q = t; q < S; q += 32) r2 += sr2[q];
+        for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+        if (t == 0) atomicAdd(sse, static_cast<double>(r2));
     }
 }
 
@@ -212,9 +246,8 @@ __global__ void k_add_step(DevScalars* sc, int k) {
 int n_params(int F, int H) { return layout(F, H).n; }
 
 size_t grad_smem(int F, int H) {
-    const Layout L = layout(F, H);
-    return sizeof(float) * (((L.n + 31) & ~31) + kBlockSamples * (F + 1) +
-                            3 * kBlockSamples * (H + 1) + 3 * H + 2);
+    return sizeof(float) * (F * H + H + H * (H + 1) + 3 * H + 1 + kBlockSamples * (F + 1) +
+                            4 * kBlockSamples * (H + 1) + 2 * kBlockSamples);
 }
 
 // The attributes are set for the largest network (32 features, 64 hidden), so that

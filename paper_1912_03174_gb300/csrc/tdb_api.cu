@@ -1543,7 +1543,7 @@ tdb_status tdb_clone(tdb_ctx* src, void* cuda_stream, void* workspace, size_t wo
     return TDB_OK;
 }
 
-tdb_status tdb_scc_shift(tdb_ctx* c, double* out) {
+tdb_status tdb_scc_shift(tdb_ctx* c, double* out, double* dq) {
     TRY(check_ctx(c, true, true));
     if (!out) {
         set_err("NULL out");
@@ -1559,6 +1559,7 @@ tdb_status tdb_scc_shift(tdb_ctx* c, double* out) {
                      c->v_ref, nullptr, c->stream);
     CKL();
     CK(cudaMemcpyAsync(out, c->gdq, sizeof(double) * c->nat, cudaMemcpyDeviceToHost, c->stream));
+    if (dq) CK(cudaMemcpyAsync(dq, c->dq, sizeof(double) * c->nat, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return TDB_OK;
 }
@@ -1632,20 +1633,46 @@ tdb_status tdb_step_window(tdb_ctx* c, const double* v_bar, int k) {
     // Hs read row-major is Z = C^T (columns of C are the eigenvectors, C^T S C = 1)
     double* Z = c->Hs;
     double* Cm = c->M;          // C
-    double* Pt = c->Xre;        // P^T = C^T S = Z S
-    double* P = c->Xim;         // P = S C
-    launch_transpose(N, Z, Cm, c->stream);
-    gemm_f64(N, N, N, Z, N, c->S, N, Pt, N, c->stream);
-    launch_transpose(N, Pt, P, c->stream);
     double* lev[4] = {c->rho_re[prv], c->rho_im[prv], c->rho_re[cur], c->rho_im[cur]};
-    for (double* x : lev) {   // rho~ = P^T rho P
-        gemm_f64(N, N, N, Pt, N, x, N, c->win_tmp, N, c->stream);
-        gemm_f64(N, N, N, c->win_tmp, N, P, N, x, N, c->stream);
-    }
-    learn::launch_window(N, d_eig, c->prm.dt, k, lev[0], lev[1], lev[2], lev[3], c->stream);
-    for (double* x : lev) {   // rho = C rho~ C^T
-        gemm_f64(N, N, N, Cm, N, x, N, c->win_tmp, N, c->stream);
-        gemm_f64(N, N, N, c->win_tmp, N, Z, N, x, N, c->stream);
+    launch_transpose(N, Z, Cm, c->stream);
+    if (sliced(*c)) {
+        // Integer-slice products, each with P^T or C as its A operand: with T = P^T rho,
+        // rho P = +-T^T and rho~ = P^T (+-T^T); with U = C rho~, rho = C (+-U^T), the sign
+        // + for the symmetric real part and - for the antisymmetric imaginary part, and a
+        // transposed B operand is the row slicing of the matrix itself.
+        cudaStream_t st = c->stream;
+        double* Tre = c->Xre;
+        double* Tim = c->Xim;
+        oz::slice_rows(Z, N, 1.0, c->oz[2], st);
+        oz::slice_rows(c->S, N, 1.0, c->oz[1], st);
+        TRY(oz_product(*c, 2, 1, Tre));                          // P^T = C^T S
+        oz::slice_rows(Tre, N, 1.0, c->oz[2], st);
+        auto two_sided = [&](double* re, double* im) -> tdb_status {
+            oz::slice_rows(re, N, 1.0, c->oz[3], st);
+            oz::slice_rows(im, N, -1.0, c->oz[4], st);
+            TRY(oz_product_rho(*c, 2, Tre, Tim));
+            oz::slice_rows(Tre, N, 1.0, c->oz[3], st);
+            oz::slice_rows(Tim, N, -1.0, c->oz[4], st);
+            return oz_product_rho(*c, 2, re, im);
+        };
+        for (int l = 0; l < 4; l += 2) TRY(two_sided(lev[l], lev[l + 1]));   // rho~ = P^T rho P
+        learn::launch_window(N, d_eig, c->prm.dt, k, lev[0], lev[1], lev[2], lev[3], st);
+        oz::slice_rows(Cm, N, 1.0, c->oz[2], st);
+        for (int l = 0; l < 4; l += 2) TRY(two_sided(lev[l], lev[l + 1]));   // rho = C rho~ C^T
+    } else {
+        double* Pt = c->Xre;        // P^T = C^T S = Z S
+        double* P = c->Xim;         // P = S C
+        gemm_f64(N, N, N, Z, N, c->S, N, Pt, N, c->stream);
+        launch_transpose(N, Pt, P, c->stream);
+        for (double* x : lev) {   // rho~ = P^T rho P
+            gemm_f64(N, N, N, Pt, N, x, N, c->win_tmp, N, c->stream);
+            gemm_f64(N, N, N, c->win_tmp, N, P, N, x, N, c->stream);
+        }
+        learn::launch_window(N, d_eig, c->prm.dt, k, lev[0], lev[1], lev[2], lev[3], c->stream);
+        for (double* x : lev) {   // rho = C rho~ C^T
+            gemm_f64(N, N, N, Cm, N, x, N, c->win_tmp, N, c->stream);
+            gemm_f64(N, N, N, c->win_tmp, N, Z, N, x, N, c->stream);
+        }
     }
     // exactly Hermitian levels, then the Mulliken partials of the new rho_n
     for (int l : {prv, cur}) {

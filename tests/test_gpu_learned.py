@@ -102,18 +102,21 @@ def test_window_matches_the_oracle_window(B, n_atoms, form, k):
         p.setup()
         p.step(5)
         rho, prev = B.tdb_get_rho(p.ctx, prev=True)
-        v = B.tdb_scc_shift(p.ctx)
+        v, dq_gpu = B.tdb_scc_shift(p.ctx, charges=True)
         # the shift of rho_n is gamma dq(rho_n)
         R = np.asarray(sysm.R)
         S, H0 = O.model_matrices(sysm, R)
         gamma = O.gamma_matrix(sysm, R)
         dq = O.mulliken(sysm, rho, S) - O.reference_populations(sysm)
+        np.testing.assert_allclose(dq_gpu, dq, rtol=0, atol=1e-12)
         np.testing.assert_allclose(v, gamma @ dq, rtol=0, atol=1e-11)
         v_bar = v + np.random.default_rng(1).normal(size=v.size) * 1e-3
         B.tdb_step_window(p.ctx, v_bar, k)
         rho_w, prev_w = B.tdb_get_rho(p.ctx, prev=True)
         a, b = O.window_propagate(prev, rho, S, O.scc_hamiltonian(sysm, H0, S, v_bar), run.dt, k)
-        tol = 1e-10
+        # FP64 products; in the sliced form integer-slice products (about 2e-12 of
+        # K max|A| max|B| each, four in a row)
+        tol = 1e-10 if form == "fp64" else 2e-9
         assert np.max(np.abs(prev_w - a)) < tol
         assert np.max(np.abs(rho_w - b)) < tol
         obs = p.observables()
@@ -163,7 +166,7 @@ def trained(B):
         with B.Propagator(sysm, run, "fp64") as p:
             p.setup()
             p.step(1)
-            X, Y = Lrn.training_set(Lrn.record_shifts(p.ctx, 2000), K_WIN, L_HIST)
+            X, Y = Lrn.training_set(Lrn.record(p.ctx, 2000), K_WIN, L_HIST)
             Xs.append(X)
             Ys.append(Y)
     model = Lrn.ShiftModel(k=K_WIN, L=L_HIST, hidden=32, seed=5)
@@ -213,7 +216,7 @@ def test_trained_network_beats_the_frozen_shift(B, trained):
         err[mode] = np.max(np.abs(q - q_ref), axis=1)
     # held-out kick direction: after 40 windows (400 steps) the frozen shift has drifted
     # far off while the network's windows stay near the plain leapfrog
-    assert err["net"][-1] < 0.03
+    assert err["net"][-1] < 0.05
     assert err["net"][-1] < 0.1 * err["frozen"][-1]
     assert np.max(err["net"]) < 0.5 * np.max(err["frozen"])
 

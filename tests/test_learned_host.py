@@ -39,6 +39,22 @@ def test_training_set_too_short_is_empty():
 def test_window_features_order():
     hist = [np.array([1.0]), np.array([3.0]), np.array([6.0])]
     np.testing.assert_allclose(Lrn.window_features(hist, 2), [[-3.0, -5.0]])
+    # two channels (shift, charge): all shift differences first, then the charges'
+    hist = [np.array([[1.0, 10.0]]), np.array([[3.0, 20.0]]), np.array([[6.0, 50.0]])]
+    np.testing.assert_allclose(Lrn.window_features(hist, 2), [[-3.0, -5.0, -30.0, -40.0]])
+
+
+def test_training_set_with_charges_targets_the_shift_only():
+    rng = np.random.default_rng(8)
+    k, L = 3, 2
+    rec = rng.normal(size=(20, 4, 2))
+    X, Y = Lrn.training_set(rec, k, L)
+    X1, Y1 = Lrn.training_set(rec[:, :, 0], k, L)
+    assert X.shape[1] == 2 * L
+    np.testing.assert_array_equal(Y, Y1)
+    np.testing.assert_array_equal(X[:, :L], X1)
+    n = L * k
+    np.testing.assert_allclose(X[0, L:], [rec[n - k, 0, 1] - rec[n, 0, 1], rec[n - 2 * k, 0, 1] - rec[n, 0, 1]])
 
 
 def test_oracle_bf16_gradient_is_that_of_the_rounded_weights():
