@@ -340,8 +340,10 @@ def c5_runs(B, torch, k=16, L=8, hidden=64, n_train=4, train_steps=1200, windows
         for _ in range(windows):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
+            torch.cuda.nvtx.range_push("c5_plain")
             B.tdb_step(p.ctx, k)
             torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
             t_plain.append(time.perf_counter() - t0)
             o = p.observables()
             q_ref.append(o["charges"])
@@ -358,8 +360,10 @@ def c5_runs(B, torch, k=16, L=8, hidden=64, n_train=4, train_steps=1200, windows
             for _ in range(windows):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
+                torch.cuda.nvtx.range_push(f"c5_window_{mode}")
                 lp.run(1)
                 torch.cuda.synchronize()
+                torch.cuda.nvtx.range_pop()
                 t_win.append(time.perf_counter() - t0)
                 o = p.observables()
                 q.append(o["charges"])
@@ -370,7 +374,7 @@ def c5_runs(B, torch, k=16, L=8, hidden=64, n_train=4, train_steps=1200, windows
         emu = np.max(np.abs(np.array(mu) - mu_ref), axis=1)
         out[mode] = {"max_charge_err": float(eq.max()), "final_charge_err": float(eq[-1]),
                      "max_dipole_err_au": float(emu.max()), "final_dipole_err_au": float(emu[-1]),
-                     "ms_per_window": 1000.0 * float(np.median(t_win[1:]))}
+                     "ms_per_window": 1000.0 * float(np.median(t_win[1:] or t_win))}
     # the judge at the stated dipole bound, every fourth window
     p = start()
     try:
@@ -473,6 +477,10 @@ def main():
     ap.add_argument("--c4-probes", type=int, default=64, help="pump-probe scan size (0: skip)")
     ap.add_argument("--c4-steps", type=int, default=200, help="timed post-kick steps per probe")
     ap.add_argument("--no-c5", action="store_true", help="skip the learned-form section")
+    ap.add_argument("--c5-runs", type=int, default=4, help="learned form: training runs")
+    ap.add_argument("--c5-steps", type=int, default=1200, help="learned form: steps per training run")
+    ap.add_argument("--c5-epochs", type=int, default=20)
+    ap.add_argument("--c5-windows", type=int, default=12)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -512,7 +520,8 @@ def main():
         c4 = None
         if args.c4_probes > 0:
             c4 = c4_runs(B, torch, args.c4_probes, args.c4_steps)
-        c5 = None if args.no_c5 else c5_runs(B, torch)
+        c5 = None if args.no_c5 else c5_runs(B, torch, n_train=args.c5_runs, train_steps=args.c5_steps,
+                                               windows=args.c5_windows, epochs=args.c5_epochs)
         if dist:
             dist.barrier()
     clocks = clk.summary()
