@@ -229,7 +229,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int quarter = warp & 3;
         const int row = m0 + quarter * 32 + lane;
         const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
-        for (int c = warp >> 2; c < BN / 32; c += kThreads / 128) {
+        for (int c = warp >> 2; c < (BN + 31) / 32; c += kThreads / 128) {
+            // columns of this chunk inside the tile (a 176-wide tile ends in a 16-column
+            // chunk; the TMEM columns read past it belong to the next accumulator or to
+            // the unused end of the allocation) and inside the matrix
+            const int lim = min(min(32, BN - c * 32), p.N - (n0 + c * 32));
             uint32_t r[32];
             tmem_ld32(tmem + lane_off + c * 32, r);
             float v[32];
@@ -267,7 +271,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (row < p.M)
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
-                        if (col0 + j < p.N) m = fmaxf(m, fabsf(v[j]));
+                        if (j < lim) m = fmaxf(m, fabsf(v[j]));
                 for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
                 if (lane == 0)
                     atomicMax(reinterpret_cast<unsigned long long*>(&p.max_out[blockIdx.z]),
@@ -276,7 +280,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (row >= p.M) continue;
             if (P.mode == 0) {
                 float* out = P.C + static_cast<size_t>(row) * P.ldc + col0;
-                if (col0 + 32 <= p.N && (P.ldc & 3) == 0) {
+                if (lim == 32 && (P.ldc & 3) == 0) {
 #pragma unroll
                     for (int j = 0; j < 32; j += 4)
                         *reinterpret_cast<float4*>(out + j) =
@@ -284,7 +288,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 } else {
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
-                        if (col0 + j < p.N) out[j] = v[j];
+                        if (j < lim) out[j] = v[j];
                 }
             } else {
                 // delta M and M = M_gs + delta M, both re-split into A pieces; 16-byte
@@ -293,7 +297,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const float* mg = p.Mgs + static_cast<size_t>(row) * p.ld_mgs + col0;
                 const size_t ob = static_cast<size_t>(row) * p.ld_out + col0;
                 bool fine = true;
-                const bool vec = col0 + 32 <= p.N && (p.ld_mgs & 3) == 0 && (p.ld_out & 7) == 0 &&
+                const bool vec = lim == 32 && (p.ld_mgs & 3) == 0 && (p.ld_out & 7) == 0 &&
                                  (p.col_m & 7) == 0;
                 if (vec) {
 #pragma unroll
@@ -330,8 +334,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 } else {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const int col = col0 + j;
-                        if (col >= p.N) continue;
+                        if (j >= lim) continue;
                         uint16_t q[3];
                         fine &= split_value<SCHEME>(v[j] * s_dm, p.bf16, q);
 #pragma unroll
@@ -472,12 +475,14 @@ cudaError_t prepare() {
     if (e == cudaSuccess) e = set_smem<kHead3, 128>();
     if (e == cudaSuccess) e = set_smem<kHiLo, 256>();
     if (e == cudaSuccess) e = set_smem<kHead3, 256>();
+    if (e == cudaSuccess) e = set_smem<kHiLo, 176>();
+    if (e == cudaSuccess) e = set_smem<kHead3, 176>();
     return e;
 }
 
 cudaError_t launch(int scheme, const Maps& m, const GemmParams& p, int nparts, cudaStream_t st,
                    int bn) {
-    if (nparts < 1 || nparts > kMaxParts || (bn != 64 && bn != 128 && bn != 256))
+    if (nparts < 1 || nparts > kMaxParts || (bn != 64 && bn != 128 && bn != 176 && bn != 256))
         return cudaErrorInvalidValue;
     for (int z = 0; z < nparts; ++z)
         if (p.part[z].K < 1 || tmem_cols(scheme, p.part[z].K, bn) > 512) return cudaErrorInvalidValue;
@@ -492,6 +497,11 @@ cudaError_t launch(int scheme, const Maps& m, const GemmParams& p, int nparts, c
             k_split_gemm<kHiLo, 256><<<grid, kThreads, smem_total<kHiLo, 256>(), st>>>(m, p);
         else
             k_split_gemm<kHead3, 256><<<grid, kThreads, smem_total<kHead3, 256>(), st>>>(m, p);
+    } else if (bn == 176) {
+        if (scheme == kHiLo)
+            k_split_gemm<kHiLo, 176><<<grid, kThreads, smem_total<kHiLo, 176>(), st>>>(m, p);
+        else
+            k_split_gemm<kHead3, 176><<<grid, kThreads, smem_total<kHead3, 176>(), st>>>(m, p);
     } else {
         if (scheme == kHiLo)
             k_split_gemm<kHiLo, 128><<<grid, kThreads, smem_total<kHiLo, 128>(), st>>>(m, p);

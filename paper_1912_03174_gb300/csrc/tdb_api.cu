@@ -627,11 +627,15 @@ tdb_status setup_tensor(Ctx& c) {
     return TDB_OK;
 }
 
-// tile width of the X product (128: measured faster than 64-wide tiles for every scheme)
 // Width of the X tiles: 128 x 256 tiles read half as much shared memory per MMA as
 // 128 x 128 ones (the split products re-read each piece several times, and shared-memory
-// bandwidth is what bounds the 128-wide tiles); small systems keep 128.
-int xbn(const Ctx& c) { return c.N >= 512 ? 256 : 128; }
+// bandwidth is what bounds the 128-wide tiles); small systems keep 128.  For
+// 768 < N <= 1024 (one K slice) 176-wide tiles give 3 parts x 8 x 6 = 144 CTAs, one wave
+// on the 152 SMs (256-wide tiles: 96).
+int xbn(const Ctx& c) {
+    if (c.N > 768 && c.N <= 1024) return 176;
+    return c.N >= 512 ? 256 : 128;
+}
 
 tdb_status build_maps(Ctx& c) {
     CK(tc::prepare());

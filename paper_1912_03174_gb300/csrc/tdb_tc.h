@@ -64,7 +64,7 @@ uint32_t idesc_f16(int bf16, int bn = 128);
 size_t smem_bytes(int scheme);
 // Once per process and device before the first launch (and outside stream capture).
 cudaError_t prepare();
-// Output tiles of 128 x bn (bn = 64, 128 or 256; the B maps must have bn-row boxes); nparts <=
+// Output tiles of 128 x bn (bn = 64, 128, 176 or 256; the B maps must have bn-row boxes); nparts <=
 // kMaxParts.  kHead3 needs (ceil(K / kHeadK) + 1) bn <= 512 TMEM columns for every part
 // (cudaErrorInvalidValue otherwise).
 cudaError_t launch(int scheme, const Maps& m, const GemmParams& p, int nparts, cudaStream_t st,

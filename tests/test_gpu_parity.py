@@ -224,6 +224,29 @@ def test_reduced_precision_forms_match_oracle(B, n_atoms, form, tol_mu, tol_rho)
     assert g["obs"]["herm_err"] == 0.0
 
 
+_ORACLE_920 = {}
+
+
+@pytest.mark.parametrize("form,tol_mu,tol_rho", [("fp16x6", 1e-6, 1e-6), ("bf16x3", 2e-5, 2e-5)])
+def test_reduced_forms_with_176_wide_x_tiles_match_oracle(B, form, tol_mu, tol_rho):
+    # 230 atoms, N = 920: the X products run in 128 x 176 tiles (six column tiles, the
+    # last one 40 columns wide, its TMA box reaching past the matrix)
+    sysm = I.small_flake(230, seed=8)
+    run = I.Run(dt=0.2, n_steps=0, scc=True, kick=1e-3, kT=I.SCC_KT)
+    n = 40
+    if "tr" not in _ORACLE_920:
+        _ORACLE_920["tr"] = _oracle(sysm, run, n)[2]
+    tr = _ORACLE_920["tr"]
+    g = _gpu_run(B, sysm, run, n, form)
+    mu = np.vstack([g["hist"], g["obs"]["dipole"][None, :]])
+    err = np.max(np.abs(mu - tr.dipole))
+    assert err < tol_mu, err
+    assert np.max(np.abs(g["rho"] - tr.rho)) < tol_rho
+    assert np.max(np.abs(g["obs"]["charges"] - tr.charges[-1])) < tol_rho
+    assert abs(g["obs"]["trace_re"] - sysm.n_electrons) / sysm.n_electrons < 1e-8
+    assert g["obs"]["herm_err"] == 0.0
+
+
 @pytest.mark.parametrize("form", ["fp32", "fp16x6", "bf16x3"])
 def test_reduced_form_checkpoint_resume_is_bitwise(B, form):
     # the state of a reduced form carries its FP32-pair master and scale bookkeeping
