@@ -632,9 +632,22 @@ tdb_status setup_tensor(Ctx& c) {
 // bandwidth is what bounds the 128-wide tiles); small systems keep 128.  For
 // 768 < N <= 1024 (one K slice) 176-wide tiles give 3 parts x 8 x 6 = 144 CTAs, one wave
 // on the 152 SMs (256-wide tiles: 96).
+// tune_x replaces this starting guess by the measured fastest width.
 int xbn(const Ctx& c) {
+    if (c.x_bn) return c.x_bn;
     if (c.N > 768 && c.N <= 1024) return 176;
     return c.N >= 512 ? 256 : 128;
+}
+
+// Tensor maps of the X product's operands for B tiles of width bn.
+bool make_x_maps(const Ctx& c, int bn, tc::Maps& m) {
+    const int N = c.N, Np = c.Np, b = piece_bf16(c);
+    bool ok = true;
+    for (int q = 0; q < c.npieces; ++q)
+        ok = ok && tc::make_map(&m.a[q], c.pc_am[q], N, 2 * Np, 2 * Np, b) &&
+             tc::make_map(&m.b[0][q], c.pc_bre[q], N, 2 * Np, 2 * Np, b, bn) &&
+             tc::make_map(&m.b[1][q], c.pc_bim[q], N, Np, Np, b, bn);
+    return ok;
 }
 
 tdb_status build_maps(Ctx& c) {
@@ -643,11 +656,9 @@ tdb_status build_maps(Ctx& c) {
     bool ok = true;
     for (int q = 0; q < c.npieces; ++q) {
         ok = ok && tc::make_map(&c.maps_dm.a[q], c.pc_sinv[q], N, N, Np, b) &&
-             tc::make_map(&c.maps_dm.b[0][q], c.pc_dh[q], N, N, Np, b, 64) &&
-             tc::make_map(&c.maps_x.a[q], c.pc_am[q], N, 2 * Np, 2 * Np, b) &&
-             tc::make_map(&c.maps_x.b[0][q], c.pc_bre[q], N, 2 * Np, 2 * Np, b, xbn(c)) &&
-             tc::make_map(&c.maps_x.b[1][q], c.pc_bim[q], N, Np, Np, b, xbn(c));
+             tc::make_map(&c.maps_dm.b[0][q], c.pc_dh[q], N, N, Np, b, 64);
     }
+    ok = ok && make_x_maps(c, xbn(c), c.maps_x);
     if (!ok) {
         set_err("cuTensorMapEncodeTiled failed");
         return TDB_ERR_CUDA;
@@ -844,6 +855,99 @@ tdb_status enqueue_step_md(Ctx& c, int cur, bool euler, int* launches, StepTimer
 }
 
 // Enqueue one propagation step for rho_n in buffer `cur` (eq:leapfrog, eq:eomrho).
+// Parameters of the X product for tiles of width bn; returns the number of parts.
+// Parts: X_a = dM rho_ref and X_re = M Re(rho - rho_ref) (the real part of X is their
+// sum), then X_im = M Im rho; each cut into x_split K slices.
+int x_params(Ctx& c, int bn, tc::GemmParams& x) {
+    const int N = c.N, Np = c.Np;
+    const bool h3 = head3(c);
+    x = tc::GemmParams{};
+    x.M = N;
+    x.N = N;
+    x.idesc = tc::idesc_f16(piece_bf16(c), bn);
+    x.bf16 = piece_bf16(c);
+    x.err = c.d_err;
+    x.max_out = h3 ? c.dyn->max_x : nullptr;
+    const int ns = x_split(c);
+    const int kc = ((N + ns - 1) / ns + 63) / 64 * 64;
+    int nparts = 0;
+    for (int prod = 0; prod < 3; ++prod)
+        for (int sl = 0; sl < ns; ++sl) {
+            const int off = sl * kc, len = std::min(kc, N - off);
+            tc::GemmPart& P = x.part[nparts];
+            P.k0_a = (prod == 0 ? 0 : Np) + off;
+            P.k0_b = (prod == 1 ? Np : 0) + off;
+            P.K = len;
+            P.mode = 0;
+            P.C = c.xp[nparts];
+            P.ldc = N;
+            P.b_set = prod == 2 ? 1 : 0;
+            if (h3) {
+                // dM pieces carry s_dm, M pieces s_m; rho_ref pieces s_ref, dRho s_rho
+                P.sa = c.s_m;
+                P.sa_dev = prod == 0 ? &c.dyn->s_dm : nullptr;
+                P.sb = c.s_ref;
+                P.sb_dev = prod == 0 ? nullptr : &c.dyn->s_rho;
+            } else {
+                P.sa = c.s_m;
+                P.sb = c.s_rho;
+            }
+            ++nparts;
+        }
+    return nparts;
+}
+
+// Autotuner of the X product's tile width (tensor-core forms), run once per context
+// before the first step is captured: each candidate width times three launches on the
+// context's current operands (CUDA events on its stream) and the fastest is kept.  Every
+// output element keeps its K order whatever the width, so the choice changes the time,
+// not the result.  The launches write only the X partials and the X maxima, which the
+// next step overwrites and resets.
+tdb_status tune_x(Ctx& c) {
+    static const int cand[] = {128, 176, 256};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 0.f;
+    int best_bn = 0;
+    tdb_status st = TDB_OK;
+    for (int bn : cand) {
+        tc::Maps m{};
+        tc::GemmParams x{};
+        if (!make_x_maps(c, bn, m)) continue;   // width not encodable for this size
+        const int np = x_params(c, bn, x);
+        cudaError_t e = tc::launch(c.scheme, m, x, np, c.stream, bn);   // warm-up
+        if (e == cudaErrorInvalidValue) {                               // width not valid here
+            cudaGetLastError();
+            continue;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e0, c.stream);
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = tc::launch(c.scheme, m, x, np, c.stream, bn);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c.stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            set_err("X tile tuning: %s", cudaGetErrorString(e));
+            st = TDB_ERR_CUDA;
+            break;
+        }
+        if (!best_bn || ms < best) {
+            best = ms;
+            best_bn = bn;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != TDB_OK) return st;
+    if (best_bn) c.x_bn = best_bn;
+    if (!make_x_maps(c, xbn(c), c.maps_x)) {
+        set_err("cuTensorMapEncodeTiled failed");
+        return TDB_ERR_CUDA;
+    }
+    return TDB_OK;
+}
+
 tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* tm = nullptr) {
     const int prv = cur ^ 1;
     const double factor = euler ? c.prm.dt : 2.0 * c.prm.dt;
@@ -915,40 +1019,8 @@ tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* t
         CK(tc::launch(c.scheme, c.maps_dm, g, 1, c.stream, 64));
         ++n;
         tc::GemmParams x{};
-        x.M = N;
-        x.N = N;
-        x.idesc = tc::idesc_f16(b, xbn(c));
-        x.bf16 = b;
-        x.err = c.d_err;
-        x.max_out = h3 ? c.dyn->max_x : nullptr;
-        // parts: X_a = dM rho_ref and X_re = M Re(rho - rho_ref) (the real part of X is their
-        // sum), then X_im = M Im rho; each cut into ns K slices
         const int ns = x_split(c);
-        const int kc = ((N + ns - 1) / ns + 63) / 64 * 64;
-        int nparts = 0;
-        for (int prod = 0; prod < 3; ++prod)
-            for (int sl = 0; sl < ns; ++sl) {
-                const int off = sl * kc, len = std::min(kc, N - off);
-                tc::GemmPart& P = x.part[nparts];
-                P.k0_a = (prod == 0 ? 0 : Np) + off;
-                P.k0_b = (prod == 1 ? Np : 0) + off;
-                P.K = len;
-                P.mode = 0;
-                P.C = c.xp[nparts];
-                P.ldc = N;
-                P.b_set = prod == 2 ? 1 : 0;
-                if (h3) {
-                    // dM pieces carry s_dm, M pieces s_m; rho_ref pieces s_ref, dRho s_rho
-                    P.sa = c.s_m;
-                    P.sa_dev = prod == 0 ? &c.dyn->s_dm : nullptr;
-                    P.sb = c.s_ref;
-                    P.sb_dev = prod == 0 ? nullptr : &c.dyn->s_rho;
-                } else {
-                    P.sa = c.s_m;
-                    P.sb = c.s_rho;
-                }
-                ++nparts;
-            }
+        const int nparts = x_params(c, xbn(c), x);
         MARK("tc_gemm_X");
         CK(tc::launch(c.scheme, c.maps_x, x, nparts, c.stream, xbn(c)));
         ++n;
@@ -999,6 +1071,7 @@ tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* t
 
 tdb_status ensure_graph(Ctx& c, int cur) {
     if (c.graph[cur]) return TDB_OK;
+    if (tensor(c) && !c.x_bn && !c.graph[cur ^ 1]) TRY(tune_x(c));
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
     int nl = 0;

@@ -122,6 +122,7 @@ struct Ctx {
     int* d_err = nullptr;        // bounded-wait time-out / piece overflow flag
     float s_sinv = 1, s_dh = 1, s_m = 1, s_rho = 1, s_ref = 1;   // power-of-two operand scales
     tc::Maps maps_dm{}, maps_x{};
+    int x_bn = 0;                // X tile width chosen by tune_x (0: not tuned yet)
 
     // host-side trajectory state
     int cur = 0;                 // index of rho_n in rho_re/rho_im
