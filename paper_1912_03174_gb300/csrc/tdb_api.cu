@@ -1877,8 +1877,6 @@ tdb_status tdb_dipole_history(tdb_ctx* c, double* out, long cap, long* n_out) {
                        c->stream));
     CK(cudaStreamSynchronize(c->stream));
     // steps n-m .. n-1 (n counted from the last ground state / set_state)
-    const long long dir = c->prm.dt > 0 ? 1 : 1;
-    (void)dir;
     for (long long j = 0; j < m; ++j) {
         const long long k = c->n - m + j;
         long long slot = k % hc;
