@@ -100,12 +100,43 @@ def _peaks():
             "sm_max_mhz": 2070.0}, "fallback"
 
 
+# cuBLAS rates measured on a GB300 with `bench.py --measure-peaks`
+# (profiles/gemm_peaks_N8192.md): context for the SIMT forms' ALU roofline.
+CUBLAS_TFLOPS = {"f64": 1.072, "f32": 69.7, "tf32": 1050.5}
+
+
 def alu_peak_tflops(kind: str, sm_mhz: float) -> float:
     """SIMT peaks from unit counts: 152 SMs x 128 FP32 lanes x 2 flop/FMA x clock;
     FP64 at the GB300 nominal 1.25 TFLOP/s (its FP64 units are 1/64 of FP32)."""
     if kind == "f32":
         return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     return 1.25
+
+
+def measure_peaks(torch, n=8192):
+    """cuBLAS GEMM rates on this GPU (TFLOP/s at n x n x n, CUDA events): FP64 (DGEMM),
+    FP32 with TF32 off (SGEMM) and TF32 — the denominators that the measured-peaks file
+    does not carry, for the SIMT FP64 and FP32 forms."""
+    out = {}
+    for name, dt, tf32, reps in (("fp64", torch.float64, False, 3), ("fp32", torch.float32, False, 10),
+                                 ("tf32", torch.float32, True, 20)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        g = torch.Generator(device="cuda").manual_seed(7)
+        a = torch.randn(n, n, dtype=dt, device="cuda", generator=g)
+        b = torch.randn(n, n, dtype=dt, device="cuda", generator=g)
+        c = torch.empty(n, n, dtype=dt, device="cuda")
+        torch.matmul(a, b, out=c)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            torch.matmul(a, b, out=c)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name + "_tflops"] = 2.0 * n ** 3 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12
+        del a, b, c
+    torch.backends.cuda.matmul.allow_tf32 = False
+    return out
 
 
 class ClockSampler:
@@ -477,6 +508,8 @@ def main():
     ap.add_argument("--c4-probes", type=int, default=64, help="pump-probe scan size (0: skip)")
     ap.add_argument("--c4-steps", type=int, default=200, help="timed post-kick steps per probe")
     ap.add_argument("--no-c5", action="store_true", help="skip the learned-form section")
+    ap.add_argument("--measure-peaks", action="store_true",
+                    help="print cuBLAS FP64/FP32/TF32 GEMM rates and exit")
     ap.add_argument("--c5-runs", type=int, default=4, help="learned form: training runs")
     ap.add_argument("--c5-steps", type=int, default=1200, help="learned form: steps per training run")
     ap.add_argument("--c5-epochs", type=int, default=20)
@@ -497,6 +530,11 @@ def main():
     import torch
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if args.measure_peaks:
+        with ClockSampler(local) as clk:
+            peaks = measure_peaks(torch)
+        print(json.dumps({"cublas_gemm_n8192": peaks, "clocks": clk.summary()}), flush=True)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -556,7 +594,8 @@ def main():
         roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": None,
                 "peak_source": f"derived from unit counts at {peaks.get('sm_max_mhz', 2070.0):.0f} MHz"
-                if kind == "f32" else "GB300 nominal FP64 1.25 TFLOP/s"}
+                if kind == "f32" else "GB300 nominal FP64 1.25 TFLOP/s",
+                "cublas_tflops": CUBLAS_TFLOPS[kind], "frac_of_cublas": ach / CUBLAS_TFLOPS[kind]}
     else:
         key = {"fp64": "update_f64", "fp32": "update_f32", "fp16x6": "update_fp16x6"}.get(head, "update_tc")
         if name == "split_dH":
