@@ -223,6 +223,28 @@ def run_form(B, torch, sysm, run, precision, steps, warmup, flush, stream):
                 launches=launches)
 
 
+def form_summary(res: dict, forms, n_electrons: float) -> dict:
+    """Per form: steps/s, and against the FP64 form (when it ran) the largest dipole
+    error over the run and the charge error at its end; the relative trace drift
+    |Tr(rho S) - N_e| / N_e and the Hermiticity error at the end."""
+    ref = res.get("fp64")
+    out = {}
+    for f in forms:
+        r = res[f]
+        o = r["obs"]
+        out[f] = {
+            "steps_per_s": 1000.0 / float(np.mean(r["ms"])),
+            "max_dipole_err_vs_fp64_au": (float(np.max(np.abs(r["hist"] - ref["hist"])))
+                                          if ref is not None else None),
+            "final_charge_err_vs_fp64": (float(np.max(np.abs(np.asarray(o["charges"])
+                                                             - np.asarray(ref["obs"]["charges"]))))
+                                         if ref is not None else None),
+            "trace_rel_drift": abs(float(o["trace_re"]) - n_electrons) / n_electrons,
+            "herm_err": float(o["herm_err"]),
+        }
+    return out
+
+
 def replica_timing(ms_step: float, world: int, dist=None):
     """Replicas only: every rank propagates its own copy of the workload, with no
     data-path collective.  The slowest rank's time per step sets the pace (a max over
@@ -614,10 +636,7 @@ def main():
                    "fp64_steps_per_s": (1000.0 / ms64) if ms64 else None,
                    "speedup_vs_fp64": (ms64 / float(np.mean(r['ms']))) if ms64 else None,
                    "max_dipole_err_vs_fp64_au": err,
-                   "forms": {f: {"steps_per_s": 1000.0 / float(np.mean(res[f]["ms"])),
-                                 "max_dipole_err_vs_fp64_au": (float(np.max(np.abs(res[f]["hist"] - res["fp64"]["hist"])))
-                                                               if "fp64" in res else None)}
-                             for f in forms},
+                   "forms": form_summary(res, forms, sysm.n_electrons),
                    "kernel_ms": {f: res[f]["prof"] for f in forms},
                    "n2048": n2048,
                    "pump_probe_c4": c4,
