@@ -428,18 +428,18 @@ def c5_runs(B, torch, k=16, L=8, hidden=64, n_train=4, train_steps=1200, windows
         out[mode] = {"max_charge_err": float(eq.max()), "final_charge_err": float(eq[-1]),
                      "max_dipole_err_au": float(emu.max()), "final_dipole_err_au": float(emu[-1]),
                      "ms_per_window": 1000.0 * float(np.median(t_win[1:] or t_win))}
-    # the judge at the stated dipole bound, every fourth window
+    # the referee at the stated dipole bound, every fourth window
     p = start()
     try:
-        lp = Lrn.LearnedPropagator(p.ctx, model, mode="net", judge_every=4, bound=float("inf"),
+        lp = Lrn.LearnedPropagator(p.ctx, model, mode="net", referee_every=4, bound=float("inf"),
                                    dipole_bound=1e-5)
         lp.warm_up()
         lp.run(windows)
         st = lp.stats
-        judge = {"dipole_bound_au": 1e-5, "judge_every": 4, "windows_run": st.windows,
-                 "judged": st.judged, "taken_over": st.taken_over,
+        referee = {"dipole_bound_au": 1e-5, "referee_every": 4, "windows_run": st.windows,
+                 "refereed": st.refereed, "taken_over": st.taken_over,
                  "plain_steps_after_warm_up": st.plain_steps - L * k,
-                 "judge_dipole_err_au": st.judge_dipole_err, "judge_charge_err": st.judge_err}
+                 "referee_dipole_err_au": st.referee_dipole_err, "referee_charge_err": st.referee_err}
     finally:
         p.close()
     model.close()
@@ -456,7 +456,7 @@ def c5_runs(B, torch, k=16, L=8, hidden=64, n_train=4, train_steps=1200, windows
             "steps_per_s_plain": 1000.0 * k / ms_plain,
             "window_vs_plain_speedup": ms_plain / ms_win,
             "errors_vs_plain": out,
-            "judge": judge,
+            "referee": referee,
             "gain_charge_err_frozen_over_net": out["frozen"]["max_charge_err"] / max(out["net"]["max_charge_err"], 1e-300),
             "timing": "host clock between device synchronisations (window: shift readback, "
                       "network inference, eigensolve and products)"}

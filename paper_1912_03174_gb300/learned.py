@@ -9,8 +9,8 @@ the library's own forward and backward kernels) is fitted on records of plain le
 runs (eq:leapfrog): its input for atom A at the start n of a window is
 (v_A(n - j k) - v_A(n)) and (dq_A(n - j k) - dq_A(n)), j = 1..L (2 L values), its
 target the mean of v_A over the steps n..n+k-1 minus v_A(n).  The plain leapfrog
-re-runs sampled windows from the same state as a judge; when the window's charges or
-dipole differ from the judge's by more than their bounds the judge's state is kept and
+re-runs sampled windows from the same state as a referee; when the window's charges or
+dipole differ from the referee's by more than their bounds the referee's state is kept and
 the run continues with plain steps.
 
 Everything here is host orchestration over the C ABI; each step runs in the library.
@@ -107,25 +107,25 @@ class ShiftModel:
 @dataclass
 class WindowStats:
     windows: int = 0
-    judged: int = 0
+    refereed: int = 0
     taken_over: bool = False
     plain_steps: int = 0
-    judge_err: list = field(default_factory=list)          # max |dq| per judged window
-    judge_dipole_err: list = field(default_factory=list)   # max |d mu| per judged window
+    referee_err: list = field(default_factory=list)          # max |dq| per refereed window
+    referee_dipole_err: list = field(default_factory=list)   # max |d mu| per refereed window
 
 
 class LearnedPropagator:
     """Advance ctx (FP64 or FP64_SLICED form, frozen nuclei, no field) in windows of
     model.k steps.  mode 'net' uses the network's shift, 'frozen' the shift at the
-    window's start (the method without the network).  judge_every: every so many
+    window's start (the method without the network).  referee_every: every so many
     windows a clone of the context takes the k plain steps instead and the charges
     (max |dq|) and dipoles (max |d mu|, a.u.) are compared; above bound or
-    dipole_bound the judge's state is kept and plain steps follow."""
+    dipole_bound the referee's state is kept and plain steps follow."""
 
-    def __init__(self, ctx: B.Context, model: ShiftModel, mode="net", judge_every=0, bound=1e-2,
+    def __init__(self, ctx: B.Context, model: ShiftModel, mode="net", referee_every=0, bound=1e-2,
                  dipole_bound=float("inf")):
         self.ctx, self.model, self.mode = ctx, model, mode
-        self.judge_every, self.bound, self.dipole_bound = judge_every, bound, dipole_bound
+        self.referee_every, self.bound, self.dipole_bound = referee_every, bound, dipole_bound
         self.history = []
         self.stats = WindowStats()
 
@@ -155,24 +155,24 @@ class LearnedPropagator:
                 self.stats.plain_steps += k
                 continue
             vb = self.v_bar()
-            judge = None
-            if self.judge_every and self.stats.windows % self.judge_every == 0:
-                judge = B.tdb_clone(self.ctx)
+            referee = None
+            if self.referee_every and self.stats.windows % self.referee_every == 0:
+                referee = B.tdb_clone(self.ctx)
             B.tdb_step_window(self.ctx, vb, k)
             self.stats.windows += 1
-            if judge is not None:
+            if referee is not None:
                 try:
-                    B.tdb_step(judge, k)
+                    B.tdb_step(referee, k)
                     oa = B.tdb_observables(self.ctx)
-                    ob = B.tdb_observables(judge)
+                    ob = B.tdb_observables(referee)
                     err = float(np.max(np.abs(oa["charges"] - ob["charges"])))
                     derr = float(np.max(np.abs(np.asarray(oa["dipole"]) - np.asarray(ob["dipole"]))))
-                    self.stats.judged += 1
-                    self.stats.judge_err.append(err)
-                    self.stats.judge_dipole_err.append(derr)
+                    self.stats.refereed += 1
+                    self.stats.referee_err.append(err)
+                    self.stats.referee_dipole_err.append(derr)
                     if err > self.bound or derr > self.dipole_bound:
-                        B.tdb_set_state(self.ctx, B.tdb_get_state(judge))
+                        B.tdb_set_state(self.ctx, B.tdb_get_state(referee))
                         self.stats.taken_over = True
                 finally:
-                    B.tdb_destroy(judge)
+                    B.tdb_destroy(referee)
         return self.stats

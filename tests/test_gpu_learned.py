@@ -221,18 +221,18 @@ def test_trained_network_beats_the_frozen_shift(B, trained):
     assert np.max(err["net"]) < 0.5 * np.max(err["frozen"])
 
 
-def test_judge_takes_over_and_continues_as_the_plain_leapfrog(B, trained):
+def test_referee_takes_over_and_continues_as_the_plain_leapfrog(B, trained):
     sysm, d, model = trained
     nw = 6
     q_ref = _plain_reference(B, sysm, d, nw)
-    # a bound below any window error: the judge keeps its own state at the first window
+    # a bound below any window error: the referee keeps its own state at the first window
     # and plain steps follow, which is the plain run bit for bit
-    p, lp, q = _learned_run(B, sysm, d, model, "net", nw, judge_every=2, bound=0.0)
+    p, lp, q = _learned_run(B, sysm, d, model, "net", nw, referee_every=2, bound=0.0)
     p.close()
-    assert lp.stats.taken_over and lp.stats.judged == 1 and lp.stats.windows == 1
+    assert lp.stats.taken_over and lp.stats.refereed == 1 and lp.stats.windows == 1
     assert np.array_equal(q, q_ref)
-    # a loose bound: judged every second window, never taken over
-    p, lp, q = _learned_run(B, sysm, d, model, "net", nw, judge_every=2, bound=1.0)
+    # a loose bound: refereed every second window, never taken over
+    p, lp, q = _learned_run(B, sysm, d, model, "net", nw, referee_every=2, bound=1.0)
     p.close()
-    assert not lp.stats.taken_over and lp.stats.judged == 3 and lp.stats.windows == nw
-    assert all(e < 0.02 for e in lp.stats.judge_err)
+    assert not lp.stats.taken_over and lp.stats.refereed == 3 and lp.stats.windows == nw
+    assert all(e < 0.02 for e in lp.stats.referee_err)

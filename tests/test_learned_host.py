@@ -146,7 +146,7 @@ def test_driver_warms_up_then_runs_windows(monkeypatch):
     fake, ctx, lp = _propagator(monkeypatch, 0.0)
     st = lp.run(5)
     assert fake.plain == 3 * 4 and fake.windows == 5 and ctx.t == 12 + 20
-    assert st.windows == 5 and st.judged == 0 and not st.taken_over
+    assert st.windows == 5 and st.refereed == 0 and not st.taken_over
     assert len(lp.history) == _FakeModel.L + 1
     # the network's shift: v + increment; the frozen mode passes v itself
     np.testing.assert_allclose(lp.v_bar(), 2.0 * ctx.q() + 0.5)
@@ -154,28 +154,28 @@ def test_driver_warms_up_then_runs_windows(monkeypatch):
     np.testing.assert_allclose(lp.v_bar(), 2.0 * ctx.q())
 
 
-def test_judge_samples_every_nth_window_and_keeps_the_window_below_the_bound(monkeypatch):
-    fake, ctx, lp = _propagator(monkeypatch, 1e-3, judge_every=3, bound=1e-2)
+def test_referee_samples_every_nth_window_and_keeps_the_window_below_the_bound(monkeypatch):
+    fake, ctx, lp = _propagator(monkeypatch, 1e-3, referee_every=3, bound=1e-2)
     st = lp.run(7)
-    assert st.judged == 3 and fake.clones == 3 and fake.destroyed == 3   # windows 0, 3, 6
+    assert st.refereed == 3 and fake.clones == 3 and fake.destroyed == 3   # windows 0, 3, 6
     assert not st.taken_over and fake.loaded == 0 and fake.windows == 7
-    np.testing.assert_allclose(st.judge_err, [1e-3, 1e-3, 1e-3], rtol=1e-9)
-    np.testing.assert_allclose(st.judge_dipole_err, [3e-3, 3e-3, 3e-3], rtol=1e-9)
+    np.testing.assert_allclose(st.referee_err, [1e-3, 1e-3, 1e-3], rtol=1e-9)
+    np.testing.assert_allclose(st.referee_dipole_err, [3e-3, 3e-3, 3e-3], rtol=1e-9)
     assert ctx.err == pytest.approx(7e-3)
 
 
-def test_judge_takes_over_on_the_charge_or_the_dipole_bound(monkeypatch):
-    # charges: the judge measures each sampled window from its own start state; window
-    # errors 1e-3, 2e-3, 3e-3, ... and judged windows 1, 3, 5: the second one (3e-3)
+def test_referee_takes_over_on_the_charge_or_the_dipole_bound(monkeypatch):
+    # charges: the referee measures each sampled window from its own start state; window
+    # errors 1e-3, 2e-3, 3e-3, ... and refereed windows 1, 3, 5: the second one (3e-3)
     # exceeds the bound
-    fake, ctx, lp = _propagator(monkeypatch, 1e-3, grow=True, judge_every=2, bound=2.5e-3)
+    fake, ctx, lp = _propagator(monkeypatch, 1e-3, grow=True, referee_every=2, bound=2.5e-3)
     st = lp.run(6)
-    assert st.taken_over and st.judged == 2 and st.windows == 3
-    np.testing.assert_allclose(st.judge_err, [1e-3, 3e-3], rtol=1e-9)
-    assert fake.loaded == 1 and ctx.err == pytest.approx(3e-3)    # the judge's state
+    assert st.taken_over and st.refereed == 2 and st.windows == 3
+    np.testing.assert_allclose(st.referee_err, [1e-3, 3e-3], rtol=1e-9)
+    assert fake.loaded == 1 and ctx.err == pytest.approx(3e-3)    # the referee's state
     assert st.plain_steps == 3 * 4 + 3 * 4                         # warm-up, then plain
     assert ctx.t == 12 + 6 * 4
     # dipole: the charge bound is loose, the dipole one (3 atoms x 1e-3) is not
-    fake, ctx, lp = _propagator(monkeypatch, 1e-3, judge_every=1, bound=1.0, dipole_bound=2e-3)
+    fake, ctx, lp = _propagator(monkeypatch, 1e-3, referee_every=1, bound=1.0, dipole_bound=2e-3)
     st = lp.run(2)
-    assert st.taken_over and st.judged == 1 and ctx.err == 0.0
+    assert st.taken_over and st.refereed == 1 and ctx.err == 0.0
