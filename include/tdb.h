@@ -195,7 +195,12 @@ tdb_status tdb_scc_shift(tdb_ctx* ctx, double* out, double* dq);
  * the window's end, and the dipole history is not written inside a window.  FP64 or
  * FP64_SLICED form, frozen nuclei and no laser field (TDB_ERR_UNSUPPORTED), not right
  * after a ground state, kick or state load (take one tdb_step first: TDB_ERR_STATE).
- * Requires |(eps_a - eps_b) dt| < 1. */
+ * Requires (eps_max - eps_min) |dt| < 1, checked after the eigensolve
+ * (TDB_ERR_UNSUPPORTED).  v_bar: n_atoms host doubles, read during the call; k >= 1
+ * (TDB_ERR_ARG).  A failed eigensolve returns TDB_ERR_CUDA.  The eigensolver workspace
+ * (cuSOLVER's plus N x N doubles) is allocated by the first call (TDB_ERR_NOMEM) and
+ * freed by tdb_destroy, also when the context's workspace is the caller's.  Synchronises
+ * once (after the eigensolve); the rest is asynchronous on the context stream. */
 tdb_status tdb_step_window(tdb_ctx* ctx, const double* v_bar, int k);
 
 /* The per-atom shift network of the learned form (this library's own GPU kernels;
@@ -204,7 +209,13 @@ tdb_status tdb_step_window(tdb_ctx* ctx, const double* v_bar, int k);
  * values), weights used in bfloat16 with FP32 accumulation, FP32 master parameters
  * packed as W1 (n_features x hidden, row-major), b1, W2 (hidden x hidden), b2, w3,
  * b3.  Trained with Adam on the mean squared error.  n_features <= 32, hidden <= 64.
- * X: n x n_features row-major host floats; Y: n host floats. */
+ * X: n x n_features row-major host floats; Y: n host floats; params and grad:
+ * tdb_shiftnet_param_count floats.  Host buffers are read or written during the call
+ * only.  The network owns its device memory and its CUDA stream, and every call
+ * synchronises that stream.  NULL arguments, n < 1, epochs < 1, batch < 1 or lr <= 0
+ * return TDB_ERR_ARG; CUDA failures TDB_ERR_CUDA.  create: uniform weights in
+ * +-sqrt(3 / fan_in) from a splitmix64 stream of seed, zero biases.  set_params also
+ * resets the Adam moments and step count.  destroy(NULL) does nothing. */
 typedef struct tdb_shiftnet tdb_shiftnet;
 tdb_status tdb_shiftnet_create(int n_features, int hidden, unsigned long long seed,
                                tdb_shiftnet** out);
