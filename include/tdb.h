@@ -200,7 +200,8 @@ tdb_status tdb_scc_shift(tdb_ctx* ctx, double* out, double* dq);
  * (TDB_ERR_ARG).  A failed eigensolve returns TDB_ERR_CUDA.  The eigensolver workspace
  * (cuSOLVER's plus N x N doubles) is allocated by the first call (TDB_ERR_NOMEM) and
  * freed by tdb_destroy, also when the context's workspace is the caller's.  Synchronises
- * once (after the eigensolve); the rest is asynchronous on the context stream. */
+ * the context stream twice (before staging v_bar, after the eigensolve); the products
+ * after it are asynchronous. */
 tdb_status tdb_step_window(tdb_ctx* ctx, const double* v_bar, int k);
 
 /* The per-atom shift network of the learned form (this library's own GPU kernels;
