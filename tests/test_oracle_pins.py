@@ -433,6 +433,37 @@ def test_window_propagation_equals_leapfrog_with_a_frozen_hamiltonian():
     assert np.max(np.abs(a0 - tr1.rho_prev)) < 1e-12 and np.max(np.abs(b0 - tr1.rho)) < 1e-12
 
 
+def test_window_mean_shift_tracks_the_scc_leapfrog_and_the_frozen_shift_drifts():
+    # the premise of the learned form: with the SCC Hamiltonian, windows of k steps whose
+    # frozen shift is the mean of the plain run's own shifts over the window stay near the
+    # plain leapfrog, while windows frozen at their starting shift drift away
+    sysm = I.small_flake(16, seed=7)
+    run = I.Run(dt=0.2, n_steps=0, scc=True, kick=0.02, kick_dir=np.array([0.6, 0.8, 0.0]),
+                kT=I.SCC_KT)
+    rho0, gs, S, Sinv = O.setup(sysm, run)
+    R = np.asarray(sysm.R, dtype=np.float64)
+    S, H0 = O.model_matrices(sysm, R)
+    gamma = O.gamma_matrix(sysm, R)
+    q0 = O.reference_populations(sysm)
+    k, nw = 10, 20
+    tr = O.propagate(sysm, run, rho0, 1 + k * nw)
+    v = (tr.charges - q0) @ gamma.T                 # eq:hscc shift of every plain step
+    tr1 = O.propagate(sysm, run, rho0, 1)
+    err = {}
+    for mode in ("mean", "frozen"):
+        prev, cur = tr1.rho_prev, tr1.rho
+        e = []
+        for w in range(nw):
+            n = 1 + w * k
+            vb = v[n:n + k].mean(axis=0) if mode == "mean" else gamma @ (O.mulliken(sysm, cur, S) - q0)
+            prev, cur = O.window_propagate(prev, cur, S, O.scc_hamiltonian(sysm, H0, S, vb),
+                                           run.dt, k)
+            e.append(np.max(np.abs(O.mulliken(sysm, cur, S) - tr.charges[n + k])))
+        err[mode] = np.array(e)
+    assert np.max(err["mean"]) < 0.01
+    assert err["frozen"][-1] > 20 * err["mean"][-1]
+
+
 def test_bf16_rounding():
     x = np.array([1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -3.3, 1e-3])
     r = O.bf16_round(x)
