@@ -1161,6 +1161,20 @@ struct StateHeader {
     double P_prev;   // moving nuclei: work rate of the previous step
 };
 
+// TDB_ERR_CUDA with a message when no CUDA device is usable (checked before any
+// allocation, so that a host without a GPU gets a clear status, not an allocation one).
+tdb_status require_device(const char* who) {
+    int ndev = 0;
+    const cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        set_err("%s: no usable CUDA device (%s)", who,
+                e != cudaSuccess ? cudaGetErrorString(e) : "device count 0");
+        return TDB_ERR_CUDA;
+    }
+    return TDB_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1196,6 +1210,7 @@ tdb_status tdb_create(const tdb_system* sys, const tdb_params* prm, void* worksp
     }
     *out = nullptr;
     TRY(validate(sys, prm));
+    TRY(require_device("tdb_create"));
     tdb_ctx* c = new (std::nothrow) tdb_ctx();
     if (!c) return TDB_ERR_NOMEM;
     fill_host(*c, sys, prm);

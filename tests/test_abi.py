@@ -66,3 +66,20 @@ def test_missing_library_fails_loudly(tmp_path):
     from paper_1912_03174_gb300 import binding
     with pytest.raises(RuntimeError):
         binding.load(str(tmp_path / "nope.so"))
+
+
+def test_without_a_device_calls_fail_with_a_status(lib):
+    # on a host with no usable GPU the library returns TDB_ERR_CUDA with a message
+    # (no abort, no CPU fallback); on a GPU host there is nothing to check here
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_1912_03174_gb300 import binding as B
+    from paper_1912_03174_gb300 import inputs as I
+    sysm, run = I.chain_c1()
+    with pytest.raises(B.TdbError) as e:
+        B.tdb_create(sysm, B.make_params(run, "fp64"))
+    assert e.value.status == 3 and "CUDA device" in str(e.value)   # TDB_ERR_CUDA
+    with pytest.raises(B.TdbError) as e:
+        B.ShiftNet(8, 16)
+    assert e.value.status == 3
