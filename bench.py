@@ -462,6 +462,47 @@ def c5_runs(B, torch, k=16, L=8, hidden=64, n_train=4, train_steps=1200, windows
                       "network inference, eigensolve and products)"}
 
 
+def shard_throughput(units: float, seconds: float, dist=None):
+    """Sharded independent work (each rank its own share, no data-path collective):
+    the whole job's units over the slowest rank's time, both reduced over ranks on the
+    host (gloo).  Returns (total units, max seconds, units per second)."""
+    if dist is not None:
+        import torch
+        u = torch.tensor([float(units)], dtype=torch.float64)
+        t = torch.tensor([float(seconds)], dtype=torch.float64)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        units, seconds = float(u.item()), float(t.item())
+    return units, seconds, (units / seconds if seconds > 0 else 0.0)
+
+
+def c4_sharded(B, torch, dist, rank, world, n_traj, post_steps, form="fp16x6"):
+    """The pump-probe scan of c4_runs over world ranks: the probe runs shared out by
+    longest-processing-time on N^3 x steps, each rank branching and stepping its own
+    share (scan.run_shard), timed between barriers; value = all probe steps over the
+    slowest rank's time."""
+    from paper_1912_03174_gb300 import inputs as I, scan
+    systems, run, which, tau = I.pump_probe_c4(n_traj=n_traj)
+    parts = scan.lpt_partition(scan.probe_costs(systems, which, post_steps), world)
+
+    def sync():
+        torch.cuda.synchronize()
+        dist.barrier()
+
+    n, pump_steps, t, _ = scan.run_shard(B, systems, run, which, tau, parts[rank], post_steps,
+                                         form, sync=sync)
+    units, t_max, rate = shard_throughput(n * post_steps, t, dist)
+    return {"workload": f"pump-probe scan: {len(which)} probe runs over flakes of "
+                        f"{'/'.join(str(s.n_atoms) for s in systems)} atoms (N = 128..1024), "
+                        f"shared out over {world} ranks by longest-processing-time on N^3 x steps, "
+                        f"{post_steps} post-kick steps timed per probe",
+            "precision": form, "probes": int(units // post_steps), "probes_this_rank": n,
+            "pump_steps_untimed_this_rank": int(pump_steps),
+            "trajectory_steps_per_s_batched": rate, "seconds_slowest_rank": t_max,
+            "scaling": "strong",
+            "timing": "host clock between barriers after device synchronisation"}
+
+
 def e2e_run(B, sysm, run, precision, steps, warmup):
     """End to end through the public API: per step the field is set from the host
     (H2D), one step runs, and the observables with charges are read back (D2H)."""
@@ -590,7 +631,10 @@ def main():
             n2048 = n2048_runs(B, torch, flush, stream, min(args.steps, 200))
         c4 = None
         if args.c4_probes > 0:
-            c4 = c4_runs(B, torch, args.c4_probes, args.c4_steps)
+            if world > 1:
+                c4 = c4_sharded(B, torch, dist, rank, world, args.c4_probes, args.c4_steps)
+            else:
+                c4 = c4_runs(B, torch, args.c4_probes, args.c4_steps)
         c5 = None if args.no_c5 else c5_runs(B, torch, n_train=args.c5_runs, train_steps=args.c5_steps,
                                                windows=args.c5_windows, epochs=args.c5_epochs)
         if dist:
