@@ -52,11 +52,8 @@ struct Params {
     uint32_t idesc[5];   // [nb]: instruction descriptor of an N = 64 nb product
 };
 
-// CL = 1: one CTA per tile.  CL = 2: clusters of two CTAs on neighbouring column tiles
-// (the same A tile): each CTA loads half of the A slices and multicasts them to both,
-// which halves the A traffic from L2; a stage is refilled once both CTAs' MMAs have
-// consumed it (the empty barrier counts one commit from each).
-template <int CL>
+// One CTA per 128 x 64 output tile; every CTA issues its own TMA loads of the A and B
+// slices it multiplies.
 __global__ void __launch_bounds__(kThreads, 1)
     k_oz_gemm(const __grid_constant__ Maps maps, Params p) {
     extern __shared__ uint8_t smem_raw[];
@@ -74,12 +71,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int nkb = (p.K + BK - 1) / BK;
     const int nchunk = (nkb + kChunkKB - 1) / kChunkKB;
 
-    const uint32_t rank = CL > 1 ? cluster_rank() : 0u;
-    const uint16_t all = static_cast<uint16_t>((1u << CL) - 1u);
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, CL);
+            mbar_init(empty0 + 8 * s, 1);
         }
         mbar_init(cfull, 1);
         mbar_init(cempty, 8);   // one arrival per drain warp
@@ -93,11 +88,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
         fence_before();
     }
-    // the peer's multicasts and commits target this CTA's barriers: initialise them first
-    if (CL > 1)
-        cluster_sync();
-    else
-        __syncthreads();
+    __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_slot;
 
@@ -111,10 +102,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mbar_expect_tx(fb, SB);
 #pragma unroll
                 for (int q = 0; q < kSlices; ++q) {
-                    if (CL == 1)
-                        tma_load_2d(st + q * A_TILE, &maps.a[q], kb * BK, m0, fb);
-                    else if (q % CL == static_cast<int>(rank))
-                        tma_load_2d_mc(st + q * A_TILE, &maps.a[q], kb * BK, m0, fb, all);
+                    tma_load_2d(st + q * A_TILE, &maps.a[q], kb * BK, m0, fb);
                     tma_load_2d(st + kSlices * A_TILE + q * B_TILE, &maps.b[z][q], kb * BK, n0, fb);
                 }
             }
@@ -154,13 +142,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                 }
                 // free the stage for a refill (none follows the last STAGES blocks, so no
-                // arrival is left in flight when the CTAs exit)
-                if (kb + STAGES < nkb) {
-                    if (CL == 1)
-                        mma_commit(empty0 + 8 * s);
-                    else
-                        mma_commit_mc(empty0 + 8 * s, all);
-                }
+                // arrival is left in flight when the CTA exits)
+                if (kb + STAGES < nkb) mma_commit(empty0 + 8 * s);
                 if ((kb % kChunkKB) == kChunkKB - 1 || kb == nkb - 1) mma_commit(cfull);
             }
         }
@@ -209,8 +192,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                      "r"(TMEM_COLS)
                      : "memory");
     }
-    // no CTA leaves while its peer may still write into it
-    if (CL > 1) cluster_sync();
 }
 
 // frexp exponent of a normal m > 0 (m = f 2^e, f in [0.5, 1)) from its bits
@@ -370,11 +351,7 @@ void slice_cols(const double* B, int ldb, Sliced& out, double* colmax, cudaStrea
 }
 
 cudaError_t prepare() {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_oz_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_oz_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-    return e;
+    return cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
 }
 
 cudaError_t gemm(const Sliced& a, const Part* parts, int nparts, int* err, cudaStream_t st) {
@@ -398,26 +375,9 @@ cudaError_t gemm(const Sliced& a, const Part* parts, int nparts, int* err, cudaS
     p.err = err;
     for (int nb = 1; nb <= 4; ++nb) p.idesc[nb] = tc::idesc_f16(0, nb * BN);
     const int ntile = (N + BN - 1) / BN;
-    if (ntile < 2) {
-        dim3 grid(ntile, (a.rows + BM - 1) / BM, nparts);
-        k_oz_gemm<1><<<grid, kThreads, SMEM, st>>>(m, p);
-        return cudaGetLastError();
-    }
-    // pairs of column tiles share their A slices (an odd count gets an idle partner that
-    // loads and multicasts its half but writes nothing)
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((ntile + 1) / 2 * 2, (a.rows + BM - 1) / BM, nparts);
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = SMEM;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_oz_gemm<2>, m, p);
+    dim3 grid(ntile, (a.rows + BM - 1) / BM, nparts);
+    k_oz_gemm<<<grid, kThreads, SMEM, st>>>(m, p);
+    return cudaGetLastError();
 }
 
 }  // namespace oz
