@@ -324,7 +324,11 @@ tdb_status tdb_slice_gemm(int M, int N, int K, const double* A, const double* B,
  * fits, 1024 x 1024 x 1024 does not).  All calls share that array and it keeps
  * the last call's contents: calls whose GPU work overlaps race, so serialise
  * them.  The first call on each device looks up the array's address and must
- * come before any stream capture.  fmt as in tdb_split_gemm. */
+ * come before any stream capture.  fmt as in tdb_split_gemm.  M, N <= 32768 and
+ * K <= 65536 (TDB_ERR_ARG).  Because the call returns before its GPU work runs, a
+ * failure on the device (a bounded wait of the product that ran out, or an operand
+ * piece that overflows, for example from an Inf or NaN in A or B) cannot be returned
+ * as a status: C is then filled with NaN.  Check C after synchronising the stream. */
 tdb_status tdb_split_gemm_noalloc(int M, int N, int K, const double* A, const double* B, int fmt,
                                   double* C, void* stream);
 

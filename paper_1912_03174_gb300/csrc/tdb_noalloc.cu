@@ -16,10 +16,16 @@
 // a device looks up the array's device address (cudaGetSymbolAddress) and sets
 // the kernel's shared-memory attribute; make that first call before any CUDA
 // stream capture.
+//
+// The call returns before the GPU work runs, so a failure on the device (a bounded
+// wait of the product that ran out, or an operand piece that overflows, e.g. from an
+// Inf or NaN input) cannot be returned as a status: the last kernel then fills all of
+// C with NaN instead of a wrong product.
 #include <cmath>
 #include <cstdint>
 #include <mutex>
 
+#include "tc_split.cuh"
 #include "tdb_internal.h"
 #include "tdb_tc.h"
 
@@ -49,7 +55,10 @@ tdb_status scratch_address(unsigned char** out) {
             cudaGetLastError();
             return TDB_ERR_CUDA;
         }
-        if (tdb::tc::prepare() != cudaSuccess) return TDB_ERR_CUDA;
+        if (tdb::tc::prepare() != cudaSuccess) {
+            cudaGetLastError();
+            return TDB_ERR_CUDA;
+        }
         g_addr[dev] = static_cast<unsigned char*>(p);
     }
     *out = g_addr[dev];
@@ -72,67 +81,60 @@ __global__ void k_scales(int fmt, const double* mx, float* s) {
     }
 }
 
-// Pieces of the transpose of B (K x N row-major, device) into Bt rows (N x ldk).
+// Pieces of the transpose of B (K x N row-major, device) into Bt rows (N x ldk), with the
+// arithmetic of the A pieces (tc::split_value on the scaled FP32 value); an overflowing
+// piece sets err = 4.
+template <int SCHEME>
 __global__ void k_split_bt(int K, int N, const double* __restrict__ B, const float* __restrict__ s,
-                           int fmt, uint16_t* p0, uint16_t* p1, uint16_t* p2, int ldk) {
+                           int bf16, uint16_t* p0, uint16_t* p1, uint16_t* p2, int ldk, int* err) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = blockIdx.y * blockDim.y + threadIdx.y;
     if (k >= K || n >= N) return;
-    const double x = B[static_cast<size_t>(k) * N + n] * static_cast<double>(s[1]);
+    uint16_t q[3];
+    const bool ok = tdb::tc::split_value<SCHEME>(
+        static_cast<float>(B[static_cast<size_t>(k) * N + n]) * s[1], bf16, q);
     const size_t o = static_cast<size_t>(n) * ldk + k;
-    if (fmt == 2) {
-        double h = rint(x);
-        h = fmin(fmax(h, -127.0), 127.0);
-        const double r = x - h;
-        const __half rh = __double2half(r);
-        p0[o] = __half_as_ushort(__double2half(h));
-        p1[o] = __half_as_ushort(rh);
-        p2[o] = __half_as_ushort(__double2half(r - static_cast<double>(__half2float(rh))));
-    } else if (fmt == 1) {
-        const float xf = static_cast<float>(x);
-        const __nv_bfloat16 h = __float2bfloat16_rn(xf);
-        p0[o] = __bfloat16_as_ushort(h);
-        p1[o] = __bfloat16_as_ushort(__float2bfloat16_rn(xf - __bfloat162float(h)));
-    } else {
-        const float xf = static_cast<float>(x);
-        const __half h = __float2half_rn(xf);
-        p0[o] = __half_as_ushort(h);
-        p1[o] = __half_as_ushort(__float2half_rn(xf - __half2float(h)));
-    }
+    p0[o] = q[0];
+    p1[o] = q[1];
+    if (SCHEME == tdb::tc::kHead3) p2[o] = q[2];
+    if (!ok) atomicCAS(err, 0, 4);
 }
 
-__global__ void k_f32_to_f64(size_t n, const float* __restrict__ in, double* __restrict__ out) {
+// C = FP32 product, or NaN everywhere when the device error flag is set
+__global__ void k_finish(size_t n, const float* __restrict__ in, const int* __restrict__ err,
+                         double* __restrict__ out) {
+    const bool bad = *err != 0;
     for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
          i += static_cast<size_t>(gridDim.x) * blockDim.x)
-        out[i] = in[i];
+        out[i] = bad ? __longlong_as_double(0x7ff8000000000000ll) : static_cast<double>(in[i]);
+}
+
+tdb_status fail(tdb_status st, const char* msg) {
+    tdb::set_last_error(msg);
+    return st;
 }
 
 }  // namespace
 
 extern "C" tdb_status tdb_split_gemm_noalloc(int M, int N, int K, const double* A, const double* B,
                                              int fmt, double* C, void* stream) {
-    if (M < 1 || N < 1 || K < 1 || !A || !B || !C || fmt < 0 || fmt > 2 ||
-        (fmt == 2 && K > 3 * tdb::tc::kHeadK)) {
-        tdb::set_last_error("tdb_split_gemm_noalloc: invalid sizes, pointers or format");
-        return TDB_ERR_ARG;
-    }
-    const int ldk = (K + 63) / 64 * 64;
+    if (M < 1 || N < 1 || K < 1 || M > 32768 || N > 32768 || K > 65536 || !A || !B || !C ||
+        fmt < 0 || fmt > 2 || (fmt == 2 && K > 3 * tdb::tc::kHeadK))
+        return fail(TDB_ERR_ARG, "tdb_split_gemm_noalloc: invalid sizes, pointers or format");
+    const size_t ldk = (static_cast<size_t>(K) + 63) / 64 * 64;
     const int npc = fmt == 2 ? 3 : 2;
     // scratch layout: flags | maxima, scales | A pieces | Bt pieces | C (FP32)
-    const size_t a_bytes = up256(2ull * M * ldk), b_bytes = up256(2ull * N * ldk);
-    const size_t need = 512 + npc * (a_bytes + b_bytes) + up256(4ull * M * N);
-    if (need > kScratchBytes) {
-        tdb::set_last_error(
-            "tdb_split_gemm_noalloc: M, N, K need more than the fixed 8 MiB scratch "
-            "(pieces of A and B^T plus an FP32 C); use tdb_split_gemm for larger products");
-        return TDB_ERR_NOMEM;
-    }
+    const size_t a_bytes = up256(2 * static_cast<size_t>(M) * ldk);
+    const size_t b_bytes = up256(2 * static_cast<size_t>(N) * ldk);
+    const size_t need = 512 + npc * (a_bytes + b_bytes) + up256(4 * static_cast<size_t>(M) * N);
+    if (need > kScratchBytes)
+        return fail(TDB_ERR_NOMEM,
+                    "tdb_split_gemm_noalloc: M, N, K need more than the fixed 8 MiB scratch "
+                    "(pieces of A and B^T plus an FP32 C); use tdb_split_gemm for larger products");
     unsigned char* base = nullptr;
-    const tdb_status st0 = scratch_address(&base);
-    if (st0 != TDB_OK) {
-        tdb::set_last_error("tdb_split_gemm_noalloc: cudaGetSymbolAddress of the scratch failed");
-        return st0;
-    }
+    if (scratch_address(&base) != TDB_OK)
+        return fail(TDB_ERR_CUDA,
+                    "tdb_split_gemm_noalloc: looking up the scratch array on this device failed");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int* err = reinterpret_cast<int*>(base);
     double* mx = reinterpret_cast<double*>(base + 256);
@@ -144,21 +146,30 @@ extern "C" tdb_status tdb_split_gemm_noalloc(int M, int N, int K, const double* 
     for (int i = 0; i < npc; ++i, q += b_bytes) bp[i] = reinterpret_cast<uint16_t*>(q);
     float* c32 = reinterpret_cast<float*>(q);
     // what must start at zero: the error flag and the two maxima
-    if (cudaMemsetAsync(base, 0, 512, st) != cudaSuccess) return TDB_ERR_CUDA;
+    if (cudaMemsetAsync(base, 0, 512, st) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TDB_ERR_CUDA, "tdb_split_gemm_noalloc: clearing the scratch flags failed");
+    }
     tdb::launch_absmax(static_cast<size_t>(M) * K, A, mx, st, nullptr);
     tdb::launch_absmax(static_cast<size_t>(K) * N, B, mx + 1, st, nullptr);
     k_scales<<<1, 32, 0, st>>>(fmt, mx, sc);
     const int bf16 = fmt == 1 ? 1 : 0;
     const int scheme = fmt == 2 ? tdb::tc::kHead3 : tdb::tc::kHiLo;
-    tdb::tc::launch_split(scheme, M, K, A, K, 1.0f, 1, bf16, ap, ldk, st, nullptr, sc, err);
+    const int ld = static_cast<int>(ldk);
+    tdb::tc::launch_split(scheme, M, K, A, K, 1.0f, 1, bf16, ap, ld, st, nullptr, sc, err);
     dim3 b(32, 8), g((K + 31) / 32, (N + 7) / 8);
-    k_split_bt<<<g, b, 0, st>>>(K, N, B, sc, fmt, bp[0], bp[1], bp[2], ldk);
-    if (cudaGetLastError() != cudaSuccess) return TDB_ERR_CUDA;
+    if (scheme == tdb::tc::kHead3)
+        k_split_bt<tdb::tc::kHead3><<<g, b, 0, st>>>(K, N, B, sc, bf16, bp[0], bp[1], bp[2], ld, err);
+    else
+        k_split_bt<tdb::tc::kHiLo><<<g, b, 0, st>>>(K, N, B, sc, bf16, bp[0], bp[1], nullptr, ld, err);
+    const cudaError_t e1 = cudaGetLastError();
+    if (e1 != cudaSuccess)
+        return fail(TDB_ERR_CUDA, "tdb_split_gemm_noalloc: launching the split kernels failed");
     tdb::tc::Maps maps{};
     for (int i = 0; i < npc; ++i)
-        if (!tdb::tc::make_map(&maps.a[i], ap[i], M, K, ldk, bf16) ||
-            !tdb::tc::make_map(&maps.b[0][i], bp[i], N, K, ldk, bf16))
-            return TDB_ERR_CUDA;
+        if (!tdb::tc::make_map(&maps.a[i], ap[i], M, K, ld, bf16) ||
+            !tdb::tc::make_map(&maps.b[0][i], bp[i], N, K, ld, bf16))
+            return fail(TDB_ERR_CUDA, "tdb_split_gemm_noalloc: cuTensorMapEncodeTiled failed");
     tdb::tc::GemmParams p{};
     p.M = M;
     p.N = N;
@@ -166,8 +177,12 @@ extern "C" tdb_status tdb_split_gemm_noalloc(int M, int N, int K, const double* 
     p.idesc = tdb::tc::idesc_f16(bf16);
     p.bf16 = bf16;
     p.err = err;
-    if (tdb::tc::launch(scheme, maps, p, 1, st) != cudaSuccess) return TDB_ERR_CUDA;
-    k_f32_to_f64<<<256, 256, 0, st>>>(static_cast<size_t>(M) * N, c32, C);
-    if (cudaGetLastError() != cudaSuccess) return TDB_ERR_CUDA;
+    if (tdb::tc::launch(scheme, maps, p, 1, st) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TDB_ERR_CUDA, "tdb_split_gemm_noalloc: launching the tensor-core product failed");
+    }
+    k_finish<<<256, 256, 0, st>>>(static_cast<size_t>(M) * N, c32, err, C);
+    if (cudaGetLastError() != cudaSuccess)
+        return fail(TDB_ERR_CUDA, "tdb_split_gemm_noalloc: launching the final conversion failed");
     return TDB_OK;
 }

@@ -51,9 +51,32 @@ def test_noalloc_matches_the_allocating_entry_point_on_two_calls(B, fmt):
         assert np.max(np.abs(got - A @ Bm) / scale) < tol
 
 
+@pytest.mark.parametrize("fmt", [0, 1, 2])
+def test_noalloc_reports_a_device_failure_as_nan_and_recovers(B, fmt):
+    """The call returns before its GPU work runs, so a device-side failure (here an
+    operand piece that overflows because A holds an Inf) shows up as C filled with NaN;
+    the next call starts from a cleared flag and is exact again."""
+    import torch
+    rng = np.random.default_rng(200 + fmt)
+    M, N, K = 96, 80, 120
+    A = rng.normal(size=(M, K))
+    Bm = rng.normal(size=(K, N))
+    bad = A.copy()
+    bad[3, 7] = np.inf
+    got = _run_noalloc(B, bad, Bm, fmt, torch)
+    assert np.all(np.isnan(got))
+    got = _run_noalloc(B, A, Bm, fmt, torch)
+    scale = np.abs(A) @ np.abs(Bm)
+    tol = 2.0 ** -20 + 16 * 2.0 ** -24 * np.sqrt(K) if fmt != 1 else 1e-4
+    assert np.all(np.isfinite(got)) and np.max(np.abs(got - A @ Bm) / scale) < tol
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch(B):
     import torch
     d = torch.zeros(1, dtype=torch.float64, device="cuda")
     with pytest.raises(B.TdbError) as e:
         B.tdb_split_gemm_noalloc(1024, 1024, 1024, d.data_ptr(), d.data_ptr(), 0, d.data_ptr(), None)
     assert e.value.status == 9 and "8 MiB" in str(e.value)
+    with pytest.raises(B.TdbError) as e:
+        B.tdb_split_gemm_noalloc(8, 8, 2 ** 31 - 1, d.data_ptr(), d.data_ptr(), 0, d.data_ptr(), None)
+    assert e.value.status == 1
