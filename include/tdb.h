@@ -244,6 +244,31 @@ void tdb_shiftnet_destroy(tdb_shiftnet* net);
  * before i have made k + 1 steps, the others k; the message names i and k. */
 tdb_status tdb_step_batch(tdb_ctx* const* ctxs, int count, long n);
 
+/* A grouped batch: count independent contexts of one tensor-core form (TDB_BF16X3,
+ * TDB_FP16X3 or TDB_FP16X6), frozen nuclei, one time step, each after its ground state
+ * (the probe runs of a pump-probe scan, Sec. 3.2, branched with tdb_clone).  Every phase of
+ * a step (delta H pieces, delta M = S^-1 delta H, X = M rho, the update with the charges,
+ * potential and dipole of the new level) is one launch over all contexts, whatever their
+ * sizes: per-context tensor maps and arguments live in device arrays, a work list maps each
+ * block to (context, tile), and the four launches of a step are one CUDA graph.  Creating
+ * the batch runs an autotuner over the X tile width (128, 176, 256) and the schedule (the
+ * contexts in the given order, or the largest first) on the contexts' current operands;
+ * the choice changes the time, not the result.  Each context keeps its own state, stream
+ * and dipole history; the batch has its own stream, ordered after the contexts' streams
+ * at each tdb_batch_step and before them afterwards.  The contexts must not be stepped on
+ * their own while the batch is used (TDB_ERR_STATE), and the batch is destroyed before
+ * them.  TDB_ERR_UNSUPPORTED for other forms or moving nuclei, TDB_ERR_ARG for mixed forms
+ * or time steps, repeated contexts or count < 1. */
+typedef struct tdb_batch tdb_batch;
+tdb_status tdb_batch_create(tdb_ctx* const* ctxs, int count, tdb_batch** out);
+/* Advance every context of the batch by n >= 0 steps (asynchronous).  A pending Euler step
+ * (after a kick, ground state or state load) is taken context by context first. */
+tdb_status tdb_batch_step(tdb_batch* batch, long n);
+/* The autotuner's choice: X tile width, schedule (0 given order, 1 largest first) and the
+ * X launch time it measured (ms); any pointer may be NULL. */
+tdb_status tdb_batch_tuning(const tdb_batch* batch, int* x_bn, int* schedule, double* x_ms);
+void tdb_batch_destroy(tdb_batch* batch);
+
 /* Observables of the current rho_n (synchronises).  charges: [n_atoms] Mulliken
  * populations q_A or NULL; forces: [n_atoms][3] Ehrenfest forces (eq:forces,
  * velocity terms dropped) or NULL. */
@@ -267,6 +292,16 @@ tdb_status tdb_set_state(tdb_ctx* ctx, const void* host_buf, size_t bytes);
 /* Invariant monitor (synchronises): NaN/Inf, |Tr(rho S) - N_e| / N_e <= tol_trace.
  * Violation returns TDB_ERR_NUMERIC and makes the context sticky. */
 tdb_status tdb_check(tdb_ctx* ctx, double tol_trace);
+
+/* Failure-detection probe (the paper has no counterpart: it tests this library's handling
+ * of a device-side wait that gives up).  Enqueues on the context stream one kernel that
+ * waits on an mbarrier nothing arrives on, polling at most `polls` times (>= 1, else
+ * TDB_ERR_ARG) like the bounded waits of the tensor-core products, and then records a
+ * time-out in the context's device error flag.  The next call that reads the flag
+ * (tdb_observables, tdb_check) returns TDB_ERR_TIMEOUT and the context becomes sticky, as
+ * after a real time-out.  The probe issues no copy and holds no tensor memory, so the
+ * GPU and the CUDA context stay usable.  Asynchronous. */
+tdb_status tdb_wait_probe(tdb_ctx* ctx, long long polls);
 
 /* Device kernel launches issued by the last tdb_step call (for accounting). */
 long tdb_last_launch_count(const tdb_ctx* ctx);
@@ -331,6 +366,21 @@ tdb_status tdb_slice_gemm(int M, int N, int K, const double* A, const double* B,
  * as a status: C is then filled with NaN.  Check C after synchronising the stream. */
 tdb_status tdb_split_gemm_noalloc(int M, int N, int K, const double* A, const double* B, int fmt,
                                   double* C, void* stream);
+
+/* Damped one-sided Fourier transforms of sampled signals, the transforms behind the
+ * absorption spectrum (eq:alpha: alpha(w) = (mu(w) - mu_0) / E0 after a kick, eq:sigma)
+ * and the transient absorption of pump-probe runs (eq:alphaeff, eq:sigmaeff, Sec. 3.2,
+ * where x is the probe dipole minus the pump-only dipole and t_damp the electronic
+ * damping time):
+ *   F_s(w_k) = dt sum_{n < K} x_s[n] exp(-n dt / t_damp) exp(+i w_k n dt)
+ * (the rectangle rule on the step grid; the sign e^{+iwt} makes Im alpha > 0 at an
+ * absorption peak).  x: nsig x K row-major host doubles; omega: nw host doubles (angular
+ * frequencies, Ha); re, im: nsig x nw host doubles (written).  t_damp > 0, or 0 / +inf for
+ * no damping; dt > 0.  FP64 on the GPU (the library allocates and frees its device
+ * buffers; synchronises).  TDB_ERR_ARG for bad sizes, pointers or values, TDB_ERR_NOMEM if
+ * the device buffers do not fit, TDB_ERR_CUDA for other CUDA failures. */
+tdb_status tdb_damped_transform(int nsig, long K, const double* x, double dt, double t_damp,
+                                int nw, const double* omega, double* re, double* im);
 
 void tdb_destroy(tdb_ctx* ctx);
 const char* tdb_status_string(tdb_status s);

@@ -91,12 +91,21 @@ SIGNATURES = {
     "tdb_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "tdb_check": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     "tdb_last_launch_count": (ctypes.c_long, [ctypes.c_void_p]),
+    "tdb_wait_probe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong]),
     "tdb_step_profiled": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_char_p), ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int)]),
     "tdb_split_gemm": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_int, _dp, _dp]),
     "tdb_slice_gemm": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]),
     "tdb_split_gemm_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "tdb_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "tdb_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_long]),
+    "tdb_batch_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int), _dp]),
+    "tdb_batch_destroy": (None, [ctypes.c_void_p]),
+    "tdb_damped_transform": (ctypes.c_int, [ctypes.c_int, ctypes.c_long, _dp, ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_int, _dp, _dp, _dp]),
     "tdb_destroy": (None, [ctypes.c_void_p]),
     "tdb_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "tdb_last_error": (ctypes.c_char_p, []),
@@ -339,6 +348,38 @@ def tdb_step_batch(ctxs, n: int):
     _check("tdb_step_batch", load().tdb_step_batch(arr, len(ctxs), int(n)))
 
 
+class Batch:
+    """A grouped batch of contexts (tdb_batch_*): every phase of a step is one launch over
+    all of them."""
+
+    def __init__(self, ctxs):
+        arr = (ctypes.c_void_p * len(ctxs))(*[c.handle for c in ctxs])
+        h = ctypes.c_void_p()
+        _check("tdb_batch_create", load().tdb_batch_create(arr, len(ctxs), ctypes.byref(h)))
+        self.handle = h
+        self.ctxs = list(ctxs)
+
+    def step(self, n: int):
+        _check("tdb_batch_step", load().tdb_batch_step(self.handle, int(n)))
+
+    def tuning(self):
+        bn, sch, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check("tdb_batch_tuning", load().tdb_batch_tuning(self.handle, ctypes.byref(bn),
+                                                           ctypes.byref(sch), ctypes.byref(ms)))
+        return {"x_bn": bn.value, "schedule": sch.value, "x_ms": ms.value}
+
+    def close(self):
+        if self.handle:
+            load().tdb_batch_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 def tdb_observables(ctx: Context, charges=True, forces=False):
     o = TdbObs()
     q = np.zeros(ctx.n_atoms) if charges else None
@@ -391,6 +432,11 @@ def tdb_check(ctx: Context, tol_trace: float = 1e-10):
     _check("tdb_check", load().tdb_check(ctx.handle, float(tol_trace)))
 
 
+def tdb_wait_probe(ctx: Context, polls: int):
+    """Enqueue a kernel whose bounded device wait runs out (failure-detection probe)."""
+    _check("tdb_wait_probe", load().tdb_wait_probe(ctx.handle, int(polls)))
+
+
 def tdb_last_launch_count(ctx: Context) -> int:
     return int(load().tdb_last_launch_count(ctx.handle))
 
@@ -437,6 +483,23 @@ def tdb_split_gemm_noalloc(M, N, K, a_ptr, b_ptr, fmt, c_ptr, stream=None):
         int(M), int(N), int(K), a_ptr, b_ptr, int(fmt), c_ptr, stream))
 
 
+def tdb_damped_transform(x, dt: float, t_damp: float, omega):
+    """F_s(w) = dt sum_n x_s[n] exp(-n dt / t_damp) exp(i w n dt) on the GPU.  x: [nsig, K] (or
+    [K]); t_damp = inf or 0 for none.  Returns complex [nsig, nw] (or [nw])."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    one = x.ndim == 1
+    x2 = x.reshape(1, -1) if one else x.reshape(-1, x.shape[-1])
+    om = np.ascontiguousarray(omega, dtype=np.float64).ravel()
+    re = np.zeros((x2.shape[0], om.size))
+    im = np.zeros_like(re)
+    td = 0.0 if not np.isfinite(t_damp) else float(t_damp)
+    _check("tdb_damped_transform", load().tdb_damped_transform(
+        int(x2.shape[0]), int(x2.shape[1]), _ptr(x2), float(dt), td, int(om.size), _ptr(om),
+        _ptr(re), _ptr(im)))
+    out = re + 1j * im
+    return out[0] if one else out.reshape(x.shape[:-1] + (om.size,))
+
+
 def tdb_destroy(ctx: Context):
     if ctx.handle:
         load().tdb_destroy(ctx.handle)
@@ -458,9 +521,10 @@ def tdb_last_error() -> str:
 class Propagator:
     """One trajectory: create -> ground state -> (kick) -> step ... -> observables."""
 
-    def __init__(self, sysm, run, precision="fp64", stream=None, workspace=None, history_cap=65536):
+    def __init__(self, sysm, run, precision="fp64", stream=None, workspace=None, history_cap=65536,
+                 window=100):
         self.sysm, self.run = sysm, run
-        self.params = make_params(run, precision, stream, history_cap)
+        self.params = make_params(run, precision, stream, history_cap, window)
         self.ctx = tdb_create(sysm, self.params, workspace)
 
     def setup(self):

@@ -74,64 +74,104 @@ __device__ double gamma_dR(double ta, double tb, double R) {
     return -1.0 / (R * R) - dz;
 }
 
-// One warp per atom A: F_A = sum over B != A of the pair terms of eq:forces
-// (energy-weighted form of the S-derivative terms, velocity terms dropped):
-//   2 sum_ij Re rho_ij dH_ij/dR_B + sum_ij (Re rho_ij (v_A + v_B) - 2 Re W_ij) dS_ij/dR_B
-// over the (A, B) blocks, plus -dq_A dq_B dgamma/dR_A + rep_A/rep_b e^{-r/rep_b} u,
-// and -dq_A E(t).  W = 1/2 (X + X^dagger), X = S^-1 H rho.
-__global__ void k_forces(int nat, int nper, int scc, const double* __restrict__ R,
-                         const double* __restrict__ rre, const double* __restrict__ wre,
-                         const double* __restrict__ v_atom, const double* __restrict__ dq,
-                         const double* __restrict__ U, ModelParams mp,
-                         const DevScalars* __restrict__ sc, double* __restrict__ F) {
-    // one block per atom A, its threads over the partners B (FP64 throughout: enough
-    // blocks and threads to keep the FP64 pipes of all SMs busy)
+// Gradient with respect to d = R_B - R_A of the weighted block sum sum_ij w_ij T_ij(d) of a
+// two-centre s/p block (T_00 = K0, T_0a = c_a K1, T_a0 = -c_a K1, T_ab = c_a c_b (K2 - K3)
+// + delta_ab K3, c = d / r), contracted before differentiating: with p_a = w_0a - w_a0 and
+// M_ab = w_ab the sum is w_00 K0 + (p.c) K1 + (c.Mc) (K2 - K3) + tr(M) K3, and with
+// dc_a/dd_q = (delta_aq - c_a c_q) / r and dr/dd = c its gradient is
+//   c [w_00 K0' + (p.c) K1' + (c.Mc)(K2' - K3') + tr(M) K3' - ((p.c) K1 + 2 (c.Mc)(K2 - K3)) / r]
+//   + [p K1 + (M + M^T) c (K2 - K3)] / r.
+// nper = 1 (s only): w_00 K0' c.
+__device__ __forceinline__ void block_sum_grad(int nper, const double (&w)[16], const double c[3],
+                                               double r, const double K[4], const double dK[4],
+                                               double g[3]) {
+    if (nper == 1) {
+        for (int q = 0; q < 3; ++q) g[q] = w[0] * dK[0] * c[q];
+        return;
+    }
+    const double p[3] = {w[1] - w[4], w[2] - w[8], w[3] - w[12]};
+    double Mc[3], MTc[3];
+    for (int a = 0; a < 3; ++a) {
+        Mc[a] = w[4 * (a + 1) + 1] * c[0] + w[4 * (a + 1) + 2] * c[1] + w[4 * (a + 1) + 3] * c[2];
+        MTc[a] = w[4 + a + 1] * c[0] + w[8 + a + 1] * c[1] + w[12 + a + 1] * c[2];
+    }
+    const double pc = p[0] * c[0] + p[1] * c[1] + p[2] * c[2];
+    const double cMc = c[0] * Mc[0] + c[1] * Mc[1] + c[2] * Mc[2];
+    const double tr = w[5] + w[10] + w[15];
+    const double d23 = K[2] - K[3];
+    const double inv_r = 1.0 / r;
+    const double par = w[0] * dK[0] + pc * dK[1] + cMc * (dK[2] - dK[3]) + tr * dK[3] -
+                       (pc * K[1] + 2.0 * cMc * d23) * inv_r;
+    for (int q = 0; q < 3; ++q)
+        g[q] = par * c[q] + (p[q] * K[1] + (Mc[q] + MTc[q]) * d23) * inv_r;
+}
+
+// One block per atom A, its threads over the partners B: F_A = sum over B != A of the pair
+// terms of eq:forces (energy-weighted form of the S-derivative terms, velocity terms
+// dropped):
+//   sum over the (A, B) block of 2 Re rho_ij dH_ij/dR_B + (Re rho_ij (v_A + v_B) - 2 Re W_ij)
+//   dS_ij/dR_B, plus -dq_A dq_B dgamma/dR_A + rep_A/rep_b e^{-r/rep_b} u, and -dq_A E(t);
+// W = 1/2 (X + X^dagger), X = S^-1 H rho.  The block sums are differentiated in contracted
+// form (block_sum_grad); FP64.
+__global__ void __launch_bounds__(128)
+    k_forces(int nat, int nper, int scc, const double* __restrict__ R,
+             const double* __restrict__ rre, const double* __restrict__ wre,
+             const double* __restrict__ v_atom, const double* __restrict__ dq,
+             const double* __restrict__ U, ModelParams mp, const DevScalars* __restrict__ sc,
+             double* __restrict__ F) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int A = blockIdx.x;
     const int N = nat * nper;
+    const double RA[3] = {R[3 * A], R[3 * A + 1], R[3 * A + 2]};
+    const double vA = v_atom[A], dqA = dq[A], tA = 3.2 * U[A];
     double f[3] = {0.0, 0.0, 0.0};
     for (int B = threadIdx.x; B < nat; B += blockDim.x) {
         if (B == A) continue;
-        const double d[3] = {R[3 * B] - R[3 * A], R[3 * B + 1] - R[3 * A + 1],
-                             R[3 * B + 2] - R[3 * A + 2]};
+        const double d[3] = {R[3 * B] - RA[0], R[3 * B + 1] - RA[1], R[3 * B + 2] - RA[2]};
         const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        const double c[3] = {d[0] / r, d[1] / r, d[2] / r};
+        const double inv_r = 1.0 / r;
+        const double c[3] = {d[0] * inv_r, d[1] * inv_r, d[2] * inv_r};
+        const double eh = exp(-r / mp.lam_H), es = exp(-r / mp.lam_S);
         double KH[4], dKH[4], KS[4], dKS[4];
-        radial(mp, r, true, KH, dKH);
-        radial(mp, r, false, KS, dKS);
-        const double vv = v_atom[A] + v_atom[B];
+        for (int k = 0; k < 4; ++k) {
+            KH[k] = mp.eta[k] * mp.t0 * eh;
+            dKH[k] = -KH[k] / mp.lam_H;
+            KS[k] = -mp.eta[k] * mp.s0 * es;
+            dKS[k] = -KS[k] / mp.lam_S;
+        }
+        const double vv = vA + v_atom[B];
+        double wh[16], ws[16];
         for (int i = 0; i < nper; ++i) {
             const size_t row = (size_t)(A * nper + i) * N + (size_t)B * nper;
             for (int j = 0; j < nper; ++j) {
-                const double p = rre[row + j], w = wre[row + j];
-                double gh[3], gs[3];
-                block_grad(i, j, c, r, KH, dKH, gh);
-                block_grad(i, j, c, r, KS, dKS, gs);
-                const double ch = 2.0 * p, cs = p * vv - 2.0 * w;
-                for (int q = 0; q < 3; ++q) f[q] += ch * gh[q] + cs * gs[q];
+                const double pr = rre[row + j], w = wre[row + j];
+                wh[4 * i + j] = 2.0 * pr;
+                ws[4 * i + j] = pr * vv - 2.0 * w;
             }
         }
+        double gh[3], gs[3];
+        block_sum_grad(nper, wh, c, r, KH, dKH, gh);
+        block_sum_grad(nper, ws, c, r, KS, dKS, gs);
+        for (int q = 0; q < 3; ++q) f[q] += gh[q] + gs[q];
         // u = (R_A - R_B) / r = -c
         if (scc) {
-            const double g = gamma_dR(3.2 * U[A], 3.2 * U[B], r);
-            for (int q = 0; q < 3; ++q) f[q] -= dq[A] * dq[B] * g * (-c[q]);
+            const double g = gamma_dR(tA, 3.2 * U[B], r);
+            const double s = dqA * dq[B] * g;
+            for (int q = 0; q < 3; ++q) f[q] += s * c[q];
         }
         if (mp.rep_A != 0.0) {
             const double e = mp.rep_A / mp.rep_b * exp(-r / mp.rep_b);
-            for (int q = 0; q < 3; ++q) f[q] += e * (-c[q]);
+            for (int q = 0; q < 3; ++q) f[q] -= e * c[q];
         }
     }
     for (int q = 0; q < 3; ++q) f[q] = warp_sum_d(f[q]);
-    __shared__ double red[3][32];
+    __shared__ double red[3][4];
     if (lane == 0)
         for (int q = 0; q < 3; ++q) red[q][warp] = f[q];
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int q = 0; q < 3; ++q) {
-            double t = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[q][w];
-            F[3 * A + q] = t - dq[A] * sc->E[q];
-        }
+    if (threadIdx.x < 3) {
+        const int q = threadIdx.x;
+        F[3 * A + q] = ((red[q][0] + red[q][1]) + (red[q][2] + red[q][3])) - dqA * sc->E[q];
     }
 }
 

@@ -234,7 +234,7 @@ __global__ void k_potential(int nat, int nper, int scc, const double* __restrict
                             DevScalars* __restrict__ sc, double* __restrict__ v_orb,
                             double* __restrict__ v_atom, double* __restrict__ gdq,
                             double* __restrict__ hist, const double* __restrict__ v_ref,
-                            float* __restrict__ dv_f, double* __restrict__ max_dv) {
+                            float* __restrict__ dv_f, double* __restrict__ max_dv, int record) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarp = blockDim.x >> 5;
     const long long n = sc->step;
@@ -268,7 +268,7 @@ __global__ void k_potential(int nat, int nper, int scc, const double* __restrict
                           (unsigned long long)__double_as_longlong(fabs(vA - v_ref[A * nper])));
         }
     }
-    if (blockIdx.x == 0) {
+    if (blockIdx.x == 0 && record) {
         __shared__ double red[4][32];
         double m0 = 0, m1 = 0, m2 = 0, ee = 0;
         for (int A = threadIdx.x; A < nat; A += blockDim.x) {
@@ -576,11 +576,12 @@ void launch_charges(const Ctx& c, const double* partial, double* q, double* dq, 
 
 void launch_potential(const Ctx& c, const double* gamma, const double* dq, const double* R,
                       DevScalars* sc, double* v_orb, double* v_atom, double* gdq, double* hist,
-                      const double* v_ref, float* dv_orb, cudaStream_t st, double* max_dv) {
+                      const double* v_ref, float* dv_orb, cudaStream_t st, double* max_dv,
+                      int record) {
     const int warps = 8;
     const int blocks = (c.nat + warps - 1) / warps;
     k_potential<<<blocks, warps * 32, 0, st>>>(c.nat, c.nper, c.prm.scc, gamma, dq, R, sc, v_orb,
-                                               v_atom, gdq, hist, v_ref, dv_orb, max_dv);
+                                               v_atom, gdq, hist, v_ref, dv_orb, max_dv, record);
 }
 
 void launch_build_hamiltonian(int N, const double* H0, const double* S, const double* v_orb,
@@ -779,38 +780,332 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float inc) {
     lo = e - (hi - s);
 }
 
+// FP32-pair ("double-float", ~48 bits) sums and products.  FP64 issues at a small fraction
+// of the FP32 rate on this part, so the per-step reductions use these.  The sum is
+// commutative bit for bit (the rounded sum and its exact error do not depend on the
+// order), so butterfly reductions give the same value on every lane.
+__device__ __forceinline__ float2 df2_add(float2 a, float2 b) {
+    float s, e;
+    two_sum(a.x, b.x, s, e);
+    e += a.y + b.y;
+    const float h = s + e;
+    return make_float2(h, e - (h - s));
+}
+// a * b with the exact product of the high parts (FMA) and the cross terms
+__device__ __forceinline__ float2 df2_mul(float2 a, float2 b) {
+    const float p = a.x * b.x;
+    const float e = fmaf(a.x, b.x, -p) + (a.x * b.y + a.y * b.x);
+    return make_float2(p, e);
+}
+__device__ __forceinline__ float2 df2_shfl_xor(float2 v, int o) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+__device__ __forceinline__ float2 df2_warp_sum(float2 v) {
+    for (int o = 16; o > 0; o >>= 1) v = df2_add(v, df2_shfl_xor(v, o));
+    return v;
+}
+__device__ __forceinline__ float2 ldcg2(const float2* p) { return __ldcg(p); }
+
+// Mulliken product of one element of the deviation master with FP32 S: (re_hi + re_lo) S
+// as (hi, lo) with the high product exact
+__device__ __forceinline__ float2 mulliken_elem(float rh, float rl, float s) {
+    const float p = rh * s;
+    return make_float2(p, fmaf(rh, s, -p) + rl * s);
+}
+// Sum of the 32 element values of a tile row (column order fixed: four interleaved
+// partial sums, then combined), shared by the update and the master partials.
+__device__ __forceinline__ float2 tile_row_sum(const float2* row) {
+    float2 a[4] = {row[0], row[1], row[2], row[3]};
+#pragma unroll
+    for (int k = 4; k < kTile; k += 4)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a[j] = df2_add(a[j], row[k + j]);
+    return df2_add(df2_add(a[0], a[1]), df2_add(a[2], a[3]));
+}
+
+// Power-of-two scale mapping a bound m into (63.5, 127] (FP32 form of tc::pscale; an
+// FP32 quotient that rounds up to a power of two gives a scale one step too large, which
+// only moves a little more of a value into its FP16 tails: the heads stay within +-127).
+__device__ __forceinline__ float pscale_f(float m) {
+    if (!(m > 0.f)) return 1099511627776.0f;   // 2^40
+    int e;
+    frexpf(127.0f / m, &e);
+    e -= 1;
+    e = min(40, max(-40, e));
+    return ldexpf(1.0f, e);
+}
+
+// E(t) of eq:pumpf with the phase formed and reduced modulo 2 pi in FP64 and the sine and
+// envelope in FP32 (relative error ~1e-7, far below the reduced forms' product error).
+__device__ void field_at_f(const FieldDev& f, double t, float E[3]) {
+    if (!f.on) {
+        E[0] = E[1] = E[2] = 0.f;
+        return;
+    }
+    const double kTwoPi = 6.283185307179586476925;
+    float env = 1.f;
+    if (f.envelope == 1) {
+        const double x = t - f.t_center;
+        const double y = x * x * (4.0 * 0.69314718055994530942 / (f.fwhm * f.fwhm));
+        const float yf = (float)y;
+        env = expf(-yf) * (1.f - (float)(y - (double)yf));
+    } else if (f.envelope == 2) {
+        if (t >= 0.0 && t <= f.fwhm) {
+            const float sv = sinf((float)(3.14159265358979323846 * t / f.fwhm));
+            env = sv * sv;
+        } else {
+            env = 0.f;
+        }
+    }
+    double ph = f.omega * t + f.phase;
+    ph -= kTwoPi * rint(ph * (1.0 / kTwoPi));
+    const float a = (float)f.E0 * sinf((float)ph) * env;
+    E[0] = a * (float)f.dir[0];
+    E[1] = a * (float)f.dir[1];
+    E[2] = a * (float)f.dir[2];
+}
+
+// Row-tile stage of the per-level evaluation (one block of 256 threads, tile r): deviation
+// charges dq_A of the tile's atoms (sums of their rows' partials in a fixed order), the
+// tile's partial potentials pv[r][A'] = sum_B gamma_A'B dq_B (eq:hscc), and its sums of
+// dq_A R_A and dq_A.
+__device__ void level_rowtile(const LevelArgs& a, int r, bool trace_only) {
+    __shared__ float2 dq_sh[kTile];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int apt = kTile / a.nper;
+    const int A0 = r * apt;
+    const int na = min(apt, a.nat - A0);
+    const int len = a.nper * a.nct;
+    for (int i = warp; i < na; i += 8) {
+        const float2* p = a.partial + (size_t)(A0 + i) * len;
+        float2 s = make_float2(0.f, 0.f);
+        // lane's partials in increasing order, eight loads in flight at a time
+        for (int k0 = lane; k0 < len; k0 += 32 * 8) {
+            float2 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                v[u] = k0 + 32 * u < len ? ldcg2(p + k0 + 32 * u) : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s = df2_add(s, v[u]);
+        }
+        s = df2_warp_sum(s);
+        if (lane == 0) dq_sh[i] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        float2 m[4] = {};
+        if (lane < na) {
+            const float2 d = dq_sh[lane];
+            const int A = A0 + lane;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) m[k] = df2_mul(d, a.R2[3 * A + k]);
+            m[3] = d;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) m[k] = df2_warp_sum(m[k]);
+        if (lane < 4) a.part[4 * r + lane] = m[lane];
+    }
+    if (trace_only || !a.scc) return;
+    for (int Ap = tid; Ap < a.nat; Ap += 256) {
+        const float2* g = a.gam2 + (size_t)Ap * a.nat + A0;
+        float2 s = make_float2(0.f, 0.f);
+        for (int i0 = 0; i0 < na; i0 += 8) {
+            float2 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = i0 + u < na ? __ldg(g + i0 + u) : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (i0 + u < na) s = df2_add(s, df2_mul(v[u], dq_sh[i0 + u]));
+        }
+        a.pv[(size_t)r * a.nat + Ap] = s;
+    }
+}
+
+// Final stage (one block): Tr(rho S) and the renormalisation factor of level `slot`; unless
+// trace_only, v - v_ref per orbital (dv_f) and its maximum (with the FP16X6 scales of the
+// next products), the dipole mu = mu_ref - sum_A dq_A R_A into sc->mu and the history slot
+// of step n_lvl, the field record.  step_end: the step counter advances to n_lvl and the
+// FP16X6 maxima move (the new level is in `slot`).  Resets the counters.
+__device__ void level_final(const LevelArgs& a, int slot, long long n_lvl, bool trace_only,
+                            bool step_end) {
+    __shared__ float2 tot[4];
+    __shared__ float E_sh[3];
+    __shared__ float red[8];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    DevScalars* sc = a.sc;
+    if (warp < 4) {
+        float2 s = make_float2(0.f, 0.f);
+        for (int r = lane; r < a.nct; r += 32) s = df2_add(s, ldcg2(a.part + 4 * r + warp));
+        s = df2_warp_sum(s);
+        if (lane == 0) tot[warp] = s;
+    } else if (tid == 128 && !trace_only) {
+        const double t = sc->t_base + (double)(n_lvl - sc->n_base) * sc->dt;
+        float E[3];
+        field_at_f(sc->field, t, E);
+        E_sh[0] = E[0];
+        E_sh[1] = E[1];
+        E_sh[2] = E[2];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // Tr(rho S) = N_e - c0 + sum_A dq_A;  f - 1 = (N_e - Tr) / Tr ~ (c0 - sum dq) / N_e
+        const float2 d = tot[3];
+        const float eps = (((float)sc->c0_trace - d.x) - d.y) * a.inv_ne;
+        sc->eps_lvl[slot] = eps;
+        sc->trace_lvl[slot] = (sc->n_e - sc->c0_trace) + ((double)d.x + (double)d.y);
+    }
+    if (trace_only) {
+        for (int i = tid; i <= a.nct; i += 256) a.count[i] = 0;
+        return;
+    }
+    const float Ex = E_sh[0], Ey = E_sh[1], Ez = E_sh[2];
+    float mx = 0.f;
+    for (int A = tid; A < a.nat; A += 256) {
+        // the tiles' partial potentials of atom A, sixteen loads in flight at a time, into
+        // four interleaved sums
+        float2 acc[4] = {};
+        if (a.scc)
+            for (int r0 = 0; r0 < a.nct; r0 += 16) {
+                float2 v[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u)
+                    v[u] = r0 + u < a.nct ? ldcg2(a.pv + (size_t)(r0 + u) * a.nat + A)
+                                          : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < 16; ++u) acc[u & 3] = df2_add(acc[u & 3], v[u]);
+            }
+        const float2 s = df2_add(df2_add(acc[0], acc[1]), df2_add(acc[2], acc[3]));
+        const float ext = fmaf(a.R2[3 * A].x, Ex, fmaf(a.R2[3 * A + 1].x, Ey, a.R2[3 * A + 2].x * Ez));
+        const float dv = s.x + (s.y + (ext + a.c_res[A]));
+        for (int k = 0; k < a.nper; ++k) a.dv_f[A * a.nper + k] = dv;
+        mx = fmaxf(mx, fabsf(dv));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) red[warp] = mx;
+    __syncthreads();
+    if (tid == 0) {
+        float m = red[0];
+        for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w]);
+        tc::DynScales* dy = a.dyn;
+        if (dy) {
+            dy->max_dv = (double)m;
+            if (a.has_scales) {
+                dy->s_dh = pscale_f(m);
+                dy->s_dm = pscale_f(m * (float)dy->sinv_norm);
+            }
+            for (int k = 0; k < tc::kMaxParts; ++k) dy->max_x[k] = 0.0;
+            if (step_end) {
+                // the maximum the update's blocks accumulated (atomics, read through L2)
+                dy->max_drho[slot] = __ldcg(&dy->max_drho[2]);
+                dy->max_drho[2] = 0.0;
+            }
+        }
+        if (step_end) sc->step = n_lvl;
+    }
+    if (warp == 1) {
+        // dipole (lanes 0-2, one component each) into sc and the history slot of step n_lvl
+        const int k = lane < 3 ? lane : 0;
+        const double mu = sc->mu_ref[k] - ((double)tot[k].x + (double)tot[k].y);
+        const double ek = mu * (double)E_sh[k];
+        const double e_ext = -(ek + __shfl_down_sync(0xffffffffu, ek, 1) +
+                               __shfl_down_sync(0xffffffffu, ek, 2));
+        if (lane < 3) {
+            long long h = n_lvl % sc->hist_cap;
+            if (h < 0) h += sc->hist_cap;
+            sc->mu[k] = mu;
+            sc->E[k] = (double)E_sh[k];
+            a.hist[3 * h + k] = mu;
+        }
+        if (lane == 0) sc->e_ext = e_ext;
+    }
+    for (int i = tid; i <= a.nct; i += 256) a.count[i] = 0;
+}
+
+// After a block has written its row partials: count it towards the row tiles it covered
+// (tile_target arrivals complete a tile); the block completing a tile runs the tile's
+// stage, and the block completing the last tile runs the final stage.  Every writer
+// fences before the counting atomics, and the stages read what other blocks wrote
+// through L2 (ld.global.cg).
+__device__ void level_arrive(const LevelArgs& a, int t0, int t1, int tile_target, int slot,
+                             long long n_lvl, bool trace_only, bool step_end) {
+    __shared__ int done[2];
+    __shared__ int last;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    // the writers of what the tail reads (row partials: first warp; maxima: first lanes)
+    if (threadIdx.y == 0 || threadIdx.x == 0) __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        done[0] = atomicAdd(&a.count[t0], 1) == tile_target - 1;
+        done[1] = t1 != t0 ? atomicAdd(&a.count[t1], 1) == tile_target - 1 : 0;
+        __threadfence();
+    }
+    __syncthreads();
+    int ntile = 0;
+    for (int k = 0; k < 2; ++k) {
+        if (!done[k]) continue;
+        level_rowtile(a, k ? t1 : t0, trace_only);
+        ++ntile;
+        __threadfence();
+        __syncthreads();
+    }
+    if (ntile == 0) return;
+    if (tid == 0) {
+        last = atomicAdd(&a.count[a.nct], ntile) + ntile == a.nct;
+        __threadfence();
+    }
+    __syncthreads();
+    if (last) level_final(a, slot, n_lvl, trace_only, step_end);
+}
+
 // Update of the FP32-pair master (eq:leapfrog, eq:eomrho, frozen nuclei): the same
 // tile-pair scheme and operands as k_update, with the increment factor * rhodot formed
 // as fh * d + fl * d (factor = fh + fl) so the step length carries no FP32 rounding.
-// Mulliken row partials of the deviation: FP32 products with S, summed in FP64.
-__global__ void __launch_bounds__(256, 6)
-    k_update_df(int N, int nct, MasterPtrs base, MasterPtrs out, float fh, float fl,
-                double factor, const float* __restrict__ Sf, double* __restrict__ partial,
-                DevScalars* __restrict__ sc, UpdateOperands ops) {
+// The base level is first renormalised to Tr(rho S) = N_e: rho_base <- f rho_base with
+// f = 1 + eps from its trace (Sec. 2.3: the exact leapfrog conserves the electron number;
+// the reduced products do not, by a few 1e-11 per step), i.e. the deviation gains
+// eps (rho_ref + deviation).  Mulliken row partials of the new deviation in FP32-pair
+// arithmetic; the last blocks evaluate the new level (level_arrive).
+__device__ __forceinline__ void update_df_block(const UpdateDfArgs& A, int b) {
+    const int N = A.N, nct = A.nct;
+    const MasterPtrs& base = A.base;
+    const MasterPtrs& out = A.out;
+    const float fh = A.fh, fl = A.fl;
+    const double factor = A.factor;
+    const float* __restrict__ Sf = A.Sf;
+    const float* __restrict__ rgs = A.rgs;
+    DevScalars* __restrict__ sc = A.sc;
+    const UpdateOperands& ops = A.ops;
+    const LevelArgs& lv = A.lv;
+    const int out_slot = A.out_slot;
     // one block per tile pair bi <= bj: block b = bj (bj + 1) / 2 + bi
-    const int b = blockIdx.x;
     int bj = (int)((sqrtf(8.0f * (float)b + 1.0f) - 1.0f) * 0.5f);
     while (bj * (bj + 1) / 2 > b) --bj;
     while ((bj + 1) * (bj + 2) / 2 <= b) ++bj;
     const int bi = b - bj * (bj + 1) / 2;
     constexpr int RPT = kTile / 8;
-    float op_scale = ops.scale;
-    if (ops.dyn) {
-        __shared__ float s_bound;
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
+    __shared__ float s_bound;
+    __shared__ float eps_sh;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        eps_sh = sc->eps_lvl[ops.base_slot];
+        if (ops.dyn) {
             // |X| <= the sum of the maxima of its partial products
             const tc::DynScales* d = ops.dyn;
-            double mre = 0.0, mim = 0.0;
-            for (int q = 0; q < ops.nre; ++q) mre += d->max_x[q];
-            for (int q = 0; q < ops.nim; ++q) mim += d->max_x[ops.nre + q];
-            s_bound = tc::pscale(d->max_drho[ops.base_slot] + fabs(factor) * 2.0 * fmax(mre, mim));
+            float mre = 0.f, mim = 0.f;
+            for (int q = 0; q < ops.nre; ++q) mre += (float)d->max_x[q];
+            for (int q = 0; q < ops.nim; ++q) mim += (float)d->max_x[ops.nre + q];
+            s_bound = pscale_f((float)d->max_drho[ops.base_slot] * (1.f + fabsf(eps_sh)) +
+                               8.f * fabsf(eps_sh) +
+                               fabsf((float)factor) * 2.0f * fmaxf(mre, mim));
         }
-        __syncthreads();
-        op_scale = s_bound;
     }
+    __syncthreads();
+    const float op_scale = ops.dyn ? s_bound : ops.scale;
+    const float eps = eps_sh;
     __shared__ float xr_ij[kTile][kTile + 1], xi_ij[kTile][kTile + 1];
     __shared__ float xr_ji[kTile][kTile + 1], xi_ji[kTile][kTile + 1];
-    __shared__ double pv_s[kTile][kTile + 1];
+    __shared__ float2 pv_s[kTile][kTile + 1];
     const int tx = threadIdx.x, ty = threadIdx.y;
     // X = sum of its partial products, in a fixed order (all loads issued first)
     auto load_x = [&](size_t i, float& a, float& b) {
@@ -841,11 +1136,11 @@ __global__ void __launch_bounds__(256, 6)
     float dmax = 0.f;
     for (int half = 0; half < (bi == bj ? 1 : 2); ++half) {
         const int ti = half ? bj : bi, tj = half ? bi : bj;
-        float brh[RPT], brl[RPT], bih[RPT], bil[RPT], sv[RPT];
+        float brh[RPT], brl[RPT], bih[RPT], bil[RPT], sv[RPT], gv[RPT];
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
             const int r = ti * kTile + ty + 8 * k, c = tj * kTile + tx;
-            brh[k] = brl[k] = bih[k] = bil[k] = sv[k] = 0.f;
+            brh[k] = brl[k] = bih[k] = bil[k] = sv[k] = gv[k] = 0.f;
             if (r < N && c < N) {
                 const size_t i = (size_t)r * N + c;
                 brh[k] = base.re_hi[i];
@@ -853,13 +1148,14 @@ __global__ void __launch_bounds__(256, 6)
                 bih[k] = base.im_hi[i];
                 bil[k] = base.im_lo[i];
                 sv[k] = Sf[i];
+                if (eps != 0.f) gv[k] = rgs[i];
             }
         }
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
             const int y = ty + 8 * k;
             const int r = ti * kTile + y, c = tj * kTile + tx;
-            double pv = 0.0;
+            float2 pv = make_float2(0.f, 0.f);
             if (r < N && c < N) {
                 float x_ij_re, x_ij_im, x_ji_re, x_ji_im;
                 if (!half) {
@@ -880,6 +1176,11 @@ __global__ void __launch_bounds__(256, 6)
                 const float ire = fmaf(fh, dre, fl * dre);
                 const float iim = fmaf(fh, dim, fl * dim);
                 float rh = brh[k], rl = brl[k], ih = bih[k], il = bil[k];
+                if (eps != 0.f) {
+                    // renormalised base: f (rho_ref + dev) - rho_ref = dev + eps (rho_ref + dev)
+                    df_add(rh, rl, eps * (gv[k] + rh));
+                    df_add(ih, il, eps * ih);
+                }
                 df_add(rh, rl, ire);
                 df_add(ih, il, iim);
                 const size_t i = (size_t)r * N + c;
@@ -887,7 +1188,7 @@ __global__ void __launch_bounds__(256, 6)
                 out.re_lo[i] = rl;
                 out.im_hi[i] = ih;
                 out.im_lo[i] = il;
-                pv = (double)(rh * sv[k]);
+                pv = mulliken_elem(rh, rl, sv[k]);
                 if (ops.dyn) dmax = fmaxf(dmax, fmaxf(fabsf(rh), fabsf(ih)));
                 if (ops.re[0]) {
                     // operands of the tensor-core products are K-major: Re rho is symmetric,
@@ -921,10 +1222,8 @@ __global__ void __launch_bounds__(256, 6)
         __syncthreads();
         if (ty == 0) {
             const int r = ti * kTile + tx;
-            double sum = 0.0;
-#pragma unroll 8
-            for (int k = 0; k < kTile; ++k) sum += pv_s[tx][k];
-            if (r < N) partial[(size_t)r * nct + tj] = sum;
+            const float2 sum = tile_row_sum(pv_s[tx]);
+            if (r < N) const_cast<float2*>(lv.partial)[(size_t)r * nct + tj] = sum;
         }
         __syncthreads();
     }
@@ -933,12 +1232,42 @@ __global__ void __launch_bounds__(256, 6)
         if (tx == 0)
             atomicMax(reinterpret_cast<unsigned long long*>(&ops.dyn->max_drho[2]),
                       (unsigned long long)__double_as_longlong((double)dmax));
-        if (bi == 0 && bj == 0 && tx == 0 && ty == 0) {
-            ops.dyn->s_rho = op_scale;
-            ops.dyn->max_dv = 0.0;
-        }
+        if (bi == 0 && bj == 0 && tx == 0 && ty == 0) ops.dyn->s_rho = op_scale;
     }
-    if (bi == 0 && bj == 0 && tx == 0 && ty == 0) sc->step += 1;
+    __syncthreads();
+    level_arrive(lv, bi, bj, nct, out_slot, sc->step + 1, false, true);
+}
+
+__global__ void __launch_bounds__(256, 6) k_update_df(UpdateDfArgs a) { update_df_block(a, blockIdx.x); }
+
+__global__ void __launch_bounds__(256, 6)
+    k_update_df_grouped(const UpdateDfArgs* __restrict__ args, const int2* __restrict__ work) {
+    const int2 w = work[blockIdx.x];
+    update_df_block(args[w.x], w.y);
+}
+
+// Per-level evaluation outside a step: block r runs the row-tile stage of tile r and the
+// block completing the last tile the final stage (the arithmetic of the update's tail).
+__global__ void __launch_bounds__(256) k_level(LevelArgs lv, int slot, int trace_only) {
+    level_arrive(lv, blockIdx.x, blockIdx.x, 1, slot, lv.sc->step, trace_only != 0, false);
+}
+
+// FP64 populations from the (hi, lo) row partials of the deviation: one warp per atom
+__global__ void k_charges_df(int nat, int nper, int nct, const float2* __restrict__ partial,
+                             const double* __restrict__ qbase, const double* __restrict__ q0,
+                             double* __restrict__ q, double* __restrict__ dq) {
+    const int lane = threadIdx.x & 31;
+    const int A = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (A >= nat) return;
+    const float2* p = partial + (size_t)A * nper * nct;
+    double s = 0.0;
+    for (int i = lane; i < nper * nct; i += 32) s += (double)p[i].x + (double)p[i].y;
+    s = warp_sum(s);
+    if (lane == 0) {
+        s += qbase[A];
+        q[A] = s;
+        dq[A] = s - q0[A];
+    }
 }
 
 // master (hi, lo) of rho - rho_ref from the FP64 view
@@ -969,24 +1298,25 @@ __global__ void k_master_to_view(size_t n, MasterPtrs m, const double* __restric
 }
 
 // Mulliken row partials of the deviation held by the master, with the arithmetic of
-// k_update_df (FP32 products, FP64 column-order sums)
+// k_update_df (exact high products, FP32-pair sums in the same column order)
 __global__ void k_master_partials(int N, int nct, MasterPtrs m, const float* __restrict__ Sf,
-                                  double* __restrict__ partial) {
-    __shared__ double pv_s[kTile][kTile + 1];
+                                  float2* __restrict__ partial) {
+    __shared__ float2 pv_s[kTile][kTile + 1];
     const int ct = blockIdx.x;
     const int col = ct * kTile + threadIdx.x;
     for (int y = threadIdx.y; y < kTile; y += blockDim.y) {
         const int row = blockIdx.y * kTile + y;
-        double v = 0.0;
-        if (row < N && col < N) v = (double)(m.re_hi[(size_t)row * N + col] * Sf[(size_t)row * N + col]);
+        float2 v = make_float2(0.f, 0.f);
+        if (row < N && col < N) {
+            const size_t i = (size_t)row * N + col;
+            v = mulliken_elem(m.re_hi[i], m.re_lo[i], Sf[i]);
+        }
         pv_s[y][threadIdx.x] = v;
     }
     __syncthreads();
     if (threadIdx.y == 0) {
         const int row = blockIdx.y * kTile + threadIdx.x;
-        double sum = 0.0;
-#pragma unroll 8
-        for (int k = 0; k < kTile; ++k) sum += pv_s[threadIdx.x][k];
+        const float2 sum = tile_row_sum(pv_s[threadIdx.x]);
         if (row < N) partial[(size_t)row * nct + ct] = sum;
     }
 }
@@ -1046,13 +1376,45 @@ __global__ void k_master_pieces(int N, MasterPtrs m, UpdateOperands ops, const d
 
 }  // namespace
 
+UpdateDfArgs update_df_args(const Ctx& c, const MasterPtrs& base, const MasterPtrs& out,
+                            double factor, DevScalars* sc, const UpdateOperands& ops,
+                            const LevelArgs& lv) {
+    UpdateDfArgs a{};
+    a.N = c.N;
+    a.nct = c.nct;
+    a.out_slot = out.re_hi == c.ms[0].re_hi ? 0 : 1;
+    a.base = base;
+    a.out = out;
+    a.fh = (float)factor;
+    a.fl = (float)(factor - (double)a.fh);
+    a.factor = factor;
+    a.Sf = c.S_f;
+    a.rgs = c.rref_f;
+    a.sc = sc;
+    a.ops = ops;
+    a.lv = lv;
+    return a;
+}
+
 void launch_update_df(const Ctx& c, const MasterPtrs& base, const MasterPtrs& out, double factor,
-                      double* partial, DevScalars* sc, const UpdateOperands& ops, cudaStream_t st) {
-    const float fh = (float)factor;
-    const float fl = (float)(factor - (double)fh);
-    dim3 b(kTile, 8);
-    k_update_df<<<c.nct * (c.nct + 1) / 2, b, 0, st>>>(c.N, c.nct, base, out, fh, fl, factor,
-                                                        c.S_f, partial, sc, ops);
+                      DevScalars* sc, const UpdateOperands& ops, const LevelArgs& lv,
+                      cudaStream_t st) {
+    k_update_df<<<c.nct * (c.nct + 1) / 2, dim3(kTile, 8), 0, st>>>(
+        update_df_args(c, base, out, factor, sc, ops, lv));
+}
+
+void launch_update_df_grouped(const UpdateDfArgs* args, const int2* work, int nwork,
+                              cudaStream_t st) {
+    k_update_df_grouped<<<nwork, dim3(kTile, 8), 0, st>>>(args, work);
+}
+
+void launch_level(const Ctx& c, const LevelArgs& lv, int slot, int trace_only, cudaStream_t st) {
+    k_level<<<c.nct, dim3(kTile, 8), 0, st>>>(lv, slot, trace_only);
+}
+
+void launch_charges_df(const Ctx& c, const float2* partial, double* q, double* dq, cudaStream_t st) {
+    k_charges_df<<<(c.nat + 7) / 8, 256, 0, st>>>(c.nat, c.nper, c.nct, partial, c.qbase, c.d_q0, q,
+                                                  dq);
 }
 
 void launch_view_to_master(const Ctx& c, const double* rre, const double* rim, const MasterPtrs& m,
@@ -1065,7 +1427,7 @@ void launch_master_to_view(const Ctx& c, const MasterPtrs& m, double* rre, doubl
     k_master_to_view<<<1216, 256, 0, st>>>((size_t)c.N * c.N, m, c.rho_ref, rre, rim);
 }
 
-void launch_master_partials(const Ctx& c, const MasterPtrs& m, double* partial, cudaStream_t st) {
+void launch_master_partials(const Ctx& c, const MasterPtrs& m, float2* partial, cudaStream_t st) {
     dim3 b(kTile, 8);
     k_master_partials<<<dim3(c.nct, c.nct), b, 0, st>>>(c.N, c.nct, m, c.S_f, partial);
 }

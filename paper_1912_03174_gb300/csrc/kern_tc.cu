@@ -85,9 +85,11 @@ __host__ __device__ constexpr int smem_total() {
     return stages<S, BN>() * stage_bytes<S, BN>() + 1024 + 256;
 }
 
+// One 128 x BN output tile (tile column tx, tile row ty) of part tz of a product.  The
+// tensor maps may live in kernel parameters or in global memory (grouped launches).
 template <int SCHEME, int BN>
-__global__ void __launch_bounds__(kThreads, 1)
-    k_split_gemm(const __grid_constant__ Maps maps, GemmParams p) {
+__device__ __forceinline__ void gemm_tile(const Maps& maps, const GemmParams& p, int tx, int ty,
+                                          int tz) {
     constexpr int PIECES = Cfg<SCHEME>::PIECES, STAGES = stages<SCHEME, BN>();
     constexpr int SB = stage_bytes<SCHEME, BN>();
     constexpr int BTILE = BN * BK * 2;
@@ -101,8 +103,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                    done = smem_u32(bars + 2 * STAGES);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const GemmPart& P = p.part[blockIdx.z];
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const GemmPart& P = p.part[tz];
+    const int m0 = ty * BM, n0 = tx * BN;
     const int nkb = (P.K + BK - 1) / BK;
     // TMEM columns [h BN, (h + 1) BN): head accumulator of K slice h; then the tail one
     const int nheads = n_heads(SCHEME, P.K);
@@ -244,7 +246,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         if (j < lim) m = fmaxf(m, fabsf(v[j]));
                 for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
                 if (lane == 0)
-                    atomicMax(reinterpret_cast<unsigned long long*>(&p.max_out[blockIdx.z]),
+                    atomicMax(reinterpret_cast<unsigned long long*>(&p.max_out[tz]),
                               static_cast<unsigned long long>(__double_as_longlong(static_cast<double>(m))));
             }
             if (row >= p.M) continue;
@@ -328,6 +330,24 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+template <int SCHEME, int BN>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_split_gemm(const __grid_constant__ Maps maps, GemmParams p) {
+    gemm_tile<SCHEME, BN>(maps, p, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Many independent products in one launch: block b takes work[b] = (problem, tile index
+// within the problem, parts outermost), so the order of the work list is the schedule.
+template <int SCHEME, int BN>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_split_gemm_grouped(const GroupedGemm* __restrict__ g, const int2* __restrict__ work) {
+    const int2 w = work[blockIdx.x];
+    const GroupedGemm& G = g[w.x];
+    const int per = G.tiles_x * G.tiles_y;
+    const int tz = w.y / per, r = w.y - tz * per;
+    gemm_tile<SCHEME, BN>(G.maps, G.p, r % G.tiles_x, r / G.tiles_x, tz);
+}
+
 // ---- splitting kernels (FP64 -> scaled 16-bit pieces) ----
 
 struct Pieces {
@@ -353,34 +373,24 @@ __global__ void k_split(int rows, int cols, const double* __restrict__ in,
     if (!ok && err) atomicCAS(err, 0, 4);
 }
 
-// delta H_kj = 1/2 S_kj (dv_k + dv_j) from FP32 copies of S and dv = v - v_ref
+// delta H_kj = 1/2 S_kj (dv_k + dv_j) from FP32 copies of S and dv = v - v_ref; block
+// (bx, by) of a grid with gy block rows
 template <int SCHEME>
-__global__ void k_split_dham(int N, const float* __restrict__ S, const float* __restrict__ dv,
-                             float scale_const, int bf16, Pieces out, int ld_out,
-                             DynScales* __restrict__ dyn, int* err) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    const int r = blockIdx.y * blockDim.y + threadIdx.y;
-    float s = scale_const;
-    if (dyn) {
-        // |delta H| <= max |dv| (|S_kj| <= 1), |delta M| <= ||S^-1||_inf max |dv|;
-        // one thread per block evaluates the scale (FP64 frexp/ldexp are slow here)
-        __shared__ float s_sh;
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
-            const double m = dyn->max_dv;
-            s_sh = pscale(m);
-            if (blockIdx.x == 0 && blockIdx.y == 0) {
-                dyn->s_dh = s_sh;
-                dyn->s_dm = pscale(m * dyn->sinv_norm);
-            }
-        }
-        __syncthreads();
-        s = s_sh;
-    }
+__device__ __forceinline__ void split_dham_block(int N, const float* __restrict__ S,
+                                                 const float* __restrict__ dv, float scale_const,
+                                                 int bf16, const Pieces& out, int ld_out,
+                                                 const DynScales* __restrict__ dyn, int* err,
+                                                 int bx, int by, int gy) {
+    const int c = bx * blockDim.x + threadIdx.x;
+    const int r = by * blockDim.y + threadIdx.y;
+    // FP16X6: the scale of this step, pscale(max |dv|), written with dv by the evaluation
+    // of the level (|delta H| <= max |dv| since |S_kj| <= 1)
+    const float s = dyn ? dyn->s_dh : scale_const;
     if (c >= N) return;
     // rows r, r + gridDim.y blockDim.y, ...: the scale prologue is paid once per block
     const float dvc = dv[c];
     bool ok = true;
-    for (int row = r; row < N; row += gridDim.y * blockDim.y) {
+    for (int row = r; row < N; row += gy * blockDim.y) {
         uint16_t q[3];
         ok &= split_value<SCHEME>(0.5f * S[static_cast<size_t>(row) * N + c] * (dv[row] + dvc) * s,
                                   bf16, q);
@@ -391,7 +401,44 @@ __global__ void k_split_dham(int N, const float* __restrict__ S, const float* __
     if (!ok && err) atomicCAS(err, 0, 4);
 }
 
+template <int SCHEME>
+__global__ void k_split_dham(int N, const float* __restrict__ S, const float* __restrict__ dv,
+                             float scale_const, int bf16, Pieces out, int ld_out,
+                             DynScales* __restrict__ dyn, int* err) {
+    split_dham_block<SCHEME>(N, S, dv, scale_const, bf16, out, ld_out, dyn, err, blockIdx.x,
+                             blockIdx.y, gridDim.y);
+}
+
+template <int SCHEME>
+__global__ void k_split_dham_grouped(const SplitDhArgs* __restrict__ args,
+                                     const int2* __restrict__ work) {
+    const int2 w = work[blockIdx.x];
+    const SplitDhArgs& a = args[w.x];
+    const int gx = (a.N + 31) / 32, gy = (a.N + 63) / 64;
+    const Pieces out{{a.out[0], a.out[1], a.out[2]}};
+    split_dham_block<SCHEME>(a.N, a.S, a.dv, a.scale, a.bf16, out, a.ld_out, a.dyn, a.err,
+                             w.y % gx, w.y / gx, gy);
+}
+
+// Failure-detection probe: one thread waits on an mbarrier that nothing arrives on, polling
+// at most `polls` times, then records a time-out (code 5).  No copy or MMA is in flight and
+// no TMEM is held, so the expired wait leaves nothing behind.
+__global__ void k_wait_probe(long long polls, int* err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    const uint32_t b = smem_u32(&bar);
+    mbar_init(b, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (long long i = 0; i < polls; ++i)
+        if (mbar_try_wait(b, 0)) return;
+    atomicCAS(err, 0, 5);
+}
+
 }  // namespace
+
+void launch_wait_probe(long long polls, int* err, cudaStream_t st) {
+    k_wait_probe<<<1, 32, 0, st>>>(polls, err);
+}
 
 size_t smem_bytes(int scheme) {
     return scheme == kHiLo ? smem_total<kHiLo, 128>() : smem_total<kHead3, 128>();
@@ -438,8 +485,22 @@ cudaError_t set_smem() {
                                 smem_total<S, BN>());
 }
 
+template <int S, int BN>
+cudaError_t set_smem_grouped() {
+    return cudaFuncSetAttribute(k_split_gemm_grouped<S, BN>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem_total<S, BN>());
+}
+
 cudaError_t prepare() {
     cudaError_t e = set_smem<kHiLo, 64>();
+    if (e == cudaSuccess) e = set_smem_grouped<kHiLo, 64>();
+    if (e == cudaSuccess) e = set_smem_grouped<kHead3, 64>();
+    if (e == cudaSuccess) e = set_smem_grouped<kHiLo, 128>();
+    if (e == cudaSuccess) e = set_smem_grouped<kHead3, 128>();
+    if (e == cudaSuccess) e = set_smem_grouped<kHiLo, 176>();
+    if (e == cudaSuccess) e = set_smem_grouped<kHead3, 176>();
+    if (e == cudaSuccess) e = set_smem_grouped<kHiLo, 256>();
+    if (e == cudaSuccess) e = set_smem_grouped<kHead3, 256>();
     if (e == cudaSuccess) e = set_smem<kHead3, 64>();
     if (e == cudaSuccess) e = set_smem<kHiLo, 128>();
     if (e == cudaSuccess) e = set_smem<kHead3, 128>();
@@ -481,6 +542,26 @@ cudaError_t launch(int scheme, const Maps& m, const GemmParams& p, int nparts, c
     return cudaGetLastError();
 }
 
+cudaError_t launch_grouped(int scheme, const GroupedGemm* g, const int2* work, int nwork,
+                           cudaStream_t st, int bn) {
+    if (nwork < 1 || (bn != 64 && bn != 128 && bn != 176 && bn != 256)) return cudaErrorInvalidValue;
+#define TDB_GROUPED(S, W)                                                                     \
+    k_split_gemm_grouped<S, W><<<nwork, kThreads, smem_total<S, W>(), st>>>(g, work)
+    if (scheme == kHiLo) {
+        if (bn == 64) TDB_GROUPED(kHiLo, 64);
+        else if (bn == 128) TDB_GROUPED(kHiLo, 128);
+        else if (bn == 176) TDB_GROUPED(kHiLo, 176);
+        else TDB_GROUPED(kHiLo, 256);
+    } else {
+        if (bn == 64) TDB_GROUPED(kHead3, 64);
+        else if (bn == 128) TDB_GROUPED(kHead3, 128);
+        else if (bn == 176) TDB_GROUPED(kHead3, 176);
+        else TDB_GROUPED(kHead3, 256);
+    }
+#undef TDB_GROUPED
+    return cudaGetLastError();
+}
+
 void launch_split(int scheme, int rows, int cols, const double* in, int ld_in, float scale, int sign,
                   int bf16, uint16_t* const* pieces, int ld_out, cudaStream_t st, const double* sub,
                   const float* scale_dev, int* err) {
@@ -493,6 +574,31 @@ void launch_split(int scheme, int rows, int cols, const double* in, int ld_in, f
     else
         k_split<kHead3><<<g, b, 0, st>>>(rows, cols, in, sub, ld_in, scale, scale_dev, sign, bf16,
                                          o, ld_out, err);
+}
+
+SplitDhArgs split_dham_args(int scheme, int N, const float* S, const float* dv, float scale,
+                            int bf16, uint16_t* const* pieces, int ld_out, DynScales* dyn, int* err) {
+    SplitDhArgs a{};
+    a.N = N;
+    a.S = S;
+    a.dv = dv;
+    a.scale = scale;
+    a.bf16 = bf16;
+    for (int t = 0; t < 3; ++t) a.out[t] = (t < 2 || scheme == kHead3) ? pieces[t] : nullptr;
+    a.ld_out = ld_out;
+    a.dyn = scheme == kHead3 ? dyn : nullptr;
+    a.err = err;
+    return a;
+}
+
+int split_dham_blocks(int N) { return ((N + 31) / 32) * ((N + 63) / 64); }
+
+void launch_split_dham_grouped(int scheme, const SplitDhArgs* args, const int2* work, int nwork,
+                               cudaStream_t st) {
+    if (scheme == kHiLo)
+        k_split_dham_grouped<kHiLo><<<nwork, dim3(32, 8), 0, st>>>(args, work);
+    else
+        k_split_dham_grouped<kHead3><<<nwork, dim3(32, 8), 0, st>>>(args, work);
 }
 
 void launch_split_dham(int scheme, int N, const float* S, const float* dv, float scale, int bf16,

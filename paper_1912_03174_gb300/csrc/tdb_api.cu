@@ -160,7 +160,7 @@ size_t carve(Ctx& c, char* base) {
     c.gdq = k.take<double>(nat);
     c.v_orb = k.take<double>(N);
     c.v_ref = k.take<double>(N);
-    c.hist = k.take<double>(3 * (size_t)c.prm.history_cap);
+    c.hist = k.take<double>(3 * ((size_t)c.prm.history_cap + 1));
     c.obs_blocks = k.take<double>(4 * kObsBlocks);
     c.obs_out = k.take<double>(16 + 2 * N);   // reductions, small energies, eigenvalues, occupations
     c.sc = k.take<DevScalars>(1);
@@ -174,6 +174,13 @@ size_t carve(Ctx& c, char* base) {
         c.qbase = k.take<double>(nat);
         c.rho_ref = k.take<double>(NN);
         c.Mgs_f = k.take<float>(NN);
+        c.rref_f = k.take<float>(NN);
+        c.gam2 = k.take<float2>(nat * nat);
+        c.R2 = k.take<float2>(3 * nat);
+        c.lv_pv = k.take<float2>((size_t)c.nct * nat);
+        c.lv_part = k.take<float2>(4 * (size_t)c.nct);
+        c.c_res = k.take<float>(nat);
+        c.lv_count = k.take<int>((size_t)c.nct + 1);
     }
     if (mixed(c)) {
         c.dv_f = k.take<float>(N);
@@ -199,7 +206,6 @@ size_t carve(Ctx& c, char* base) {
         c.Sinv_f = k.take<float>(NN);
         c.dM_f = k.take<float>(2 * NN);     // [delta M | M], row stride 2N
         c.M_f = c.dM_f ? c.dM_f + N : nullptr;
-        c.rref_f = k.take<float>(NN);
     }
     if (tensor(c)) {
         const size_t Np = (N + 63) / 64 * 64;
@@ -501,7 +507,7 @@ tdb_status upload_clock(Ctx& c, long long step, long long n_base, double t_base)
     h.n_base = n_base;
     h.t_base = t_base;
     h.dt = c.prm.dt;
-    h.hist_cap = c.prm.history_cap;
+    h.hist_cap = c.prm.history_cap + 1;
     CK(cudaMemcpyAsync(c.sc, &h, sizeof h, cudaMemcpyHostToDevice, c.stream));
     CK(cudaStreamSynchronize(c.stream));
     c.n = step;
@@ -526,11 +532,40 @@ UpdateOperands master_operands(Ctx& c) {
     return ops;
 }
 
-// Reduced forms: partials and operands of rho_n from the master.  With `restored`
-// (FP16X6 resuming from a checkpoint of the same form) the scales saved with the state
-// are kept, so that the continuation repeats the original run bit for bit.
+// Arguments of the per-level evaluation of the reduced forms.
+LevelArgs level_args(Ctx& c) {
+    LevelArgs a{};
+    a.nat = c.nat;
+    a.nper = c.nper;
+    a.nct = c.nct;
+    a.scc = c.prm.scc;
+    a.partial = reinterpret_cast<const float2*>(c.partial);
+    a.gam2 = c.gam2;
+    a.R2 = c.R2;
+    a.c_res = c.c_res;
+    a.pv = c.lv_pv;
+    a.part = c.lv_part;
+    a.dv_f = c.dv_f;
+    a.dyn = head3(c) ? c.dyn : nullptr;
+    a.has_scales = head3(c) ? 1 : 0;
+    a.sc = c.sc;
+    a.hist = c.hist;
+    a.count = c.lv_count;
+    a.inv_ne = (float)(1.0 / c.n_electrons);
+    return a;
+}
+
+// Reduced forms: partials and operands of rho_n from the master, then the evaluation of
+// both levels (Tr(rho S) of rho_{n-1}; charges, potential, dipole and trace of rho_n), with
+// the arithmetic the update's tail uses, so that a loaded state continues bit for bit.
+// With `restored` (FP16X6 resuming from a checkpoint of the same form) the scales saved
+// with the state are kept.
 tdb_status derived_from_master(Ctx& c, bool restored = false) {
-    launch_master_partials(c, c.ms[c.cur], c.partial, c.stream);
+    float2* part = reinterpret_cast<float2*>(c.partial);
+    const LevelArgs lv = level_args(c);
+    launch_master_partials(c, c.ms[c.cur ^ 1], part, c.stream);
+    launch_level(c, lv, c.cur ^ 1, 1, c.stream);
+    launch_master_partials(c, c.ms[c.cur], part, c.stream);
     if (tensor(c)) {
         UpdateOperands ops = master_operands(c);
         if (head3(c) && restored) {
@@ -542,14 +577,12 @@ tdb_status derived_from_master(Ctx& c, bool restored = false) {
                 launch_master_absmax(c, c.ms[l], &c.dyn->max_drho[l], c.stream);
             }
             launch_master_pieces(c, c.ms[c.cur], ops, &c.dyn->max_drho[c.cur], nullptr, c.stream);
-            // the next step's bookkeeping moves max_drho[2] into max_drho[cur]: keep it equal
-            CK(cudaMemcpyAsync(&c.dyn->max_drho[2], &c.dyn->max_drho[c.cur], sizeof(double),
-                               cudaMemcpyDeviceToDevice, c.stream));
-            CK(cudaMemsetAsync(&c.dyn->max_dv, 0, sizeof(double), c.stream));
+            CK(cudaMemsetAsync(&c.dyn->max_drho[2], 0, sizeof(double), c.stream));
         } else {
             launch_master_pieces(c, c.ms[c.cur], ops, nullptr, nullptr, c.stream);
         }
     }
+    launch_level(c, lv, c.cur, 0, c.stream);
     CKL();
     return TDB_OK;
 }
@@ -574,6 +607,50 @@ tdb_status materialize(Ctx& c) {
     for (int l = 0; l < 2; ++l) launch_master_to_view(c, c.ms[l], c.rho_re[l], c.rho_im[l], c.stream);
     CKL();
     c.view_valid = true;
+    return TDB_OK;
+}
+
+// Constants of the reduced forms' per-level evaluation after the ground state: gamma and
+// the positions as FP32 pairs, the SCC residual of rho_ref per atom, N_e - sum_A q_A(rho_ref)
+// and the dipole of rho_ref (host FP64, once).
+tdb_status setup_level_constants(Ctx& c) {
+    const int nat = c.nat, N = c.N;
+    std::vector<double> g((size_t)nat * nat), qb(nat), vref(N), q0v(nat);
+    DevScalars h{};
+    CK(cudaMemcpyAsync(g.data(), c.gamma, sizeof(double) * g.size(), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaMemcpyAsync(qb.data(), c.qbase, sizeof(double) * nat, cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaMemcpyAsync(vref.data(), c.v_ref, sizeof(double) * N, cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaMemcpyAsync(q0v.data(), c.d_q0, sizeof(double) * nat, cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaMemcpyAsync(&h, c.sc, sizeof h, cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    auto split = [](double x) {
+        const float h = (float)x;
+        return make_float2(h, (float)(x - (double)h));
+    };
+    std::vector<float2> g2(g.size()), r2(3 * (size_t)nat);
+    for (size_t i = 0; i < g.size(); ++i) g2[i] = split(g[i]);
+    for (int i = 0; i < 3 * nat; ++i) r2[i] = split(c.R[i]);
+    std::vector<float> cres(nat);
+    double qsum = 0.0, mu[3] = {0.0, 0.0, 0.0};
+    for (int A = 0; A < nat; ++A) {
+        qsum += qb[A];
+        const double dq = qb[A] - q0v[A];
+        for (int k = 0; k < 3; ++k) mu[k] -= dq * c.R[3 * A + k];
+        double gd = 0.0;
+        if (c.prm.scc)
+            for (int B = 0; B < nat; ++B) gd += g[(size_t)A * nat + B] * (qb[B] - q0v[B]);
+        cres[A] = c.prm.scc ? (float)(gd - vref[(size_t)A * c.nper]) : 0.0f;
+    }
+    h.c0_trace = c.n_electrons - qsum;
+    h.n_e = c.n_electrons;
+    for (int k = 0; k < 3; ++k) h.mu_ref[k] = mu[k];
+    h.eps_lvl[0] = h.eps_lvl[1] = 0.0f;
+    CK(cudaMemcpyAsync(c.gam2, g2.data(), sizeof(float2) * g2.size(), cudaMemcpyHostToDevice, c.stream));
+    CK(cudaMemcpyAsync(c.R2, r2.data(), sizeof(float2) * r2.size(), cudaMemcpyHostToDevice, c.stream));
+    CK(cudaMemcpyAsync(c.c_res, cres.data(), sizeof(float) * nat, cudaMemcpyHostToDevice, c.stream));
+    CK(cudaMemsetAsync(c.lv_count, 0, sizeof(int) * ((size_t)c.nct + 1), c.stream));
+    CK(cudaMemcpyAsync(c.sc, &h, sizeof h, cudaMemcpyHostToDevice, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
     return TDB_OK;
 }
 
@@ -940,6 +1017,8 @@ tdb_status tune_x(Ctx& c) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != TDB_OK) return st;
+    // the timing launches accumulated X maxima: the evaluation of the level had reset them
+    if (c.dyn) CK(cudaMemsetAsync(c.dyn->max_x, 0, sizeof(c.dyn->max_x), c.stream));
     if (best_bn) c.x_bn = best_bn;
     if (!make_x_maps(c, xbn(c), c.maps_x)) {
         set_err("cuTensorMapEncodeTiled failed");
@@ -948,20 +1027,74 @@ tdb_status tune_x(Ctx& c) {
     return TDB_OK;
 }
 
+// The four launches of a tensor-form step for rho_n in buffer cur (split of delta H, delta M,
+// X, update with the level evaluation), as argument structs: enqueue_step launches them for
+// one context, a grouped batch for many at once.
+struct TensorStep {
+    tc::SplitDhArgs split;
+    tc::GemmParams dm;
+    tc::GemmParams x;
+    int x_parts, x_bn;
+    UpdateDfArgs upd;
+};
+
+TensorStep tensor_step_args(Ctx& c, int cur, bool euler, int bn) {
+    const int N = c.N, Np = c.Np, b = piece_bf16(c), prv = cur ^ 1;
+    const bool h3 = head3(c);
+    TensorStep ts{};
+    ts.split = tc::split_dham_args(c.scheme, N, c.S_f, c.dv_f, c.s_dh, b, c.pc_dh, Np,
+                                   h3 ? c.dyn : nullptr, c.d_err);
+    // delta M = S^-1 delta H; the epilogue writes the pieces of [delta M | M_gs + delta M]
+    tc::GemmParams& g = ts.dm;
+    g.M = N;
+    g.N = N;
+    g.part[0] = {0, 0, N, 1, nullptr, 0, c.s_sinv, 0.f, nullptr, h3 ? &c.dyn->s_dh : nullptr, 0};
+    g.part[0].sb = c.s_dh;
+    g.idesc = tc::idesc_f16(b, 64);
+    g.bf16 = b;
+    g.Mgs = c.Mgs_f;
+    g.ld_mgs = N;
+    for (int q = 0; q < 3; ++q) g.out[q] = c.pc_am[q];
+    g.ld_out = 2 * Np;
+    g.col_m = Np;
+    g.s_m = c.s_m;
+    g.s_dm_dev = &c.dyn->s_dm;
+    g.err = c.d_err;
+    ts.x_bn = bn;
+    ts.x_parts = x_params(c, bn, ts.x);
+    // the update writes the pieces of rho_{n+1} - rho_ref itself (FP16X6: scaled from a
+    // bound on their size) and tracks their maximum
+    const int ns = x_split(c);
+    UpdateOperands ops = master_operands(c);
+    ops.cur = cur;
+    ops.base_slot = euler ? cur : prv;
+    ops.nre = 2 * ns;
+    ops.nim = ns;
+    for (int q = 0; q < 2 * ns; ++q) ops.xre[q] = c.xp[q];
+    for (int q = 0; q < ns; ++q) ops.xim[q] = c.xp[2 * ns + q];
+    const double factor = euler ? c.prm.dt : 2.0 * c.prm.dt;
+    ts.upd = update_df_args(c, euler ? c.ms[cur] : c.ms[prv], c.ms[prv], factor, c.sc, ops,
+                            level_args(c));
+    return ts;
+}
+
 tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* tm = nullptr) {
     const int prv = cur ^ 1;
     const double factor = euler ? c.prm.dt : 2.0 * c.prm.dt;
     const double* bre = euler ? c.rho_re[cur] : c.rho_re[prv];
     const double* bim = euler ? c.rho_im[cur] : c.rho_im[prv];
     int n = 0;
-    MARK("charges");
-    launch_charges(c, c.partial, c.q, c.dq, c.stream, nullptr, nullptr, head3(c) ? c.dyn : nullptr,
-                   cur, c.qbase);
-    ++n;
-    MARK("potential");
-    launch_potential(c, c.gamma, c.dq, c.d_R, c.sc, c.v_orb, c.v_atom, c.gdq, c.hist, c.v_ref,
-                     mixed(c) ? c.dv_f : nullptr, c.stream, head3(c) ? &c.dyn->max_dv : nullptr);
-    ++n;
+    if (!mixed(c)) {
+        // charges and SCC potential of rho_n (the reduced forms evaluate the new level in the
+        // update's tail, and the current one after a ground state, kick or state load)
+        MARK("charges");
+        launch_charges(c, c.partial, c.q, c.dq, c.stream);
+        ++n;
+        MARK("potential");
+        launch_potential(c, c.gamma, c.dq, c.d_R, c.sc, c.v_orb, c.v_atom, c.gdq, c.hist, c.v_ref,
+                         nullptr, c.stream);
+        ++n;
+    }
     if (sliced(c)) {
         const int N = c.N;
         MARK("slice_H");
@@ -993,49 +1126,20 @@ tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* t
                       c.partial, c.sc, c.stream);
         ++n;
     } else if (tensor(c)) {
-        const int N = c.N, Np = c.Np, b = piece_bf16(c);
-        const bool h3 = head3(c);
+        const TensorStep ts = tensor_step_args(c, cur, euler, xbn(c));
         MARK("split_dH");
-        tc::launch_split_dham(c.scheme, N, c.S_f, c.dv_f, c.s_dh, b, c.pc_dh, Np,
-                              h3 ? c.dyn : nullptr, c.stream, c.d_err);
+        tc::launch_split_dham(c.scheme, ts.split.N, ts.split.S, ts.split.dv, ts.split.scale,
+                              ts.split.bf16, ts.split.out, ts.split.ld_out, ts.split.dyn, c.stream,
+                              ts.split.err);
         ++n;
-        // delta M = S^-1 delta H; the epilogue writes the pieces of [delta M | M_gs + delta M]
-        tc::GemmParams g{};
-        g.M = N;
-        g.N = N;
-        g.part[0] = {0, 0, N, 1, nullptr, 0, c.s_sinv, 0.f, nullptr, h3 ? &c.dyn->s_dh : nullptr, 0};
-        g.part[0].sb = c.s_dh;
-        g.idesc = tc::idesc_f16(b, 64);
-        g.bf16 = b;
-        g.Mgs = c.Mgs_f;
-        g.ld_mgs = N;
-        for (int q = 0; q < 3; ++q) g.out[q] = c.pc_am[q];
-        g.ld_out = 2 * Np;
-        g.col_m = Np;
-        g.s_m = c.s_m;
-        g.s_dm_dev = &c.dyn->s_dm;
-        g.err = c.d_err;
         MARK("tc_gemm_dM");
-        CK(tc::launch(c.scheme, c.maps_dm, g, 1, c.stream, 64));
+        CK(tc::launch(c.scheme, c.maps_dm, ts.dm, 1, c.stream, 64));
         ++n;
-        tc::GemmParams x{};
-        const int ns = x_split(c);
-        const int nparts = x_params(c, xbn(c), x);
         MARK("tc_gemm_X");
-        CK(tc::launch(c.scheme, c.maps_x, x, nparts, c.stream, xbn(c)));
+        CK(tc::launch(c.scheme, c.maps_x, ts.x, ts.x_parts, c.stream, ts.x_bn));
         ++n;
-        // the update writes the pieces of rho_{n+1} - rho_ref itself (FP16X6: scaled from a
-        // bound on their size) and tracks their maximum
-        UpdateOperands ops = master_operands(c);
-        ops.cur = cur;
-        ops.base_slot = euler ? cur : prv;
-        ops.nre = 2 * ns;
-        ops.nim = ns;
-        for (int q = 0; q < 2 * ns; ++q) ops.xre[q] = c.xp[q];
-        for (int q = 0; q < ns; ++q) ops.xim[q] = c.xp[2 * ns + q];
         MARK("update");
-        launch_update_df(c, euler ? c.ms[cur] : c.ms[prv], c.ms[prv], factor, c.partial, c.sc, ops,
-                         c.stream);
+        launch_update_df(c, ts.upd.base, ts.upd.out, factor, c.sc, ts.upd.ops, ts.upd.lv, c.stream);
         ++n;
     } else {
         const int N = c.N;
@@ -1059,8 +1163,9 @@ tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* t
         ops.xre[0] = c.Xre_f;
         ops.xim[0] = c.Xim_f;
         ops.nre = ops.nim = 1;
-        launch_update_df(c, euler ? c.ms[cur] : c.ms[prv], c.ms[prv], factor, c.partial, c.sc, ops,
-                         c.stream);
+        ops.base_slot = euler ? cur : prv;
+        launch_update_df(c, euler ? c.ms[cur] : c.ms[prv], c.ms[prv], factor, c.sc, ops,
+                         level_args(c), c.stream);
         ++n;
     }
     MARK("end");
@@ -1463,15 +1568,16 @@ tdb_status tdb_ground_state(tdb_ctx* c, int* iters_out, double* residual_out) {
                            cudaMemcpyDeviceToDevice, c->stream));
         gemm_f64_ham(N, c->Sinv, c->H0, c->S, c->v_ref, c->M, c->stream);  // M_gs
         launch_f64_to_f32(NN, c->M, c->Mgs_f, c->stream);
-        if (c->prm.precision == TDB_FP32) launch_f64_to_f32(NN, c->rho_ref, c->rref_f, c->stream);
+        launch_f64_to_f32(NN, c->rho_ref, c->rref_f, c->stream);
         // Mulliken populations of rho_ref: the step adds those of rho - rho_ref
         launch_mulliken_partials(N, c->rho_ref, c->S, c->partial, c->stream);
         launch_charges(*c, c->partial, c->qbase, c->dq, c->stream);
         CKL();
+        TRY(setup_level_constants(*c));
         if (tensor(*c)) TRY(setup_tensor(*c));
     }
-    TRY(refresh_derived(*c));
     TRY(upload_clock(*c, 0, 0, 0.0));
+    TRY(refresh_derived(*c));
     CK(cudaStreamSynchronize(c->stream));
     return TDB_OK;
 }
@@ -1513,6 +1619,11 @@ tdb_status tdb_set_field(tdb_ctx* c, const tdb_field* f) {
         c->field_on = false;
     }
     TRY(upload_field(*c));
+    if (mixed(*c) && c->have_gs) {
+        // the reduced forms evaluated rho_n's potential with the old field: redo it
+        launch_level(*c, level_args(*c), c->cur, 0, c->stream);
+        CKL();
+    }
     CK(cudaStreamSynchronize(c->stream));
     return TDB_OK;
 }
@@ -1520,6 +1631,24 @@ tdb_status tdb_set_field(tdb_ctx* c, const tdb_field* f) {
 }  // extern "C"
 
 namespace {
+
+// FP64 Mulliken charges and SCC potential of the current rho_n into q, dq, gdq, v_atom,
+// v_orb (for observables).  The FP64 forms also record the dipole and field of rho_n; the
+// reduced forms keep the record their level evaluation made and change nothing the next
+// step reads.
+tdb_status fp64_charges_potential(Ctx& c) {
+    if (mixed(c)) {
+        launch_charges_df(c, reinterpret_cast<const float2*>(c.partial), c.q, c.dq, c.stream);
+        launch_potential(c, c.gamma, c.dq, c.d_R, c.sc, c.v_orb, c.v_atom, c.gdq, c.hist, c.v_ref,
+                         nullptr, c.stream, nullptr, 0);
+    } else {
+        launch_charges(c, c.partial, c.q, c.dq, c.stream);
+        launch_potential(c, c.gamma, c.dq, c.d_R, c.sc, c.v_orb, c.v_atom, c.gdq, c.hist, c.v_ref,
+                         nullptr, c.stream);
+    }
+    CKL();
+    return TDB_OK;
+}
 
 // State and stability checks before a context steps.
 tdb_status step_checks(tdb_ctx* c) {
@@ -1646,10 +1775,7 @@ tdb_status tdb_scc_shift(tdb_ctx* c, double* out, double* dq) {
         return TDB_ERR_UNSUPPORTED;
     }
     // charges and potential of the current rho_n, as tdb_observables takes them
-    launch_charges(*c, c->partial, c->q, c->dq, c->stream, nullptr, nullptr, nullptr, 0, c->qbase);
-    launch_potential(*c, c->gamma, c->dq, c->d_R, c->sc, c->v_orb, c->v_atom, c->gdq, c->hist,
-                     c->v_ref, nullptr, c->stream);
-    CKL();
+    TRY(fp64_charges_potential(*c));
     CK(cudaMemcpyAsync(out, c->gdq, sizeof(double) * c->nat, cudaMemcpyDeviceToHost, c->stream));
     if (dq) CK(cudaMemcpyAsync(dq, c->dq, sizeof(double) * c->nat, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -1832,10 +1958,7 @@ tdb_status tdb_observables(tdb_ctx* c, tdb_obs* o, double* charges, double* forc
     if (c->prm.move_nuclei) {
         TRY(md_forces(*c, cur, c->euler_next, 0, nullptr));
     } else {
-        launch_charges(*c, c->partial, c->q, c->dq, c->stream, nullptr, nullptr, nullptr, 0,
-                       c->qbase);
-        launch_potential(*c, c->gamma, c->dq, c->d_R, c->sc, c->v_orb, c->v_atom, c->gdq, c->hist,
-                         c->v_ref, nullptr, c->stream);
+        TRY(fp64_charges_potential(*c));
     }
     TRY(materialize(*c));
     launch_obs_reduce(c->N, c->rho_re[cur], c->rho_im[cur], c->H0, c->S, c->obs_blocks, kObsBlocks,
@@ -1884,20 +2007,22 @@ tdb_status tdb_dipole_history(tdb_ctx* c, double* out, long cap, long* n_out) {
         set_err("invalid history request");
         return TDB_ERR_ARG;
     }
-    const long long hc = c->prm.history_cap;
-    const long long avail = std::min<long long>(std::max<long long>(c->n, 0), hc);
+    const long long cap_h = c->prm.history_cap;
+    const long long hc = cap_h + 1;   // ring slots (one more than the history length)
+    const long long avail = std::min<long long>(std::max<long long>(c->n, 0), cap_h);
     const long long m = std::min<long long>(avail, cap);
-    std::vector<double> ring(3 * hc);
-    CK(cudaMemcpyAsync(ring.data(), c->hist, sizeof(double) * 3 * hc, cudaMemcpyDeviceToHost,
-                       c->stream));
+    // steps n-m .. n-1 (n counted from the last ground state / set_state): at most two
+    // contiguous runs of the ring
+    long long k0 = (c->n - m) % hc;
+    if (k0 < 0) k0 += hc;
+    const long long first = std::min(m, hc - k0);
+    if (first > 0)
+        CK(cudaMemcpyAsync(out, c->hist + 3 * k0, sizeof(double) * 3 * first, cudaMemcpyDeviceToHost,
+                           c->stream));
+    if (m > first)
+        CK(cudaMemcpyAsync(out + 3 * first, c->hist, sizeof(double) * 3 * (m - first),
+                           cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    // steps n-m .. n-1 (n counted from the last ground state / set_state)
-    for (long long j = 0; j < m; ++j) {
-        const long long k = c->n - m + j;
-        long long slot = k % hc;
-        if (slot < 0) slot += hc;
-        for (int d = 0; d < 3; ++d) out[3 * j + d] = ring[3 * slot + d];
-    }
     *n_out = (long)m;
     return TDB_OK;
 }
@@ -2050,12 +2175,14 @@ tdb_status tdb_set_state(tdb_ctx* c, const void* buf, size_t bytes) {
             CK(cudaStreamSynchronize(c->stream));
         }
         c->view_valid = true;
+        TRY(upload_clock(*c, hd.n, hd.n_base, hd.t_base));
         TRY(derived_from_master(*c, true));
         CK(cudaStreamSynchronize(c->stream));
     } else {
+        TRY(upload_clock(*c, hd.n, hd.n_base, hd.t_base));
         TRY(refresh_derived(*c));
+        CK(cudaStreamSynchronize(c->stream));
     }
-    TRY(upload_clock(*c, hd.n, hd.n_base, hd.t_base));
     return TDB_OK;
 }
 
@@ -2074,6 +2201,17 @@ tdb_status tdb_check(tdb_ctx* c, double tol_trace) {
 }
 
 long tdb_last_launch_count(const tdb_ctx* c) { return c ? c->last_launches : 0; }
+
+tdb_status tdb_wait_probe(tdb_ctx* c, long long polls) {
+    TRY(check_ctx(c, false, false));
+    if (polls < 1) {
+        set_err("tdb_wait_probe: polls must be >= 1");
+        return TDB_ERR_ARG;
+    }
+    tc::launch_wait_probe(polls, c->d_err, c->stream);
+    CKL();
+    return TDB_OK;
+}
 
 tdb_status tdb_step_profiled(tdb_ctx* c, double* ms, const char** names, int cap, int* n_out) {
     TRY(check_ctx(c, true, false));
@@ -2142,5 +2280,345 @@ const char* tdb_status_string(tdb_status s) {
 }
 
 const char* tdb_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Grouped batches: many independent contexts of one tensor-core form advanced together,
+// every phase of a step one launch over all of them (the probe runs of a pump-probe scan,
+// Sec. 3.2, are independent trajectories of uneven size).
+// ---------------------------------------------------------------------------
+
+struct tdb_batch {
+    std::vector<tdb_ctx*> ctxs;
+    std::vector<int> off;              // parity of each context against ctxs[0]
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    int scheme = 0, x_bn = 128, schedule = 0;
+    float tuned_ms = 0.f;
+    char* dmem = nullptr;              // argument arrays and work lists (one allocation)
+    tc::SplitDhArgs* d_split[2] = {};
+    tc::GroupedGemm* d_dm[2] = {};
+    tc::GroupedGemm* d_x[2] = {};
+    UpdateDfArgs* d_upd[2] = {};
+    int2 *w_split = nullptr, *w_dm = nullptr, *w_x = nullptr, *w_upd = nullptr;
+    int n_split = 0, n_dm = 0, n_x = 0, n_upd = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+// Work list of a grouped launch: every block of every problem, problem by problem in the
+// schedule's order (0: as given; 1: largest N first).
+std::vector<int2> work_list(const tdb_batch& b, const std::vector<int>& blocks, int schedule) {
+    std::vector<int> order(b.ctxs.size());
+    for (size_t p = 0; p < order.size(); ++p) order[p] = (int)p;
+    if (schedule == 1)
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int x, int y) { return b.ctxs[x]->N > b.ctxs[y]->N; });
+    std::vector<int2> w;
+    for (int p : order)
+        for (int k = 0; k < blocks[p]; ++k) w.push_back(make_int2(p, k));
+    return w;
+}
+
+tc::GroupedGemm grouped(const tc::Maps& m, const tc::GemmParams& p, int N, int bn, int nparts) {
+    tc::GroupedGemm g{};
+    g.maps = m;
+    g.p = p;
+    g.tiles_x = cdiv(N, bn);
+    g.tiles_y = cdiv(N, 128);
+    g.nparts = nparts;
+    return g;
+}
+
+// Argument arrays of both parities and the work lists for X tile width bn and a schedule,
+// uploaded into b.dmem (allocated here).
+tdb_status batch_layout(tdb_batch& b, int bn, int schedule) {
+    const int P = (int)b.ctxs.size();
+    std::vector<tc::SplitDhArgs> split[2];
+    std::vector<tc::GroupedGemm> dm[2], xg[2];
+    std::vector<UpdateDfArgs> upd[2];
+    std::vector<int> nb_split(P), nb_dm(P), nb_x(P), nb_upd(P);
+    for (int g = 0; g < 2; ++g)
+        for (int p = 0; p < P; ++p) {
+            Ctx& c = *b.ctxs[p];
+            const TensorStep ts = tensor_step_args(c, g ^ b.off[p], false, bn);
+            tc::Maps mx{};
+            if (!make_x_maps(c, bn, mx)) {
+                set_err("grouped batch: cuTensorMapEncodeTiled failed");
+                return TDB_ERR_CUDA;
+            }
+            split[g].push_back(ts.split);
+            dm[g].push_back(grouped(c.maps_dm, ts.dm, c.N, 64, 1));
+            xg[g].push_back(grouped(mx, ts.x, c.N, bn, ts.x_parts));
+            upd[g].push_back(ts.upd);
+            nb_split[p] = tc::split_dham_blocks(c.N);
+            nb_dm[p] = dm[g].back().tiles_x * dm[g].back().tiles_y;
+            nb_x[p] = xg[g].back().tiles_x * xg[g].back().tiles_y * ts.x_parts;
+            nb_upd[p] = c.nct * (c.nct + 1) / 2;
+        }
+    const std::vector<int2> ws = work_list(b, nb_split, schedule), wd = work_list(b, nb_dm, schedule),
+                            wx = work_list(b, nb_x, schedule), wu = work_list(b, nb_upd, schedule);
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t s_split = up(sizeof(tc::SplitDhArgs) * P), s_gg = up(sizeof(tc::GroupedGemm) * P),
+                 s_upd = up(sizeof(UpdateDfArgs) * P);
+    const size_t total = 2 * (s_split + 2 * s_gg + s_upd) +
+                         up(sizeof(int2) * ws.size()) + up(sizeof(int2) * wd.size()) +
+                         up(sizeof(int2) * wx.size()) + up(sizeof(int2) * wu.size());
+    if (b.dmem) {
+        CK(cudaStreamSynchronize(b.stream));
+        cudaFree(b.dmem);
+        b.dmem = nullptr;
+    }
+    if (cudaMalloc(&b.dmem, total) != cudaSuccess) {
+        cudaGetLastError();
+        set_err("grouped batch: device allocation of %zu bytes failed", total);
+        return TDB_ERR_NOMEM;
+    }
+    std::vector<char> h(total);
+    size_t o = 0;
+    auto put = [&](const void* src, size_t n, size_t span) {
+        std::memcpy(h.data() + o, src, n);
+        char* d = b.dmem + o;
+        o += span;
+        return d;
+    };
+    for (int g = 0; g < 2; ++g) {
+        b.d_split[g] = reinterpret_cast<tc::SplitDhArgs*>(put(split[g].data(), sizeof(tc::SplitDhArgs) * P, s_split));
+        b.d_dm[g] = reinterpret_cast<tc::GroupedGemm*>(put(dm[g].data(), sizeof(tc::GroupedGemm) * P, s_gg));
+        b.d_x[g] = reinterpret_cast<tc::GroupedGemm*>(put(xg[g].data(), sizeof(tc::GroupedGemm) * P, s_gg));
+        b.d_upd[g] = reinterpret_cast<UpdateDfArgs*>(put(upd[g].data(), sizeof(UpdateDfArgs) * P, s_upd));
+    }
+    b.w_split = reinterpret_cast<int2*>(put(ws.data(), sizeof(int2) * ws.size(), up(sizeof(int2) * ws.size())));
+    b.w_dm = reinterpret_cast<int2*>(put(wd.data(), sizeof(int2) * wd.size(), up(sizeof(int2) * wd.size())));
+    b.w_x = reinterpret_cast<int2*>(put(wx.data(), sizeof(int2) * wx.size(), up(sizeof(int2) * wx.size())));
+    b.w_upd = reinterpret_cast<int2*>(put(wu.data(), sizeof(int2) * wu.size(), up(sizeof(int2) * wu.size())));
+    b.n_split = (int)ws.size();
+    b.n_dm = (int)wd.size();
+    b.n_x = (int)wx.size();
+    b.n_upd = (int)wu.size();
+    CK(cudaMemcpyAsync(b.dmem, h.data(), total, cudaMemcpyHostToDevice, b.stream));
+    CK(cudaStreamSynchronize(b.stream));
+    b.x_bn = bn;
+    b.schedule = schedule;
+    return TDB_OK;
+}
+
+// One grouped step of global parity g: four launches over all contexts.
+tdb_status batch_enqueue(tdb_batch& b, int g) {
+    tc::launch_split_dham_grouped(b.scheme, b.d_split[g], b.w_split, b.n_split, b.stream);
+    CK(tc::launch_grouped(b.scheme, b.d_dm[g], b.w_dm, b.n_dm, b.stream, 64));
+    CK(tc::launch_grouped(b.scheme, b.d_x[g], b.w_x, b.n_x, b.stream, b.x_bn));
+    launch_update_df_grouped(b.d_upd[g], b.w_upd, b.n_upd, b.stream);
+    CKL();
+    return TDB_OK;
+}
+
+void batch_free_graphs(tdb_batch& b) {
+    for (auto& gr : b.graph)
+        if (gr) {
+            cudaGraphExecDestroy(gr);
+            gr = nullptr;
+        }
+}
+
+// Autotuner of the grouped X product: every (tile width, schedule) pair times three
+// launches on the contexts' current operands; the fastest is kept.  Every output element
+// keeps its K order whatever the width and order, so the choice changes the time only.
+// The timing launches accumulate X maxima, which are reset afterwards (as after tune_x).
+tdb_status batch_tune(tdb_batch& b) {
+    static const int cand[] = {128, 176, 256};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 0.f;
+    int best_bn = 0, best_s = 0;
+    tdb_status st = TDB_OK;
+    for (int bn : cand) {
+        bool valid = true;
+        for (tdb_ctx* c : b.ctxs) {
+            tc::Maps m{};
+            valid = valid && make_x_maps(*c, bn, m);   // width not encodable for this size
+        }
+        if (!valid) continue;
+        for (int sched = 0; sched < 2; ++sched) {
+            st = batch_layout(b, bn, sched);
+            if (st != TDB_OK) break;
+            cudaError_t e = tc::launch_grouped(b.scheme, b.d_x[0], b.w_x, b.n_x, b.stream, bn);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, b.stream);
+            for (int r = 0; r < 3 && e == cudaSuccess; ++r)
+                e = tc::launch_grouped(b.scheme, b.d_x[0], b.w_x, b.n_x, b.stream, bn);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, b.stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                set_err("grouped batch tuning: %s", cudaGetErrorString(e));
+                st = TDB_ERR_CUDA;
+                break;
+            }
+            if (!best_bn || ms < best) {
+                best = ms;
+                best_bn = bn;
+                best_s = sched;
+            }
+        }
+        if (st != TDB_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != TDB_OK) return st;
+    for (tdb_ctx* c : b.ctxs)
+        if (c->dyn) CK(cudaMemsetAsync(c->dyn->max_x, 0, sizeof(c->dyn->max_x), b.stream));
+    b.tuned_ms = best / 3.f;
+    return batch_layout(b, best_bn ? best_bn : 128, best_s);
+}
+
+tdb_status batch_capture(tdb_batch& b) {
+    batch_free_graphs(b);
+    for (int g = 0; g < 2; ++g) {
+        cudaGraph_t gr = nullptr;
+        CK(cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeThreadLocal));
+        const tdb_status st = batch_enqueue(b, g);
+        const cudaError_t e = cudaStreamEndCapture(b.stream, &gr);
+        if (st != TDB_OK || e != cudaSuccess) {
+            if (gr) cudaGraphDestroy(gr);
+            if (st == TDB_OK) set_err("grouped batch: graph capture failed: %s", cudaGetErrorString(e));
+            return st != TDB_OK ? st : TDB_ERR_CUDA;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&b.graph[g], gr, 0);
+        cudaGraphDestroy(gr);
+        if (ei != cudaSuccess) {
+            set_err("grouped batch: graph instantiate failed: %s", cudaGetErrorString(ei));
+            return TDB_ERR_CUDA;
+        }
+    }
+    return TDB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void tdb_batch_destroy(tdb_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_free_graphs(*b);
+    if (b->dmem) cudaFree(b->dmem);
+    if (b->ev) cudaEventDestroy(b->ev);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+tdb_status tdb_batch_create(tdb_ctx* const* ctxs, int count, tdb_batch** out) {
+    if (!ctxs || count < 1 || !out) {
+        set_err("tdb_batch_create: need count >= 1 contexts and an output pointer");
+        return TDB_ERR_ARG;
+    }
+    *out = nullptr;
+    for (int i = 0; i < count; ++i) {
+        TRY(step_checks(ctxs[i]));
+        tdb_ctx* c = ctxs[i];
+        if (!tensor(*c) || c->prm.move_nuclei) {
+            set_err("tdb_batch_create: context %d is not a frozen-nuclei tensor-core form", i);
+            return TDB_ERR_UNSUPPORTED;
+        }
+        if (c->prm.precision != ctxs[0]->prm.precision || c->prm.dt != ctxs[0]->prm.dt) {
+            set_err("tdb_batch_create: context %d differs in form or time step from context 0", i);
+            return TDB_ERR_ARG;
+        }
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == c) {
+                set_err("tdb_batch_create: context %d appears twice", i);
+                return TDB_ERR_ARG;
+            }
+    }
+    tdb_batch* b = new tdb_batch;
+    b->ctxs.assign(ctxs, ctxs + count);
+    b->scheme = ctxs[0]->scheme;
+    tdb_status st = TDB_OK;
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        set_err("tdb_batch_create: stream or event creation failed");
+        st = TDB_ERR_CUDA;
+    }
+    if (st == TDB_OK && tc::prepare() != cudaSuccess) {
+        cudaGetLastError();
+        set_err("tdb_batch_create: kernel attributes");
+        st = TDB_ERR_CUDA;
+    }
+    for (int i = 0; i < count && st == TDB_OK; ++i) {
+        if (cudaStreamSynchronize(ctxs[i]->stream) != cudaSuccess) st = TDB_ERR_CUDA;
+        b->off.push_back(ctxs[i]->cur ^ ctxs[0]->cur);
+    }
+    if (st == TDB_OK) st = batch_tune(*b);
+    if (st == TDB_OK) st = batch_capture(*b);
+    if (st != TDB_OK) {
+        tdb_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return TDB_OK;
+}
+
+tdb_status tdb_batch_tuning(const tdb_batch* b, int* x_bn, int* schedule, double* x_ms) {
+    if (!b) {
+        set_err("NULL batch");
+        return TDB_ERR_ARG;
+    }
+    if (x_bn) *x_bn = b->x_bn;
+    if (schedule) *schedule = b->schedule;
+    if (x_ms) *x_ms = b->tuned_ms;
+    return TDB_OK;
+}
+
+tdb_status tdb_batch_step(tdb_batch* b, long n) {
+    if (!b || n < 0) {
+        set_err("tdb_batch_step: NULL batch or n < 0");
+        return TDB_ERR_ARG;
+    }
+    const int P = (int)b->ctxs.size();
+    for (int i = 0; i < P; ++i) {
+        TRY(step_checks(b->ctxs[i]));
+        if ((b->ctxs[i]->cur ^ b->ctxs[0]->cur) != b->off[i]) {
+            set_err("tdb_batch_step: context %d was stepped on its own since the batch was made", i);
+            return TDB_ERR_STATE;
+        }
+    }
+    long k = 0;
+    // an Euler step (after a kick, ground state or state load) is taken context by context
+    bool euler = false;
+    for (tdb_ctx* c : b->ctxs) euler = euler || c->euler_next;
+    if (euler && n > 0) {
+        for (int i = 0; i < P; ++i) {
+            long l = 0;
+            TRY(step_one(b->ctxs[i], &l));
+            b->ctxs[i]->last_launches = l;
+        }
+        k = 1;
+    }
+    if (k >= n) return TDB_OK;
+    // the batch stream follows every context's stream, and they follow it
+    for (tdb_ctx* c : b->ctxs) {
+        CK(cudaEventRecord(b->ev, c->stream));
+        CK(cudaStreamWaitEvent(b->stream, b->ev, 0));
+    }
+    for (; k < n; ++k) {
+        CK(cudaGraphLaunch(b->graph[b->ctxs[0]->cur], b->stream));
+        for (tdb_ctx* c : b->ctxs) {
+            c->cur ^= 1;
+            c->n += 1;
+            c->view_valid = false;
+            c->last_launches = 4;
+        }
+    }
+    CK(cudaEventRecord(b->ev, b->stream));
+    for (tdb_ctx* c : b->ctxs) CK(cudaStreamWaitEvent(c->stream, b->ev, 0));
+    return TDB_OK;
+}
 
 }  // extern "C"

@@ -36,7 +36,37 @@ struct DevScalars {
     double mu[3];        // dipole of rho_n
     double e_coul;       // 1/2 dq . gamma dq of rho_n
     double e_ext;        // dq . (R E(t_n))
-    long long hist_cap;
+    long long hist_cap;  // slots of the dipole ring (the requested history length + 1)
+    // reduced-precision forms: Tr(rho S) of each master level and the renormalisation
+    // factor f - 1 = N_e / Tr(rho S) - 1 that the update applies to it as a base level
+    double trace_lvl[2];
+    float eps_lvl[2];
+    // ground-state constants of the per-level evaluation: N_e - sum_A q_A(rho_ref) and
+    // the dipole of rho_ref
+    double c0_trace;
+    double mu_ref[3];
+    double n_e;          // N_e
+};
+
+// Per-level evaluation of the reduced-precision forms: the Mulliken charges of a master
+// level and what follows from them (SCC potential, dipole, trace), evaluated in FP32-pair
+// arithmetic.  Row-tile stage (one block per 32-row tile): deviation charges of the tile's
+// atoms and their partial potentials; final stage (one block): sums over the tiles.
+struct LevelArgs {
+    int nat, nper, nct, scc;
+    const float2* partial;     // [N][nct] Mulliken row partials of the deviation (hi, lo)
+    const float2* gam2;        // [nat][nat] gamma as (hi, lo)
+    const float2* R2;          // [nat][3] positions as (hi, lo)
+    const float* c_res;        // [nat] (gamma dq(rho_ref))_A - v_ref_A: SCC residual of rho_ref
+    float2* pv;                // [nct][nat] partial potentials of the row tiles
+    float2* part;              // [nct][4] per tile: sum dq R_x, R_y, R_z, sum dq
+    float* dv_f;               // [N] v - v_ref per orbital (written by the final stage)
+    tc::DynScales* dyn;        // FP16X6 scales (may be null)
+    DevScalars* sc;
+    double* hist;
+    int* count;                // [nct + 1] tile and stage counters, zero between launches
+    float inv_ne;              // 1 / N_e
+    int has_scales;            // write s_dh, s_dm from max |dv| (FP16X6)
 };
 
 // Moving-nuclei scalars: the work integral of P = Re Tr[S^-1 H rho (D - D^T)].
@@ -96,6 +126,10 @@ struct Ctx {
     float *S_f = nullptr, *Sinv_f = nullptr, *Mgs_f = nullptr, *rref_f = nullptr;
     float *dM_f = nullptr, *M_f = nullptr;           // delta M, M = M_gs + delta M
     float *Xre_f = nullptr, *Xim_f = nullptr;
+    // per-level evaluation of the reduced forms (LevelArgs)
+    float2 *gam2 = nullptr, *R2 = nullptr, *lv_pv = nullptr, *lv_part = nullptr;
+    float* c_res = nullptr;
+    int* lv_count = nullptr;
 
     // reduced-precision master (two leapfrog levels) and the FP64 view's state
     MasterPtrs ms[2] = {};
@@ -171,10 +205,11 @@ void launch_charges(const Ctx& c, const double* partial, double* q, double* dq, 
                     double* reset0 = nullptr, double* reset1 = nullptr,
                     tc::DynScales* dyn = nullptr, int cur = 0, const double* qbase = nullptr);
 // max_dv (may be null): atomicMax of |v - v_ref| over atoms
+// record = 0: only v_orb, v_atom, gdq (no dipole, history or field record in sc)
 void launch_potential(const Ctx& c, const double* gamma, const double* dq, const double* R,
                       DevScalars* sc, double* v_orb, double* v_atom, double* gdq, double* hist,
                       const double* v_ref, float* dv_orb, cudaStream_t st,
-                      double* max_dv = nullptr);
+                      double* max_dv = nullptr, int record = 1);
 void launch_build_hamiltonian(int N, const double* H0, const double* S, const double* v_orb,
                               double* H, cudaStream_t st);
 // FP64 leapfrog / Euler update (zre, zim: NAC term of moving nuclei, or null)
@@ -216,13 +251,40 @@ void launch_power(const Ctx& c, const double* xre, const double* D, double* part
 void launch_vel_n(const Ctx& c, const double* F, int first, cudaStream_t st);
 void launch_vv(const Ctx& c, const double* F, cudaStream_t st);
 // reduced-precision master (kern_step.cu)
+// Arguments of one update of the reduced forms (one problem of a grouped launch).
+struct UpdateDfArgs {
+    int N, nct, out_slot, pad;
+    MasterPtrs base, out;
+    float fh, fl;
+    double factor;
+    const float* Sf;
+    const float* rgs;
+    DevScalars* sc;
+    UpdateOperands ops;
+    LevelArgs lv;
+};
+UpdateDfArgs update_df_args(const Ctx& c, const MasterPtrs& base, const MasterPtrs& out,
+                            double factor, DevScalars* sc, const UpdateOperands& ops,
+                            const LevelArgs& lv);
+// Updates of many contexts in one launch: block b runs tile pair work[b].y of args[work[b].x].
+void launch_update_df_grouped(const UpdateDfArgs* args, const int2* work, int nwork,
+                              cudaStream_t st);
+// The update of the reduced forms also renormalises its base level (f = N_e / Tr(rho S))
+// and, in its last blocks, evaluates the new level (LevelArgs) for the next step.
 void launch_update_df(const Ctx& c, const MasterPtrs& base, const MasterPtrs& out, double factor,
-                      double* partial, DevScalars* sc, const UpdateOperands& ops, cudaStream_t st);
+                      DevScalars* sc, const UpdateOperands& ops, const LevelArgs& lv,
+                      cudaStream_t st);
+// Evaluation of the current level outside a step (after a ground state, kick, field change or
+// state load), with the arithmetic of the update's tail; trace_only: only Tr(rho S) and the
+// renormalisation factor of level `slot` (partials of that level in lv.partial).
+void launch_level(const Ctx& c, const LevelArgs& lv, int slot, int trace_only, cudaStream_t st);
 void launch_view_to_master(const Ctx& c, const double* rre, const double* rim, const MasterPtrs& m,
                            cudaStream_t st);
 void launch_master_to_view(const Ctx& c, const MasterPtrs& m, double* rre, double* rim,
                            cudaStream_t st);
-void launch_master_partials(const Ctx& c, const MasterPtrs& m, double* partial, cudaStream_t st);
+void launch_master_partials(const Ctx& c, const MasterPtrs& m, float2* partial, cudaStream_t st);
+// FP64 populations q_A = qbase_A + sum of the (hi, lo) row partials, dq_A = q_A - q0_A
+void launch_charges_df(const Ctx& c, const float2* partial, double* q, double* dq, cudaStream_t st);
 void launch_master_absmax(const Ctx& c, const MasterPtrs& m, double* out, cudaStream_t st);
 void launch_master_pieces(const Ctx& c, const MasterPtrs& m, const UpdateOperands& ops,
                           const double* mx_exact, const float* dev_scale, cudaStream_t st);

@@ -70,16 +70,29 @@ cudaError_t prepare();
 cudaError_t launch(int scheme, const Maps& m, const GemmParams& p, int nparts, cudaStream_t st,
                    int bn = 128);
 
+// One product of a grouped launch: its tensor maps and parameters (in device memory) and its
+// tile grid (tiles_x column tiles x tiles_y row tiles x nparts parts).
+struct GroupedGemm {
+    Maps maps;
+    GemmParams p;
+    int tiles_x, tiles_y, nparts, pad;
+};
+// Many products in one launch of 128 x bn tiles: block b computes tile work[b].y (parts
+// outermost, then rows, then columns) of product work[b].x.  Every product must satisfy the
+// conditions of launch() for bn; g and work are device arrays.
+cudaError_t launch_grouped(int scheme, const GroupedGemm* g, const int2* work, int nwork,
+                           cudaStream_t st, int bn);
+
 // Pieces of sign * scale * (in - sub) (sub may be null) for a rows x cols block.
 // scale_dev (if set) overrides scale.
 void launch_split(int scheme, int rows, int cols, const double* in, int ld_in, float scale,
                   int sign, int bf16, uint16_t* const* pieces, int ld_out, cudaStream_t st,
                   const double* sub = nullptr, const float* scale_dev = nullptr, int* err = nullptr);
 // Pieces of delta H_kj = 1/2 S_kj (dv_k + dv_j) from FP32 S and dv = v - v_ref.  With dyn
-// (kHead3), the scales come from the bound max|dv| (dyn->max_dv): s_dh = pscale(max|dv|)
-// and s_dm = pscale(||S^-1||_inf max|dv|) are stored in dyn->s_dh / dyn->s_dm.
+// (kHead3) the scale is dyn->s_dh = pscale(max|dv|), which the evaluation of the level
+// writes together with dv and s_dm = pscale(||S^-1||_inf max|dv|).
 struct DynScales {
-    double max_dv;        // max |v - v_ref| of this step (atomicMax on the bit pattern)
+    double max_dv;        // max |v - v_ref| of this step
     double max_drho[3];   // max |rho - rho_ref| per density buffer; [2]: the one being written
     double sinv_norm;     // ||S^-1||_inf
     double max_x[kMaxParts];   // max |X| of each product output of this step
@@ -89,6 +102,25 @@ struct DynScales {
 void launch_split_dham(int scheme, int N, const float* S, const float* dv, float scale, int bf16,
                        uint16_t* const* pieces, int ld_out, DynScales* dyn, cudaStream_t st,
                        int* err);
+// The same for many contexts in one launch: block b runs block work[b].y (of
+// split_dham_blocks(N) per problem) of args[work[b].x].
+struct SplitDhArgs {
+    int N, bf16, ld_out, pad;
+    const float* S;
+    const float* dv;
+    float scale;
+    uint16_t* out[3];
+    DynScales* dyn;
+    int* err;
+};
+SplitDhArgs split_dham_args(int scheme, int N, const float* S, const float* dv, float scale,
+                            int bf16, uint16_t* const* pieces, int ld_out, DynScales* dyn, int* err);
+int split_dham_blocks(int N);
+void launch_split_dham_grouped(int scheme, const SplitDhArgs* args, const int2* work, int nwork,
+                               cudaStream_t st);
+
+// One kernel whose bounded mbarrier wait (at most polls polls) runs out and sets *err = 5.
+void launch_wait_probe(long long polls, int* err, cudaStream_t st);
 
 // Power-of-two scale mapping a magnitude bound m into (63.5, 127]: the integer heads then
 // use their full 7-bit range and up to 1040 head products (<= 127^2 each) sum exactly in FP32.

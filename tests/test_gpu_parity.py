@@ -220,7 +220,7 @@ def test_reduced_precision_forms_match_oracle(B, n_atoms, form, tol_mu, tol_rho)
     err = np.max(np.abs(mu - tr.dipole))
     assert err < tol_mu, err
     assert np.max(np.abs(g["rho"] - tr.rho)) < tol_rho
-    assert abs(g["obs"]["trace_re"] - sysm.n_electrons) / sysm.n_electrons < 1e-8
+    assert abs(g["obs"]["trace_re"] - sysm.n_electrons) / sysm.n_electrons < 1e-10
     assert g["obs"]["herm_err"] == 0.0
 
 
@@ -243,7 +243,7 @@ def test_reduced_forms_with_176_wide_x_tiles_match_oracle(B, form, tol_mu, tol_r
     assert err < tol_mu, err
     assert np.max(np.abs(g["rho"] - tr.rho)) < tol_rho
     assert np.max(np.abs(g["obs"]["charges"] - tr.charges[-1])) < tol_rho
-    assert abs(g["obs"]["trace_re"] - sysm.n_electrons) / sysm.n_electrons < 1e-8
+    assert abs(g["obs"]["trace_re"] - sysm.n_electrons) / sysm.n_electrons < 1e-10
     assert g["obs"]["herm_err"] == 0.0
 
 
@@ -278,7 +278,25 @@ def test_reduced_forms_at_n2048_track_the_fp64_form(B, form, tol):
     assert err < tol, err
     assert np.max(np.abs(g["rho"] - ref["rho"])) < 10 * tol
     assert g["obs"]["herm_err"] == 0.0
-    assert abs(g["obs"]["trace_re"] - sysm.n_electrons) / sysm.n_electrons < 1e-8
+    assert abs(g["obs"]["trace_re"] - sysm.n_electrons) / sysm.n_electrons < 1e-10
+
+
+@pytest.mark.parametrize("form", ["fp32", "bf16x3", "fp16x3", "fp16x6", "fp64s"])
+def test_every_form_conserves_the_electron_number_over_a_long_run(B, form):
+    # Sec. 2.3: with S frozen the leapfrog conserves Tr(rho S) = N_e exactly; the reduced
+    # products do not, so the reduced forms renormalise the base level of every update to
+    # N_e.  130 atoms (N = 520), 2400 steps, Tr(rho S) (FP64 view) sampled every 200 steps.
+    sysm = I.small_flake(130, seed=8)
+    run = I.Run(dt=0.2, n_steps=0, scc=True, kick=1e-3, kT=I.SCC_KT)
+    worst = 0.0
+    with B.Propagator(sysm, run, form) as p:
+        p.setup()
+        for _ in range(12):
+            p.step(200)
+            o = p.observables(charges=False)
+            worst = max(worst, abs(o["trace_re"] - sysm.n_electrons) / sysm.n_electrons)
+            assert o["herm_err"] == 0.0
+    assert worst < 1e-10, worst
 
 
 def test_exact_head_form_beats_the_hi_lo_forms(B):
@@ -401,3 +419,30 @@ def test_ehrenfest_checkpoint_resume_is_bitwise(B):
         b.step(40)
         assert np.array_equal(B.tdb_get_rho(a.ctx), B.tdb_get_rho(b.ctx))
         assert B.tdb_get_state(a.ctx) == B.tdb_get_state(b.ctx)
+
+
+def test_a_bounded_device_wait_that_runs_out_makes_the_context_sticky(B):
+    # failure detection without a GPU fault: a kernel waits on an mbarrier that nothing
+    # arrives on, gives up after a bounded number of polls and records a time-out; the host
+    # reads TDB_ERR_TIMEOUT at its next synchronising call, after which only observables,
+    # state reads and destroy are allowed -- and the GPU stays usable
+    sysm = I.small_flake(10, seed=3)
+    run = I.Run(dt=0.2, n_steps=0, scc=True, kick=1e-3, kT=I.SCC_KT)
+    with B.Propagator(sysm, run, "fp16x6") as p:
+        p.setup()
+        p.step(5)
+        B.tdb_wait_probe(p.ctx, 1000)
+        with pytest.raises(B.TdbError) as e:
+            p.observables()
+        assert e.value.status == 8
+        with pytest.raises(B.TdbError) as e:
+            p.step(1)
+        assert e.value.status == 2
+        o = p.observables()            # allowed on a sticky context
+        assert o["step"] == 5
+        assert len(B.tdb_get_state(p.ctx)) > 0
+    # a fresh context on the same device works normally
+    with B.Propagator(sysm, run, "fp16x6") as p:
+        p.setup()
+        p.step(5)
+        assert p.observables()["step"] == 5

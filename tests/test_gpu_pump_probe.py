@@ -84,3 +84,56 @@ def test_branched_probe_run_matches_oracle(B):
     mu = np.vstack([hist, obs["dipole"][None, :]])
     assert np.max(np.abs(mu - tr2.dipole)) < 1e-10
     assert obs["step"] == k + m and abs(obs["t"] - (k + m) * run.dt) < 1e-10
+
+
+def test_grouped_batch_equals_separate_stepping(B):
+    # four FP16X6 contexts of uneven size (N = 40, 132, 256, 520), two of them one leapfrog
+    # parity off the others, all kicked: a grouped batch (one launch per phase over all of
+    # them) and the same contexts stepped one by one end in the same state bit for bit
+    run = I.Run(dt=0.2, n_steps=0, scc=True, kick=0.0, kT=I.SCC_KT)
+    a, b = [], []
+    try:
+        for (nat, seed), extra in zip([(10, 1), (33, 2), (64, 3), (130, 4)], [0, 1, 0, 1]):
+            s = I.small_flake(nat, seed=seed)
+            for lst in (a, b):
+                p = B.Propagator(s, run, "fp16x6")
+                p.setup()
+                p.step(3 + extra)
+                B.tdb_kick(p.ctx, 1e-3, np.array([1.0, 0.0, 0.0]))
+                lst.append(p)
+        with B.Batch([p.ctx for p in b]) as bt:
+            bt.step(1)                         # the Euler step, context by context
+            bt.step(40)
+            tn = bt.tuning()
+            with pytest.raises(B.TdbError) as e:   # a context stepped on its own
+                B.tdb_step(b[0].ctx, 1)
+                bt.step(1)
+            assert e.value.status == 2
+        a[0].step(1)
+        for p in a:
+            p.step(41)
+        for pa, pb in zip(a, b):
+            assert B.tdb_get_state(pa.ctx) == B.tdb_get_state(pb.ctx)
+            assert np.array_equal(B.tdb_dipole_history(pa.ctx, 41), B.tdb_dipole_history(pb.ctx, 41))
+        assert tn["x_bn"] in (128, 176, 256) and tn["schedule"] in (0, 1) and tn["x_ms"] > 0
+    finally:
+        for p in a + b:
+            p.close()
+
+
+def test_grouped_batch_rejects_mixed_forms(B):
+    run = I.Run(dt=0.2, n_steps=0, scc=True, kick=1e-3, kT=I.SCC_KT)
+    s = I.small_flake(10, seed=1)
+    with B.Propagator(s, run, "fp16x6") as p, B.Propagator(s, run, "fp64") as q, \
+            B.Propagator(s, run, "bf16x3") as r:
+        for x in (p, q, r):
+            x.setup()
+        with pytest.raises(B.TdbError) as e:
+            B.Batch([p.ctx, q.ctx])
+        assert e.value.status == 10
+        with pytest.raises(B.TdbError) as e:
+            B.Batch([p.ctx, r.ctx])
+        assert e.value.status == 1
+        with pytest.raises(B.TdbError) as e:
+            B.Batch([p.ctx, p.ctx])
+        assert e.value.status == 1
