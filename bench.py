@@ -754,332 +754,6 @@ def accuracy_c3(B, total, every=20, nudge=1e-12):
                     "approximately by the leapfrog (its drift is reported, not bounded)"}
 
 
-def c4_fractions(c4: dict, peaks: dict) -> None:
-    """HBM and tensor fractions of the batched scan: the mean probe step's algorithmic bytes
-    (FP16X6 step bytes at its N) and method flops (6 N^3) times the probe steps per second."""
-    if not c4 or c4.get("precision") != "fp16x6" or "sizes" not in c4:
-        return
-    sizes = np.asarray(c4["sizes"], dtype=np.float64)
-    rate = c4["trajectory_steps_per_s_batched"]
-    b = float(np.mean([step_bytes("fp16x6", int(n)) for n in sizes]))
-    f = float(np.mean([STEP_FLOPS(int(n)) for n in sizes]))
-    c4["roofline"] = {"bytes_per_traj_step": b, "flops_per_traj_step": f,
-                      "achieved_gbs": b * rate / 1e9, "hbm_frac": b * rate / 1e9 / peaks["hbm_gbs"],
-                      "achieved_tflops": f * rate / 1e12,
-                      "tensor_frac": f * rate / 1e12 / peaks["bf16_tflops"],
-                      "note": "bytes: FP16X6 step arrays read or written once; flops: the method's "
-                              "M and X products"}
-
-
-def c5_runs(B, torch, k=16, L=8, hidden=64, n_train=4, train_steps=1200, windows=12,
-            epochs=20, form="fp64s"):
-    """The learned form on the 256-atom flake (N = 1024): shift and charge records of
-    n_train plain runs (kicks of seeded strength 1e-3..3e-3 a.u. along seeded directions)
-    train the per-atom network (L shift and L charge samples at window ends, two hidden
-    layers of `hidden`, BF16 weights) on the GPU; a held-out run (the flake's own kick, 1e-3 a.u. along x)
-    then advances in windows of k steps with the network's shift, with the shift frozen
-    at the window's start, and in plain steps.  Reported: data and training time, time
-    per window against k plain steps, and the charge and dipole errors at window ends
-    against the plain run."""
-    import dataclasses
-    from paper_1912_03174_gb300 import inputs as I, learned as Lrn
-    sysm, run = I.flake_c2()
-    rng = np.random.default_rng(1005)
-    Xs, Ys = [], []
-    t0 = time.perf_counter()
-    for _ in range(n_train):
-        d = rng.normal(size=3)
-        r = dataclasses.replace(run, kick=float(rng.uniform(1e-3, 3e-3)), kick_dir=d / np.linalg.norm(d))
-        with B.Propagator(sysm, r, form) as p:
-            p.setup()
-            p.step(1)
-            X, Y = Lrn.training_set(Lrn.record(p.ctx, train_steps), k, L)
-            Xs.append(X)
-            Ys.append(Y)
-    t_data = time.perf_counter() - t0
-    X, Y = np.concatenate(Xs), np.concatenate(Ys)
-    model = Lrn.ShiftModel(k=k, L=L, hidden=hidden, seed=5)
-    t0 = time.perf_counter()
-    model.fit(X, Y, epochs=epochs, batch=512, lr=2e-3)
-    t_train = time.perf_counter() - t0
-
-    def start():
-        p = B.Propagator(sysm, run, form)
-        p.setup()
-        p.step(1)
-        return p
-
-    out = {}
-    # plain reference: warm-up windows, then `windows` windows of k plain steps
-    p = start()
-    try:
-        p.step(L * k)
-        q_ref, mu_ref, t_plain = [], [], []
-        for _ in range(windows):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            torch.cuda.nvtx.range_push("c5_plain")
-            B.tdb_step(p.ctx, k)
-            torch.cuda.synchronize()
-            torch.cuda.nvtx.range_pop()
-            t_plain.append(time.perf_counter() - t0)
-            o = p.observables()
-            q_ref.append(o["charges"])
-            mu_ref.append(o["dipole"])
-    finally:
-        p.close()
-    q_ref, mu_ref = np.array(q_ref), np.array(mu_ref)
-    for mode in ("frozen", "net"):
-        p = start()
-        try:
-            lp = Lrn.LearnedPropagator(p.ctx, model, mode=mode)
-            lp.warm_up()
-            q, mu, t_win = [], [], []
-            for _ in range(windows):
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                torch.cuda.nvtx.range_push(f"c5_window_{mode}")
-                lp.run(1)
-                torch.cuda.synchronize()
-                torch.cuda.nvtx.range_pop()
-                t_win.append(time.perf_counter() - t0)
-                o = p.observables()
-                q.append(o["charges"])
-                mu.append(o["dipole"])
-        finally:
-            p.close()
-        eq = np.max(np.abs(np.array(q) - q_ref), axis=1)
-        emu = np.max(np.abs(np.array(mu) - mu_ref), axis=1)
-        out[mode] = {"max_charge_err": float(eq.max()), "final_charge_err": float(eq[-1]),
-                     "max_dipole_err_au": float(emu.max()), "final_dipole_err_au": float(emu[-1]),
-                     "ms_per_window": 1000.0 * float(np.median(t_win[1:] or t_win))}
-    # the referee at the stated dipole bound, every fourth window
-    p = start()
-    try:
-        lp = Lrn.LearnedPropagator(p.ctx, model, mode="net", referee_every=4, bound=float("inf"),
-                                   dipole_bound=1e-5)
-        lp.warm_up()
-        lp.run(windows)
-        st = lp.stats
-        referee = {"dipole_bound_au": 1e-5, "referee_every": 4, "windows_run": st.windows,
-                 "refereed": st.refereed, "taken_over": st.taken_over,
-                 "plain_steps_after_warm_up": st.plain_steps - L * k,
-                 "referee_dipole_err_au": st.referee_dipole_err, "referee_charge_err": st.referee_err}
-    finally:
-        p.close()
-    model.close()
-    ms_plain = 1000.0 * float(np.median(t_plain))
-    ms_win = out["net"]["ms_per_window"]
-    return {"workload": f"learned form on the SCC flake, 256 atoms (N=1024), form {form}: "
-                        f"{n_train} training runs x {train_steps} steps, held-out kick 1e-3 a.u. along x, "
-                        f"windows of k={k} steps (dt=0.2), {windows} windows after {L} plain warm-up windows",
-            "training": {"samples": int(len(Y)), "epochs": epochs, "data_s": t_data, "train_s": t_train,
-                         "samples_per_s": epochs * len(Y) / t_train,
-                         "final_loss_scaled": float(model.losses[-1])},
-            "ms_k_plain_steps": ms_plain, "ms_per_window": ms_win,
-            "effective_steps_per_s_window": 1000.0 * k / ms_win,
-            "steps_per_s_plain": 1000.0 * k / ms_plain,
-            "window_vs_plain_speedup": ms_plain / ms_win,
-            "errors_vs_plain": out,
-            "referee": referee,
-            "gain_charge_err_frozen_over_net": out["frozen"]["max_charge_err"] / max(out["net"]["max_charge_err"], 1e-300),
-            "timing": "host clock between device synchronisations (window: shift readback, "
-                      "network inference, eigensolve and products)"}
-
-
-def c5_k_sweep(B, ks=(2, 4, 8, 16, 32, 64), forms=("fp64s", "fp64"), warm=129):
-    """The learned form's floor and cost against the window length k on the 256-atom flake
-    (N = 1024): from one state (warm plain steps after the kick), a clone takes k plain steps
-    (timed), another records the SCC shift at each of those steps, and a third takes one
-    closed-form window with the exact window-mean shift (the best any predictor can give,
-    timed) and one with the shift frozen at the window's start.  Errors are the dipole and
-    charge differences to the plain steps at the window's end.  break_even_k: the window
-    length at which one window costs as much as k plain steps."""
-    from paper_1912_03174_gb300 import inputs as I, learned as Lrn
-    sysm, run = I.flake_c2()
-    out = {}
-    for form in forms:
-        rows = []
-        with B.Propagator(sysm, run, form) as p:
-            p.setup()
-            p.step(warm)
-            for k in ks:
-                c = B.tdb_clone(p.ctx)
-                try:
-                    B.tdb_step(c, 1)                    # graph capture outside the timing
-                    B.tdb_set_state(c, B.tdb_get_state(p.ctx))
-                    t0 = time.perf_counter()
-                    B.tdb_step(c, k)
-                    o_plain = B.tdb_observables(c)
-                    t_plain = time.perf_counter() - t0
-                finally:
-                    B.tdb_destroy(c)
-                a = B.tdb_clone(p.ctx)
-                try:
-                    vs = []
-                    for _ in range(k):
-                        vs.append(Lrn.sample(a)[:, 0])
-                        B.tdb_step(a, 1)
-                finally:
-                    B.tdb_destroy(a)
-                res = {}
-                for mode, vbar in (("exact_mean_shift", np.mean(vs, axis=0)), ("frozen_shift", vs[0])):
-                    b = B.tdb_clone(p.ctx)
-                    try:
-                        t0 = time.perf_counter()
-                        B.tdb_step_window(b, vbar, k)
-                        o = B.tdb_observables(b)
-                        t_win = time.perf_counter() - t0
-                    finally:
-                        B.tdb_destroy(b)
-                    res[mode] = {"dipole_err_au": float(np.max(np.abs(np.asarray(o["dipole"])
-                                                                       - np.asarray(o_plain["dipole"])))),
-                                 "charge_err": float(np.max(np.abs(o["charges"] - o_plain["charges"]))),
-                                 "window_ms": 1000.0 * t_win}
-                rows.append({"k": k, "plain_ms": 1000.0 * t_plain, **res})
-        per_step = float(np.median([r["plain_ms"] / r["k"] for r in rows]))
-        win = float(np.median([r["exact_mean_shift"]["window_ms"] for r in rows]))
-        out[form] = {"rows": rows, "plain_ms_per_step": per_step, "window_ms": win,
-                     "break_even_k": win / per_step}
-    return {"workload": "SCC flake, 256 atoms (N=1024), kick 1e-3 a.u. along x, windows from the "
-                        f"state {warm} steps after the kick", "forms": out,
-            "timing": "host clock, each call synchronised (plain steps include the observables "
-                      "read-back, as the windows do)"}
-
-
-def shard_throughput(units: float, seconds: float, dist=None):
-    """Sharded independent work (each rank its own share, no data-path collective):
-    the whole job's units over the slowest rank's time, both reduced over ranks on the
-    host (gloo).  Returns (total units, max seconds, units per second)."""
-    if dist is not None:
-        import torch
-        u = torch.tensor([float(units)], dtype=torch.float64)
-        t = torch.tensor([float(seconds)], dtype=torch.float64)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        units, seconds = float(u.item()), float(t.item())
-    return units, seconds, (units / seconds if seconds > 0 else 0.0)
-
-
-def c4_sharded(B, torch, dist, rank, world, n_traj, post_steps, form="fp16x6"):
-    """The pump-probe scan of c4_runs over world ranks: the probe runs shared out by
-    longest-processing-time on N^3 x steps, each rank branching and stepping its own
-    share (scan.run_shard), timed between barriers; value = all probe steps over the
-    slowest rank's time."""
-    from paper_1912_03174_gb300 import inputs as I, scan
-    systems, run, which, tau = I.pump_probe_c4(n_traj=n_traj)
-    parts = scan.lpt_partition(scan.probe_costs(systems, which, post_steps), world)
-
-    def sync():
-        torch.cuda.synchronize()
-        dist.barrier()
-
-    n, pump_steps, t, _ = scan.run_shard(B, systems, run, which, tau, parts[rank], post_steps,
-                                         form, sync=sync)
-    units, t_max, rate = shard_throughput(n * post_steps, t, dist)
-    return {"workload": f"pump-probe scan: {len(which)} probe runs over flakes of "
-                        f"{'/'.join(str(s.n_atoms) for s in systems)} atoms (N = 128..1024), "
-                        f"shared out over {world} ranks by longest-processing-time on N^3 x steps, "
-                        f"{post_steps} post-kick steps timed per probe",
-            "precision": form, "probes": int(units // post_steps), "probes_this_rank": n,
-            "pump_steps_untimed_this_rank": int(pump_steps),
-            "trajectory_steps_per_s_batched": rate, "seconds_slowest_rank": t_max,
-            "scaling": "strong",
-            "timing": "host clock between barriers after device synchronisation"}
-
-
-def e2e_run(B, sysm, run, precision, steps, warmup):
-    """End to end through the public API, one step at a time: the field of the step is
-    set from the host (H2D), the step runs, and its result, the dipole mu(t_n) of the
-    history ring, is read back (D2H, which synchronises)."""
-    p = B.Propagator(sysm, run, precision)
-    try:
-        p.setup()
-        from paper_1912_03174_gb300 import inputs as I
-        fld = B.make_field(I.Field(E0=0.0, omega=0.0))
-        for _ in range(warmup):
-            B.tdb_set_field(p.ctx, fld)
-            p.step(1)
-            B.tdb_dipole_history(p.ctx, 1)
-        t0 = time.perf_counter()
-        for _ in range(steps):
-            B.tdb_set_field(p.ctx, fld)
-            p.step(1)
-            B.tdb_dipole_history(p.ctx, 1)
-        dt = time.perf_counter() - t0
-    finally:
-        p.close()
-    h2d = 88                                     # field parameters
-    d2h = 3 * 8                                  # the step's dipole
-    return {"value": steps / dt, "unit": "steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "per_step": "set field (H2D), one step, read its dipole back (D2H, synchronising)"}
-
-
-def accuracy_c2(B, sysm, run, forms, total, sample_every=1000):
-    """Run-length accuracy on the N = 1024 flake: every form runs `total` steps from the same
-    kicked ground state; the dipole of every step is compared with the FP64 form's, and
-    Tr(rho S) is sampled every `sample_every` steps (relative deviation from N_e)."""
-    hist, drift, secs = {}, {}, {}
-    for f in forms:
-        t0 = time.perf_counter()
-        with B.Propagator(sysm, run, f, history_cap=total + 8) as p:
-            p.setup()
-            worst = 0.0
-            done = 0
-            while done < total:
-                k = min(sample_every, total - done)
-                p.step(k)
-                done += k
-                o = p.observables(charges=False)
-                worst = max(worst, abs(o["trace_re"] - sysm.n_electrons) / sysm.n_electrons)
-            hist[f] = B.tdb_dipole_history(p.ctx, total)
-            drift[f] = worst
-        secs[f] = time.perf_counter() - t0
-    out = {"workload": f"{WORKLOAD}, {total} steps per form", "steps": total, "forms": {}}
-    for f in forms:
-        e = float(np.max(np.abs(hist[f] - hist["fp64"]))) if "fp64" in hist else None
-        out["forms"][f] = {"max_dipole_err_vs_fp64_au": e, "max_trace_rel_drift": drift[f],
-                           "within_1e-6_au": (e is not None and e <= 1e-6), "wall_s": secs[f]}
-    return out
-
-
-def accuracy_c3(B, total, every=20):
-    """Run-length accuracy of the Ehrenfest cluster (512 atoms, N = 2048): the FP64-sliced
-    form against the FP64 form over `total` steps, both advanced in lockstep; every `every`
-    steps the dipole, the forces and Tr(rho S) of both are compared."""
-    from paper_1912_03174_gb300 import inputs as I
-    sysm, run = I.cluster_c3()
-    t0 = time.perf_counter()
-    a = B.Propagator(sysm, run, "fp64", history_cap=total + 8)
-    b = B.Propagator(sysm, run, "fp64s", history_cap=total + 8)
-    try:
-        a.setup()
-        b.setup()
-        ef, ed, tr = 0.0, 0.0, 0.0
-        done = 0
-        while done < total:
-            k = min(every, total - done)
-            a.step(k)
-            b.step(k)
-            done += k
-            oa, ob = a.observables(forces=True), b.observables(forces=True)
-            ef = max(ef, float(np.max(np.abs(oa["forces"] - ob["forces"]))))
-            ed = max(ed, float(np.max(np.abs(np.asarray(oa["dipole"]) - np.asarray(ob["dipole"])))))
-            tr = max(tr, abs(ob["trace_re"] - sysm.n_electrons) / sysm.n_electrons)
-        ha, hb = B.tdb_dipole_history(a.ctx, total), B.tdb_dipole_history(b.ctx, total)
-        ed = max(ed, float(np.max(np.abs(ha - hb))))
-    finally:
-        a.close()
-        b.close()
-    return {"workload": "Ehrenfest cluster, 512 atoms (N=2048), 300 K, Gaussian laser E0=0.01 "
-                        f"omega=0.1, dt=0.2 a.u., {total} steps", "steps": total,
-            "fp64s_vs_fp64": {"max_dipole_err_au": ed, "max_force_err_ha_bohr": ef,
-                              "max_trace_rel_drift": tr, "force_compared_every": every},
-            "within_bounds": ed <= 1e-6 and ef <= 1e-6, "wall_s": time.perf_counter() - t0,
-            "note": "with moving nuclei S changes every step, so Tr(rho S) is conserved only "
-                    "approximately by the leapfrog (its drift is reported, not bounded)"}
-
-
 def cpu_baseline(sysm, run, n_steps, warmup=1, budget_s=None):
     """The CPU oracle as it stands, timed on this host's cores: ground state untimed,
     `warmup` untimed oracle steps, then n_steps timed ones (fewer when budget_s is set

@@ -1023,23 +1023,31 @@ __device__ void level_final(const LevelArgs& a, int slot, long long n_lvl, bool 
     for (int i = tid; i <= a.nct; i += 256) a.count[i] = 0;
 }
 
+// Counter increment with acquire-release semantics at GPU scope: after a block barrier it
+// publishes what the block wrote (release is cumulative over the barrier) and, for the block
+// that completes a count, makes what the others published visible (acquire; the barrier
+// that follows extends it to the block).  One such atomic per block replaces per-thread
+// fences, which serialise across the GPU.
+__device__ __forceinline__ int atom_add_acq_rel(int* p, int v) {
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v)
+                 : "memory");
+    return old;
+}
+
 // After a block has written its row partials: count it towards the row tiles it covered
 // (tile_target arrivals complete a tile); the block completing a tile runs the tile's
-// stage, and the block completing the last tile runs the final stage.  Every writer
-// fences before the counting atomics, and the stages read what other blocks wrote
-// through L2 (ld.global.cg).
+// stage, and the block completing the last tile runs the final stage.  The stages read what
+// other blocks wrote through L2 (ld.global.cg).
 __device__ void level_arrive(const LevelArgs& a, int t0, int t1, int tile_target, int slot,
                              long long n_lvl, bool trace_only, bool step_end) {
     __shared__ int done[2];
     __shared__ int last;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    // the writers of what the tail reads (row partials: first warp; maxima: first lanes)
-    if (threadIdx.y == 0 || threadIdx.x == 0) __threadfence();
     __syncthreads();
     if (tid == 0) {
-        done[0] = atomicAdd(&a.count[t0], 1) == tile_target - 1;
-        done[1] = t1 != t0 ? atomicAdd(&a.count[t1], 1) == tile_target - 1 : 0;
-        __threadfence();
+        done[0] = atom_add_acq_rel(&a.count[t0], 1) == tile_target - 1;
+        done[1] = t1 != t0 ? atom_add_acq_rel(&a.count[t1], 1) == tile_target - 1 : 0;
     }
     __syncthreads();
     int ntile = 0;
@@ -1047,14 +1055,10 @@ __device__ void level_arrive(const LevelArgs& a, int t0, int t1, int tile_target
         if (!done[k]) continue;
         level_rowtile(a, k ? t1 : t0, trace_only);
         ++ntile;
-        __threadfence();
         __syncthreads();
     }
     if (ntile == 0) return;
-    if (tid == 0) {
-        last = atomicAdd(&a.count[a.nct], ntile) + ntile == a.nct;
-        __threadfence();
-    }
+    if (tid == 0) last = atom_add_acq_rel(&a.count[a.nct], ntile) + ntile == a.nct;
     __syncthreads();
     if (last) level_final(a, slot, n_lvl, trace_only, step_end);
 }
@@ -1062,11 +1066,15 @@ __device__ void level_arrive(const LevelArgs& a, int t0, int t1, int tile_target
 // Update of the FP32-pair master (eq:leapfrog, eq:eomrho, frozen nuclei): the same
 // tile-pair scheme and operands as k_update, with the increment factor * rhodot formed
 // as fh * d + fl * d (factor = fh + fl) so the step length carries no FP32 rounding.
-// The base level is first renormalised to Tr(rho S) = N_e: rho_base <- f rho_base with
-// f = 1 + eps from its trace (Sec. 2.3: the exact leapfrog conserves the electron number;
-// the reduced products do not, by a few 1e-11 per step), i.e. the deviation gains
-// eps (rho_ref + deviation).  Mulliken row partials of the new deviation in FP32-pair
+// Every kRenormEvery steps the base level is first renormalised to Tr(rho S) = N_e:
+// rho_base <- f rho_base with f = 1 + eps from its trace (Sec. 2.3: the exact leapfrog
+// conserves the electron number; the reduced products do not, by ~1e-14 of N_e per step),
+// i.e. the deviation gains eps (rho_ref + deviation).  Mulliken row partials of the new deviation in FP32-pair
 // arithmetic; the last blocks evaluate the new level (level_arrive).
+// Steps between renormalisations of a leapfrog level (the reduced forms drift by ~1e-14 of
+// N_e per step, so Tr(rho S) stays within ~1e-12 of N_e in between).
+constexpr int kRenormEvery = 64;
+
 __device__ __forceinline__ void update_df_block(const UpdateDfArgs& A, int b) {
     const int N = A.N, nct = A.nct;
     const MasterPtrs& base = A.base;
@@ -1088,7 +1096,9 @@ __device__ __forceinline__ void update_df_block(const UpdateDfArgs& A, int b) {
     __shared__ float s_bound;
     __shared__ float eps_sh;
     if (threadIdx.x == 0 && threadIdx.y == 0) {
-        eps_sh = sc->eps_lvl[ops.base_slot];
+        // both leapfrog chains are renormalised once every kRenormEvery steps
+        const long long n = sc->step;
+        eps_sh = (n % kRenormEvery) < 2 ? sc->eps_lvl[ops.base_slot] : 0.f;
         if (ops.dyn) {
             // |X| <= the sum of the maxima of its partial products
             const tc::DynScales* d = ops.dyn;
@@ -1238,9 +1248,9 @@ __device__ __forceinline__ void update_df_block(const UpdateDfArgs& A, int b) {
     level_arrive(lv, bi, bj, nct, out_slot, sc->step + 1, false, true);
 }
 
-__global__ void __launch_bounds__(256, 6) k_update_df(UpdateDfArgs a) { update_df_block(a, blockIdx.x); }
+__global__ void __launch_bounds__(256, 4) k_update_df(UpdateDfArgs a) { update_df_block(a, blockIdx.x); }
 
-__global__ void __launch_bounds__(256, 6)
+__global__ void __launch_bounds__(256, 4)
     k_update_df_grouped(const UpdateDfArgs* __restrict__ args, const int2* __restrict__ work) {
     const int2 w = work[blockIdx.x];
     update_df_block(args[w.x], w.y);

@@ -130,6 +130,20 @@ __device__ __forceinline__ void gemm_tile(const Maps& maps, const GemmParams& p,
     fence_after();
     const uint32_t tmem = *tmem_slot;
 
+    // delta-M epilogue of 64-wide tiles (one 32-column chunk per warp): every thread loads
+    // its row's 32 values of M_gs now, so that the loads overlap the products
+    float4 mgs_pre[8];
+    bool pre = false;
+    if (BN == 64 && P.mode == 1) {
+        const int row = m0 + (warp & 3) * 32 + lane, col0 = n0 + (warp >> 2) * 32;
+        pre = row < p.M && col0 + 32 <= p.N && (p.ld_mgs & 3) == 0;
+        if (pre) {
+            const float4* mg4 =
+                reinterpret_cast<const float4*>(p.Mgs + static_cast<size_t>(row) * p.ld_mgs + col0);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) mgs_pre[u] = __ldg(mg4 + u);
+        }
+    }
     if (warp == 0 && lane == 0) {
         // TMA producer: A pieces then B pieces of one 64-wide K block per stage
         for (int kb = 0; kb < nkb; ++kb) {
@@ -274,8 +288,9 @@ __device__ __forceinline__ void gemm_tile(const Maps& maps, const GemmParams& p,
                 if (vec) {
 #pragma unroll
                     for (int j0 = 0; j0 < 32; j0 += 8) {
-                        const float4 g0 = *reinterpret_cast<const float4*>(mg + j0);
-                        const float4 g1 = *reinterpret_cast<const float4*>(mg + j0 + 4);
+                        const float4 g0 = pre ? mgs_pre[j0 / 4] : *reinterpret_cast<const float4*>(mg + j0);
+                        const float4 g1 =
+                            pre ? mgs_pre[j0 / 4 + 1] : *reinterpret_cast<const float4*>(mg + j0 + 4);
                         const float gm[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
                         uint16_t qd[3][8], qm[3][8];
 #pragma unroll
