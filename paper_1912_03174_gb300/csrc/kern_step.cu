@@ -1073,7 +1073,7 @@ __device__ void level_arrive(const LevelArgs& a, int t0, int t1, int tile_target
 // arithmetic; the last blocks evaluate the new level (level_arrive).
 // Steps between renormalisations of a leapfrog level (the reduced forms drift by ~1e-14 of
 // N_e per step, so Tr(rho S) stays within ~1e-12 of N_e in between).
-constexpr int kRenormEvery = 64;
+constexpr int kRenormEvery = 8;
 
 __device__ __forceinline__ void update_df_block(const UpdateDfArgs& A, int b) {
     const int N = A.N, nct = A.nct;

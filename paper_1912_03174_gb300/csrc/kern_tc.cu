@@ -403,15 +403,28 @@ __device__ __forceinline__ void split_dham_block(int N, const float* __restrict_
     const float s = dyn ? dyn->s_dh : scale_const;
     if (c >= N) return;
     // rows r, r + gridDim.y blockDim.y, ...: the scale prologue is paid once per block
-    const float dvc = dv[c];
+    const float dvc = __ldg(dv + c);
     bool ok = true;
-    for (int row = r; row < N; row += gy * blockDim.y) {
-        uint16_t q[3];
-        ok &= split_value<SCHEME>(0.5f * S[static_cast<size_t>(row) * N + c] * (dv[row] + dvc) * s,
-                                  bf16, q);
-        const size_t o = static_cast<size_t>(row) * ld_out + c;
+    const int stride = gy * blockDim.y;
+    // eight rows per pass with their loads in flight together
+    for (int row0 = r; row0 < N; row0 += 8 * stride) {
+        float sv[8], dr[8];
 #pragma unroll
-        for (int t = 0; t < Cfg<SCHEME>::PIECES; ++t) out.p[t][o] = q[t];
+        for (int u = 0; u < 8; ++u) {
+            const int row = row0 + u * stride;
+            sv[u] = row < N ? __ldg(S + static_cast<size_t>(row) * N + c) : 0.f;
+            dr[u] = row < N ? __ldg(dv + row) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int row = row0 + u * stride;
+            if (row >= N) break;
+            uint16_t q[3];
+            ok &= split_value<SCHEME>(0.5f * sv[u] * (dr[u] + dvc) * s, bf16, q);
+            const size_t o = static_cast<size_t>(row) * ld_out + c;
+#pragma unroll
+            for (int t = 0; t < Cfg<SCHEME>::PIECES; ++t) out.p[t][o] = q[t];
+        }
     }
     if (!ok && err) atomicCAS(err, 0, 4);
 }

@@ -215,14 +215,18 @@ def cluster_c3(seed: int = 1003, n_atoms: int = 512):
     """Ehrenfest cluster: 512 atoms (N = 2048) by random insertion at
     0.02 bohr^-3 with a 2.4 bohr minimum distance, 12 amu, 300 K Maxwell
     velocities; SCC; Gaussian-envelope laser E0 = 0.01, omega = 0.1 Ha,
-    FWHM 10 fs centred at 20 fs, along x; dt = 0.2, 10000 steps."""
+    FWHM 10 fs centred at 20 fs, along x; dt = 0.2, 10000 steps.  Pair repulsion
+    A exp(-r / 0.5) with A fitted to zero initial virial (the 512-atom workload)."""
     rng = np.random.default_rng(seed)
     R = random_cluster(n_atoms, 0.02, 2.4, rng)
     eps_s, eps_p, U, mass = _species_params(rng, 1, scc=True)
     species = np.zeros(n_atoms, np.int32)
     V = maxwell_velocities(mass[species], 300.0, rng)
+    # pair repulsion amplitude fitted once to zero initial virial of the 512-atom cluster
+    # (oracle/fit_c3_repulsion.py); without it the unrelaxed cluster collapses
+    rep_A = 66.78242917 if (n_atoms == 512 and seed == 1003) else 1.0
     sysm = System(f"cluster{n_atoms}", R, species, eps_s, eps_p, U, mass,
-                  n_electrons=4.0 * n_atoms, rep_A=1.0, rep_b=0.5, V=V)
+                  n_electrons=4.0 * n_atoms, rep_A=rep_A, rep_b=0.5, V=V)
     fwhm = 10.0 * FS
     fld = Field(E0=0.01, omega=0.1, phase=0.0, t_center=2.0 * fwhm, fwhm=fwhm, envelope=1)
     run = Run(dt=0.2, n_steps=10000, scc=True, move_nuclei=True, field=fld, kT=SCC_KT)

@@ -504,3 +504,23 @@ def test_shiftnet_gradient_matches_central_differences():
         fd[i] = (O.shiftnet_loss_grad(p + e, X, Y, F, H, bf16=False)[0]
                  - O.shiftnet_loss_grad(p - e, X, Y, F, H, bf16=False)[0]) / (2 * h)
     assert np.max(np.abs(g - fd)) < 1e-7 * max(1.0, np.max(np.abs(g)))
+
+
+def test_fitted_repulsion_zeroes_the_initial_virial():
+    # oracle/fit_c3_repulsion.py: with A from the fit, the total ground-state force of the
+    # unrelaxed cluster (electronic and repulsive, eq:forces at rest, no field) has zero virial
+    import dataclasses
+    from oracle import fit_c3_repulsion as FIT
+    sysm, run = I.cluster_c3(n_atoms=32)
+    A = FIT.virial_repulsion(sysm, run)
+    s = dataclasses.replace(sysm, rep_A=A)
+    R = np.asarray(s.R, dtype=np.float64)
+    rho, gs, S, Sinv = O.setup(s, dataclasses.replace(run, field=None, move_nuclei=False))
+    S, H0 = O.model_matrices(s, R)
+    gamma = O.gamma_matrix(s, R)
+    dq = O.mulliken(s, rho, S) - O.reference_populations(s)
+    v = O.atom_potential(gamma, dq, R, np.zeros(3), True)
+    F = O.forces(s, rho, S, Sinv, O.scc_hamiltonian(s, H0, S, v), gamma, dq, v, R, np.zeros(3), True)
+    Rc = R - R.mean(axis=0)
+    assert A > 1.0
+    assert abs(np.sum(Rc * F)) < 1e-9 * np.sum(np.abs(Rc * F))
