@@ -299,7 +299,8 @@ tdb_status tdb_check(tdb_ctx* ctx, double tol_trace);
  * TDB_ERR_ARG) like the bounded waits of the tensor-core products, and then records a
  * time-out in the context's device error flag.  The next call that reads the flag
  * (tdb_observables, tdb_check) returns TDB_ERR_TIMEOUT and the context becomes sticky, as
- * after a real time-out.  The probe issues no copy and holds no tensor memory, so the
+ * after a real time-out.  (The same flag records a split piece that overflowed its scale in
+ * the FP16X6/FP16X3/BF16X3 products; that read returns TDB_ERR_NUMERIC.)  The probe issues no copy and holds no tensor memory, so the
  * GPU and the CUDA context stay usable.  Asynchronous. */
 tdb_status tdb_wait_probe(tdb_ctx* ctx, long long polls);
 

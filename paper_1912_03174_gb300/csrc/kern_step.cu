@@ -877,18 +877,33 @@ __device__ void level_rowtile(const LevelArgs& a, int r, bool trace_only) {
     const int A0 = r * apt;
     const int na = min(apt, a.nat - A0);
     const int len = a.nper * a.nct;
+    const bool pv_on = !trace_only && a.scc;
+    const float2 z = make_float2(0.f, 0.f);
+    // every load of the stage goes out first (one round trip): the row partials of this
+    // warp's first atom, gamma of this thread's first atom against the tile's atoms, and
+    // the positions of the tile's atoms
+    float2 pp[8], gv[8], rr[3] = {z, z, z};
+    {
+        const float2* p = a.partial + (size_t)(A0 + warp) * len;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            pp[u] = (warp < na && lane + 32 * u < len) ? ldcg2(p + lane + 32 * u) : z;
+        const float2* g = a.gam2 + (size_t)tid * a.nat + A0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) gv[u] = (pv_on && tid < a.nat && u < na) ? __ldg(g + u) : z;
+        if (warp == 0 && lane < na)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) rr[k] = __ldg(a.R2 + 3 * (A0 + lane) + k);
+    }
     for (int i = warp; i < na; i += 8) {
-        const float2* p = a.partial + (size_t)(A0 + i) * len;
-        float2 s = make_float2(0.f, 0.f);
-        // lane's partials in increasing order, eight loads in flight at a time
-        for (int k0 = lane; k0 < len; k0 += 32 * 8) {
-            float2 v[8];
+        float2 s = z;
+        if (i == warp) {
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                v[u] = k0 + 32 * u < len ? ldcg2(p + k0 + 32 * u) : make_float2(0.f, 0.f);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) s = df2_add(s, v[u]);
+            for (int u = 0; u < 8; ++u) s = df2_add(s, pp[u]);
         }
+        // the rest of this atom's partials (long rows), then further atoms of this warp
+        for (int k = (i == warp ? lane + 256 : lane); k < len; k += 32)
+            s = df2_add(s, ldcg2(a.partial + (size_t)(A0 + i) * len + k));
         s = df2_warp_sum(s);
         if (lane == 0) dq_sh[i] = s;
     }
@@ -897,56 +912,107 @@ __device__ void level_rowtile(const LevelArgs& a, int r, bool trace_only) {
         float2 m[4] = {};
         if (lane < na) {
             const float2 d = dq_sh[lane];
-            const int A = A0 + lane;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) m[k] = df2_mul(d, a.R2[3 * A + k]);
+            for (int k = 0; k < 3; ++k) m[k] = df2_mul(d, rr[k]);
             m[3] = d;
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) m[k] = df2_warp_sum(m[k]);
         if (lane < 4) a.part[4 * r + lane] = m[lane];
     }
-    if (trace_only || !a.scc) return;
+    if (!pv_on) return;
     for (int Ap = tid; Ap < a.nat; Ap += 256) {
         const float2* g = a.gam2 + (size_t)Ap * a.nat + A0;
-        float2 s = make_float2(0.f, 0.f);
-        for (int i0 = 0; i0 < na; i0 += 8) {
-            float2 v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = i0 + u < na ? __ldg(g + i0 + u) : make_float2(0.f, 0.f);
+        float2 s = z;
+        int i = 0;
+        if (Ap == tid) {
 #pragma unroll
             for (int u = 0; u < 8; ++u)
-                if (i0 + u < na) s = df2_add(s, df2_mul(v[u], dq_sh[i0 + u]));
+                if (u < na) s = df2_add(s, df2_mul(gv[u], dq_sh[u]));
+            i = 8;
         }
+        for (; i < na; ++i) s = df2_add(s, df2_mul(__ldg(g + i), dq_sh[i]));
         a.pv[(size_t)r * a.nat + Ap] = s;
     }
 }
 
-// Final stage (one block): Tr(rho S) and the renormalisation factor of level `slot`; unless
-// trace_only, v - v_ref per orbital (dv_f) and its maximum (with the FP16X6 scales of the
-// next products), the dipole mu = mu_ref - sum_A dq_A R_A into sc->mu and the history slot
-// of step n_lvl, the field record.  step_end: the step counter advances to n_lvl and the
-// FP16X6 maxima move (the new level is in `slot`).  Resets the counters.
-__device__ void level_final(const LevelArgs& a, int slot, long long n_lvl, bool trace_only,
-                            bool step_end) {
+// Final stage, a kernel of its own after the tile stages (one block per 32 atoms, eight
+// threads per atom): v - v_ref per orbital (dv_f) from the tiles' partial potentials, the
+// maximum |dv| over the blocks; the block that finishes last takes Tr(rho S) and the
+// renormalisation factor of level `slot`, the FP16X6 scales of the next products, the dipole
+// mu = mu_ref - sum_A dq_A R_A into sc->mu and the history slot of step n_lvl, the field
+// record, and with step_end the step counter (to n_lvl) and the FP16X6 maxima (the new level
+// is in `slot`); it resets every counter.  trace_only (one block): only Tr(rho S) and f - 1.
+__device__ __forceinline__ int atom_add_acq_rel(int* p, int v);
+
+__device__ void level_final_block(const LevelArgs& a, int slot, long long n_lvl, bool trace_only,
+                                  bool step_end, int blk, int nblk) {
     __shared__ float2 tot[4];
     __shared__ float E_sh[3];
     __shared__ float red[8];
+    __shared__ int last;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     DevScalars* sc = a.sc;
+    const float2 z = make_float2(0.f, 0.f);
+    int* max_bits = a.count + a.nct + 1;     // max |dv| of this evaluation (float bits, >= 0)
+    if (!trace_only) {
+        if (tid == 0) {
+            float E[3] = {0.f, 0.f, 0.f};
+            if (sc->field.on) {
+                const double t = sc->t_base + (double)(n_lvl - sc->n_base) * sc->dt;
+                field_at_f(sc->field, t, E);
+            }
+            E_sh[0] = E[0];
+            E_sh[1] = E[1];
+            E_sh[2] = E[2];
+        }
+        // eight threads per atom, thread j of an atom summing tiles j, j + 8, ... in order
+        const int A = blk * 32 + (tid >> 3), j = tid & 7;
+        float2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            v[u] = (a.scc && A < a.nat && j + 8 * u < a.nct) ? ldcg2(a.pv + (size_t)(j + 8 * u) * a.nat + A) : z;
+        float rx = 0.f, ry = 0.f, rz = 0.f, cr = 0.f;
+        if (A < a.nat && j == 0) {
+            rx = __ldg(&a.R2[3 * A].x);
+            ry = __ldg(&a.R2[3 * A + 1].x);
+            rz = __ldg(&a.R2[3 * A + 2].x);
+            cr = __ldg(a.c_res + A);
+        }
+        float2 acc = z;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc = df2_add(acc, v[u]);
+        for (int r = j + 64; r < a.nct; r += 8)
+            if (a.scc && A < a.nat) acc = df2_add(acc, ldcg2(a.pv + (size_t)r * a.nat + A));
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) acc = df2_add(acc, df2_shfl_xor(acc, o));
+        __syncthreads();
+        float mx = 0.f;
+        if (A < a.nat && j == 0) {
+            const float ext = fmaf(rx, E_sh[0], fmaf(ry, E_sh[1], rz * E_sh[2]));
+            const float dv = acc.x + (acc.y + (ext + cr));
+            for (int k = 0; k < a.nper; ++k) a.dv_f[A * a.nper + k] = dv;
+            mx = fabsf(dv);
+        }
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) red[warp] = mx;
+        __syncthreads();
+        if (tid == 0) {
+            float m = red[0];
+            for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w]);
+            atomicMax(max_bits, __float_as_int(m));
+            last = atom_add_acq_rel(a.count + a.nct, 1) == nblk - 1;
+        }
+        __syncthreads();
+        if (!last) return;
+    }
+    // the last block: sums of the tiles' dipole and trace parts (warps 0-3)
     if (warp < 4) {
-        float2 s = make_float2(0.f, 0.f);
+        float2 s = z;
         for (int r = lane; r < a.nct; r += 32) s = df2_add(s, ldcg2(a.part + 4 * r + warp));
         s = df2_warp_sum(s);
         if (lane == 0) tot[warp] = s;
-    } else if (tid == 128 && !trace_only) {
-        const double t = sc->t_base + (double)(n_lvl - sc->n_base) * sc->dt;
-        float E[3];
-        field_at_f(sc->field, t, E);
-        E_sh[0] = E[0];
-        E_sh[1] = E[1];
-        E_sh[2] = E[2];
     }
     __syncthreads();
     if (tid == 0) {
@@ -956,71 +1022,45 @@ __device__ void level_final(const LevelArgs& a, int slot, long long n_lvl, bool 
         sc->eps_lvl[slot] = eps;
         sc->trace_lvl[slot] = (sc->n_e - sc->c0_trace) + ((double)d.x + (double)d.y);
     }
-    if (trace_only) {
-        for (int i = tid; i <= a.nct; i += 256) a.count[i] = 0;
-        return;
-    }
-    const float Ex = E_sh[0], Ey = E_sh[1], Ez = E_sh[2];
-    float mx = 0.f;
-    for (int A = tid; A < a.nat; A += 256) {
-        // the tiles' partial potentials of atom A, sixteen loads in flight at a time, into
-        // four interleaved sums
-        float2 acc[4] = {};
-        if (a.scc)
-            for (int r0 = 0; r0 < a.nct; r0 += 16) {
-                float2 v[16];
-#pragma unroll
-                for (int u = 0; u < 16; ++u)
-                    v[u] = r0 + u < a.nct ? ldcg2(a.pv + (size_t)(r0 + u) * a.nat + A)
-                                          : make_float2(0.f, 0.f);
-#pragma unroll
-                for (int u = 0; u < 16; ++u) acc[u & 3] = df2_add(acc[u & 3], v[u]);
+    if (!trace_only) {
+        if (tid == 0) {
+            const float m = __int_as_float(__ldcg(max_bits));
+            tc::DynScales* dy = a.dyn;
+            if (dy) {
+                dy->max_dv = (double)m;
+                if (a.has_scales) {
+                    dy->s_dh = pscale_f(m);
+                    dy->s_dm = pscale_f(m * (float)dy->sinv_norm);
+                }
+                for (int k = 0; k < tc::kMaxParts; ++k) dy->max_x[k] = 0.0;
+                if (step_end) {
+                    // the maximum the update's blocks accumulated (atomics, read through L2)
+                    dy->max_drho[slot] = __ldcg(&dy->max_drho[2]);
+                    dy->max_drho[2] = 0.0;
+                }
             }
-        const float2 s = df2_add(df2_add(acc[0], acc[1]), df2_add(acc[2], acc[3]));
-        const float ext = fmaf(a.R2[3 * A].x, Ex, fmaf(a.R2[3 * A + 1].x, Ey, a.R2[3 * A + 2].x * Ez));
-        const float dv = s.x + (s.y + (ext + a.c_res[A]));
-        for (int k = 0; k < a.nper; ++k) a.dv_f[A * a.nper + k] = dv;
-        mx = fmaxf(mx, fabsf(dv));
+            if (step_end) sc->step = n_lvl;
+        }
+        if (warp == 1) {
+            // dipole (lanes 0-2, one component each) into sc and the history slot of step n_lvl
+            const int k = lane < 3 ? lane : 0;
+            const double mu = sc->mu_ref[k] - ((double)tot[k].x + (double)tot[k].y);
+            const double ek = mu * (double)E_sh[k];
+            const double e_ext = -(ek + __shfl_down_sync(0xffffffffu, ek, 1) +
+                                   __shfl_down_sync(0xffffffffu, ek, 2));
+            if (lane < 3) {
+                long long h = n_lvl % sc->hist_cap;
+                if (h < 0) h += sc->hist_cap;
+                sc->mu[k] = mu;
+                sc->E[k] = (double)E_sh[k];
+                a.hist[3 * h + k] = mu;
+            }
+            if (lane == 0) sc->e_ext = e_ext;
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) red[warp] = mx;
+    // the reset includes the maximum |dv| that thread 0 read above
     __syncthreads();
-    if (tid == 0) {
-        float m = red[0];
-        for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w]);
-        tc::DynScales* dy = a.dyn;
-        if (dy) {
-            dy->max_dv = (double)m;
-            if (a.has_scales) {
-                dy->s_dh = pscale_f(m);
-                dy->s_dm = pscale_f(m * (float)dy->sinv_norm);
-            }
-            for (int k = 0; k < tc::kMaxParts; ++k) dy->max_x[k] = 0.0;
-            if (step_end) {
-                // the maximum the update's blocks accumulated (atomics, read through L2)
-                dy->max_drho[slot] = __ldcg(&dy->max_drho[2]);
-                dy->max_drho[2] = 0.0;
-            }
-        }
-        if (step_end) sc->step = n_lvl;
-    }
-    if (warp == 1) {
-        // dipole (lanes 0-2, one component each) into sc and the history slot of step n_lvl
-        const int k = lane < 3 ? lane : 0;
-        const double mu = sc->mu_ref[k] - ((double)tot[k].x + (double)tot[k].y);
-        const double ek = mu * (double)E_sh[k];
-        const double e_ext = -(ek + __shfl_down_sync(0xffffffffu, ek, 1) +
-                               __shfl_down_sync(0xffffffffu, ek, 2));
-        if (lane < 3) {
-            long long h = n_lvl % sc->hist_cap;
-            if (h < 0) h += sc->hist_cap;
-            sc->mu[k] = mu;
-            sc->E[k] = (double)E_sh[k];
-            a.hist[3 * h + k] = mu;
-        }
-        if (lane == 0) sc->e_ext = e_ext;
-    }
-    for (int i = tid; i <= a.nct; i += 256) a.count[i] = 0;
+    for (int i = tid; i <= a.nct + 1; i += 256) a.count[i] = 0;
 }
 
 // Counter increment with acquire-release semantics at GPU scope: after a block barrier it
@@ -1036,31 +1076,24 @@ __device__ __forceinline__ int atom_add_acq_rel(int* p, int v) {
 }
 
 // After a block has written its row partials: count it towards the row tiles it covered
-// (tile_target arrivals complete a tile); the block completing a tile runs the tile's
-// stage, and the block completing the last tile runs the final stage.  The stages read what
-// other blocks wrote through L2 (ld.global.cg).
-__device__ void level_arrive(const LevelArgs& a, int t0, int t1, int tile_target, int slot,
-                             long long n_lvl, bool trace_only, bool step_end) {
+// (tile_target arrivals complete a tile); the block completing a tile runs the tile's stage,
+// reading what other blocks wrote through L2 (ld.global.cg).  The final stage is a kernel of
+// its own (level_final_block).
+__device__ void level_arrive(const LevelArgs& a, int t0, int t1, int tile_target, bool trace_only) {
     __shared__ int done[2];
-    __shared__ int last;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     __syncthreads();
-    if (tid == 0) {
-        done[0] = atom_add_acq_rel(&a.count[t0], 1) == tile_target - 1;
-        done[1] = t1 != t0 ? atom_add_acq_rel(&a.count[t1], 1) == tile_target - 1 : 0;
+    // the two tiles' counters by two threads at once
+    if (tid < 2) {
+        const int t = tid ? t1 : t0;
+        done[tid] = (tid == 0 || t1 != t0) ? atom_add_acq_rel(&a.count[t], 1) == tile_target - 1 : 0;
     }
     __syncthreads();
-    int ntile = 0;
     for (int k = 0; k < 2; ++k) {
         if (!done[k]) continue;
         level_rowtile(a, k ? t1 : t0, trace_only);
-        ++ntile;
         __syncthreads();
     }
-    if (ntile == 0) return;
-    if (tid == 0) last = atom_add_acq_rel(&a.count[a.nct], ntile) + ntile == a.nct;
-    __syncthreads();
-    if (last) level_final(a, slot, n_lvl, trace_only, step_end);
 }
 
 // Update of the FP32-pair master (eq:leapfrog, eq:eomrho, frozen nuclei): the same
@@ -1245,7 +1278,7 @@ __device__ __forceinline__ void update_df_block(const UpdateDfArgs& A, int b) {
         if (bi == 0 && bj == 0 && tx == 0 && ty == 0) ops.dyn->s_rho = op_scale;
     }
     __syncthreads();
-    level_arrive(lv, bi, bj, nct, out_slot, sc->step + 1, false, true);
+    level_arrive(lv, bi, bj, nct, false);
 }
 
 __global__ void __launch_bounds__(256, 4) k_update_df(UpdateDfArgs a) { update_df_block(a, blockIdx.x); }
@@ -1258,8 +1291,23 @@ __global__ void __launch_bounds__(256, 4)
 
 // Per-level evaluation outside a step: block r runs the row-tile stage of tile r and the
 // block completing the last tile the final stage (the arithmetic of the update's tail).
-__global__ void __launch_bounds__(256) k_level(LevelArgs lv, int slot, int trace_only) {
-    level_arrive(lv, blockIdx.x, blockIdx.x, 1, slot, lv.sc->step, trace_only != 0, false);
+__global__ void __launch_bounds__(256) k_level(LevelArgs lv, int trace_only) {
+    level_arrive(lv, blockIdx.x, blockIdx.x, 1, trace_only != 0);
+}
+
+// The final stage of a level evaluation: after an update (step_end, the new level n + 1 in
+// slot) or after the tile stages of k_level (the current level).
+__global__ void __launch_bounds__(256) k_level_final(LevelArgs lv, int slot, int trace_only, int step_end) {
+    const long long n_lvl = lv.sc->step + (step_end ? 1 : 0);
+    level_final_block(lv, slot, n_lvl, trace_only != 0, step_end != 0, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(256)
+    k_level_final_grouped(const LevelFinalArgs* __restrict__ args, const int2* __restrict__ work) {
+    const int2 w = work[blockIdx.x];
+    const LevelFinalArgs& f = args[w.x];
+    const long long n_lvl = f.lv.sc->step + 1;
+    level_final_block(f.lv, f.slot, n_lvl, false, true, w.y, level_final_blocks(f.lv.nat));
 }
 
 // FP64 populations from the (hi, lo) row partials of the deviation: one warp per atom
@@ -1419,7 +1467,18 @@ void launch_update_df_grouped(const UpdateDfArgs* args, const int2* work, int nw
 }
 
 void launch_level(const Ctx& c, const LevelArgs& lv, int slot, int trace_only, cudaStream_t st) {
-    k_level<<<c.nct, dim3(kTile, 8), 0, st>>>(lv, slot, trace_only);
+    k_level<<<c.nct, dim3(kTile, 8), 0, st>>>(lv, trace_only);
+    k_level_final<<<trace_only ? 1 : level_final_blocks(c.nat), dim3(kTile, 8), 0, st>>>(
+        lv, slot, trace_only, 0);
+}
+
+void launch_level_final(const Ctx& c, const LevelArgs& lv, int slot, cudaStream_t st) {
+    k_level_final<<<level_final_blocks(c.nat), dim3(kTile, 8), 0, st>>>(lv, slot, 0, 1);
+}
+
+void launch_level_final_grouped(const LevelFinalArgs* args, const int2* work, int nwork,
+                                cudaStream_t st) {
+    k_level_final_grouped<<<nwork, dim3(kTile, 8), 0, st>>>(args, work);
 }
 
 void launch_charges_df(const Ctx& c, const float2* partial, double* q, double* dq, cudaStream_t st) {

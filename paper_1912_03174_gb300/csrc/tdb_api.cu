@@ -180,7 +180,7 @@ size_t carve(Ctx& c, char* base) {
         c.lv_pv = k.take<float2>((size_t)c.nct * nat);
         c.lv_part = k.take<float2>(4 * (size_t)c.nct);
         c.c_res = k.take<float>(nat);
-        c.lv_count = k.take<int>((size_t)c.nct + 1);
+        c.lv_count = k.take<int>((size_t)c.nct + 2);
     }
     if (mixed(c)) {
         c.dv_f = k.take<float>(N);
@@ -648,7 +648,7 @@ tdb_status setup_level_constants(Ctx& c) {
     CK(cudaMemcpyAsync(c.gam2, g2.data(), sizeof(float2) * g2.size(), cudaMemcpyHostToDevice, c.stream));
     CK(cudaMemcpyAsync(c.R2, r2.data(), sizeof(float2) * r2.size(), cudaMemcpyHostToDevice, c.stream));
     CK(cudaMemcpyAsync(c.c_res, cres.data(), sizeof(float) * nat, cudaMemcpyHostToDevice, c.stream));
-    CK(cudaMemsetAsync(c.lv_count, 0, sizeof(int) * ((size_t)c.nct + 1), c.stream));
+    CK(cudaMemsetAsync(c.lv_count, 0, sizeof(int) * ((size_t)c.nct + 2), c.stream));
     CK(cudaMemcpyAsync(c.sc, &h, sizeof h, cudaMemcpyHostToDevice, c.stream));
     CK(cudaStreamSynchronize(c.stream));
     return TDB_OK;
@@ -1141,6 +1141,9 @@ tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* t
         MARK("update");
         launch_update_df(c, ts.upd.base, ts.upd.out, factor, c.sc, ts.upd.ops, ts.upd.lv, c.stream);
         ++n;
+        MARK("level");
+        launch_level_final(c, ts.upd.lv, ts.upd.out_slot, c.stream);
+        ++n;
     } else {
         const int N = c.N;
         // delta M = S^-1 delta H (left half of [dM | M]), M = M_gs + delta M (right half)
@@ -1166,6 +1169,9 @@ tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* t
         ops.base_slot = euler ? cur : prv;
         launch_update_df(c, euler ? c.ms[cur] : c.ms[prv], c.ms[prv], factor, c.sc, ops,
                          level_args(c), c.stream);
+        ++n;
+        MARK("level");
+        launch_level_final(c, level_args(c), prv, c.stream);
         ++n;
     }
     MARK("end");
@@ -1951,6 +1957,13 @@ tdb_status tdb_observables(tdb_ctx* c, tdb_obs* o, double* charges, double* forc
         CK(cudaStreamSynchronize(c->stream));
         if (*he != 0 && !c->sticky) {
             c->sticky = true;
+            // codes 1-3: a bounded wait of a tensor-core product (producer, MMA, epilogue),
+            // 5: the wait probe; 4: a value outside the range of its split pieces at the
+            // scale of the step
+            if (*he == 4) {
+                set_err("a split piece overflowed its scale (device code 4)");
+                return TDB_ERR_NUMERIC;
+            }
             set_err("a bounded device-side wait timed out (code %d)", *he);
             return TDB_ERR_TIMEOUT;
         }
@@ -2301,8 +2314,9 @@ struct tdb_batch {
     tc::GroupedGemm* d_dm[2] = {};
     tc::GroupedGemm* d_x[2] = {};
     UpdateDfArgs* d_upd[2] = {};
-    int2 *w_split = nullptr, *w_dm = nullptr, *w_x = nullptr, *w_upd = nullptr;
-    int n_split = 0, n_dm = 0, n_x = 0, n_upd = 0;
+    LevelFinalArgs* d_fin[2] = {};
+    int2 *w_split = nullptr, *w_dm = nullptr, *w_x = nullptr, *w_upd = nullptr, *w_fin = nullptr;
+    int n_split = 0, n_dm = 0, n_x = 0, n_upd = 0, n_fin = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
 };
 
@@ -2341,7 +2355,8 @@ tdb_status batch_layout(tdb_batch& b, int bn, int schedule) {
     std::vector<tc::SplitDhArgs> split[2];
     std::vector<tc::GroupedGemm> dm[2], xg[2];
     std::vector<UpdateDfArgs> upd[2];
-    std::vector<int> nb_split(P), nb_dm(P), nb_x(P), nb_upd(P);
+    std::vector<LevelFinalArgs> fin[2];
+    std::vector<int> nb_split(P), nb_dm(P), nb_x(P), nb_upd(P), nb_fin(P);
     for (int g = 0; g < 2; ++g)
         for (int p = 0; p < P; ++p) {
             Ctx& c = *b.ctxs[p];
@@ -2355,19 +2370,26 @@ tdb_status batch_layout(tdb_batch& b, int bn, int schedule) {
             dm[g].push_back(grouped(c.maps_dm, ts.dm, c.N, 64, 1));
             xg[g].push_back(grouped(mx, ts.x, c.N, bn, ts.x_parts));
             upd[g].push_back(ts.upd);
+            LevelFinalArgs f{};
+            f.lv = ts.upd.lv;
+            f.slot = ts.upd.out_slot;
+            fin[g].push_back(f);
+            nb_fin[p] = level_final_blocks(c.nat);
             nb_split[p] = tc::split_dham_blocks(c.N);
             nb_dm[p] = dm[g].back().tiles_x * dm[g].back().tiles_y;
             nb_x[p] = xg[g].back().tiles_x * xg[g].back().tiles_y * ts.x_parts;
             nb_upd[p] = c.nct * (c.nct + 1) / 2;
         }
     const std::vector<int2> ws = work_list(b, nb_split, schedule), wd = work_list(b, nb_dm, schedule),
-                            wx = work_list(b, nb_x, schedule), wu = work_list(b, nb_upd, schedule);
+                            wx = work_list(b, nb_x, schedule), wu = work_list(b, nb_upd, schedule),
+                            wf = work_list(b, nb_fin, schedule);
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t s_split = up(sizeof(tc::SplitDhArgs) * P), s_gg = up(sizeof(tc::GroupedGemm) * P),
-                 s_upd = up(sizeof(UpdateDfArgs) * P);
-    const size_t total = 2 * (s_split + 2 * s_gg + s_upd) +
+                 s_upd = up(sizeof(UpdateDfArgs) * P), s_fin = up(sizeof(LevelFinalArgs) * P);
+    const size_t total = 2 * (s_split + 2 * s_gg + s_upd + s_fin) +
                          up(sizeof(int2) * ws.size()) + up(sizeof(int2) * wd.size()) +
-                         up(sizeof(int2) * wx.size()) + up(sizeof(int2) * wu.size());
+                         up(sizeof(int2) * wx.size()) + up(sizeof(int2) * wu.size()) +
+                         up(sizeof(int2) * wf.size());
     if (b.dmem) {
         CK(cudaStreamSynchronize(b.stream));
         cudaFree(b.dmem);
@@ -2391,11 +2413,14 @@ tdb_status batch_layout(tdb_batch& b, int bn, int schedule) {
         b.d_dm[g] = reinterpret_cast<tc::GroupedGemm*>(put(dm[g].data(), sizeof(tc::GroupedGemm) * P, s_gg));
         b.d_x[g] = reinterpret_cast<tc::GroupedGemm*>(put(xg[g].data(), sizeof(tc::GroupedGemm) * P, s_gg));
         b.d_upd[g] = reinterpret_cast<UpdateDfArgs*>(put(upd[g].data(), sizeof(UpdateDfArgs) * P, s_upd));
+        b.d_fin[g] = reinterpret_cast<LevelFinalArgs*>(put(fin[g].data(), sizeof(LevelFinalArgs) * P, s_fin));
     }
     b.w_split = reinterpret_cast<int2*>(put(ws.data(), sizeof(int2) * ws.size(), up(sizeof(int2) * ws.size())));
     b.w_dm = reinterpret_cast<int2*>(put(wd.data(), sizeof(int2) * wd.size(), up(sizeof(int2) * wd.size())));
     b.w_x = reinterpret_cast<int2*>(put(wx.data(), sizeof(int2) * wx.size(), up(sizeof(int2) * wx.size())));
     b.w_upd = reinterpret_cast<int2*>(put(wu.data(), sizeof(int2) * wu.size(), up(sizeof(int2) * wu.size())));
+    b.w_fin = reinterpret_cast<int2*>(put(wf.data(), sizeof(int2) * wf.size(), up(sizeof(int2) * wf.size())));
+    b.n_fin = (int)wf.size();
     b.n_split = (int)ws.size();
     b.n_dm = (int)wd.size();
     b.n_x = (int)wx.size();
@@ -2413,6 +2438,7 @@ tdb_status batch_enqueue(tdb_batch& b, int g) {
     CK(tc::launch_grouped(b.scheme, b.d_dm[g], b.w_dm, b.n_dm, b.stream, 64));
     CK(tc::launch_grouped(b.scheme, b.d_x[g], b.w_x, b.n_x, b.stream, b.x_bn));
     launch_update_df_grouped(b.d_upd[g], b.w_upd, b.n_upd, b.stream);
+    launch_level_final_grouped(b.d_fin[g], b.w_fin, b.n_fin, b.stream);
     CKL();
     return TDB_OK;
 }
@@ -2613,7 +2639,7 @@ tdb_status tdb_batch_step(tdb_batch* b, long n) {
             c->cur ^= 1;
             c->n += 1;
             c->view_valid = false;
-            c->last_launches = 4;
+            c->last_launches = 5;
         }
     }
     CK(cudaEventRecord(b->ev, b->stream));

@@ -64,7 +64,7 @@ struct LevelArgs {
     tc::DynScales* dyn;        // FP16X6 scales (may be null)
     DevScalars* sc;
     double* hist;
-    int* count;                // [nct + 1] tile and stage counters, zero between launches
+    int* count;                // [nct + 2] tile and block counters and max |dv| bits, zero between steps
     float inv_ne;              // 1 / N_e
     int has_scales;            // write s_dh, s_dm from max |dv| (FP16X6)
 };
@@ -278,6 +278,15 @@ void launch_update_df(const Ctx& c, const MasterPtrs& base, const MasterPtrs& ou
 // state load), with the arithmetic of the update's tail; trace_only: only Tr(rho S) and the
 // renormalisation factor of level `slot` (partials of that level in lv.partial).
 void launch_level(const Ctx& c, const LevelArgs& lv, int slot, int trace_only, cudaStream_t st);
+// The final stage of the level evaluation after an update (the new level in slot).
+__host__ __device__ inline int level_final_blocks(int nat) { return (nat + 31) / 32; }
+void launch_level_final(const Ctx& c, const LevelArgs& lv, int slot, cudaStream_t st);
+struct LevelFinalArgs {
+    LevelArgs lv;
+    int slot, pad;
+};
+void launch_level_final_grouped(const LevelFinalArgs* args, const int2* work, int nwork,
+                                cudaStream_t st);
 void launch_view_to_master(const Ctx& c, const double* rre, const double* rim, const MasterPtrs& m,
                            cudaStream_t st);
 void launch_master_to_view(const Ctx& c, const MasterPtrs& m, double* rre, double* rim,
