@@ -199,11 +199,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def run_form(B, torch, sysm, run, precision, steps, warmup, flush, stream):
+TENSOR_FORMS = ("bf16x3", "fp16x3", "fp16x6")
+
+
+def run_form(B, torch, sysm, run, precision, steps, warmup, flush, stream, x_tile=0):
     """Ground state + kick, W warm-up steps, K timed steps (per-step events, L2
-    flushed between them).  Returns timing and the dipole trajectory."""
+    flushed between them).  Returns timing and the dipole trajectory.  x_tile: the X
+    product's tile width of the tensor-core forms (0: timed at the first step)."""
     p = B.Propagator(sysm, run, precision, stream=stream.cuda_stream, history_cap=warmup + steps + 8)
     try:
+        if x_tile and precision in TENSOR_FORMS:
+            B.tdb_set_x_tile(p.ctx, x_tile)
         p.setup()
         with torch.cuda.stream(stream):
             p.step(warmup)
@@ -228,10 +234,11 @@ def run_form(B, torch, sysm, run, precision, steps, warmup, flush, stream):
             for name, t in B.tdb_step_profiled(p.ctx):
                 prof.setdefault(name, []).append(t)
         obs = p.observables()
+        tile = B.tdb_x_tile(p.ctx)
     finally:
         p.close()
     return dict(ms=ms, hist=hist, prof={k: float(np.mean(v)) for k, v in prof.items()}, obs=obs,
-                launches=launches)
+                launches=launches, x_tile=tile)
 
 
 def form_summary(res: dict, forms, n_electrons: float) -> dict:
@@ -881,6 +888,8 @@ def main():
     ap.add_argument("--c4-probes", type=int, default=64, help="pump-probe scan size (0: skip)")
     ap.add_argument("--c4-steps", type=int, default=200, help="timed post-kick steps per probe")
     ap.add_argument("--no-c5", action="store_true", help="skip the learned-form section")
+    ap.add_argument("--x-tile", type=int, default=0,
+                    help="X product tile width of the tensor-core forms (0: timed at the first step)")
     ap.add_argument("--measure-peaks", action="store_true",
                     help="print cuBLAS FP64/FP32/TF32 GEMM rates and exit")
     ap.add_argument("--c5-runs", type=int, default=4, help="learned form: training runs")
@@ -932,7 +941,8 @@ def main():
             dist.barrier()
         t0 = time.perf_counter()
         for f in forms:
-            res[f] = run_form(B, torch, sysm, run, f, args.steps, args.warmup, flush, stream)
+            res[f] = run_form(B, torch, sysm, run, f, args.steps, args.warmup, flush, stream,
+                              x_tile=args.x_tile)
         secs["forms"] = time.perf_counter() - t0
         n2048 = None
         if not args.no_n2048:
@@ -991,6 +1001,7 @@ def main():
                    "speedup_vs_fp64": (ms64 / float(np.mean(r['ms']))) if ms64 else None,
                    "max_dipole_err_vs_fp64_au": err,
                    "forms": form_summary(res, forms, sysm.n_electrons),
+                   "x_tile": {f: res[f]["x_tile"] for f in forms if res[f]["x_tile"] > 0},
                    "kernel_ms": {f: res[f]["prof"] for f in forms},
                    "n2048": n2048,
                    "pump_probe_c4": c4,

@@ -293,6 +293,16 @@ tdb_status tdb_set_state(tdb_ctx* ctx, const void* host_buf, size_t bytes);
  * Violation returns TDB_ERR_NUMERIC and makes the context sticky. */
 tdb_status tdb_check(tdb_ctx* ctx, double tol_trace);
 
+/* Width of the X product's tiles in the tensor-core forms (FP16X6, FP16X3, BF16X3): 128, 176
+ * or 256 columns, or 0 for the default (the candidates timed at the first step, the fastest
+ * kept).  The width changes the time of a step, not its result (every output element keeps
+ * its order of accumulation).  TDB_ERR_ARG for another value or a width the product cannot
+ * take at this N, TDB_ERR_UNSUPPORTED for the other forms.  Synchronises the context. */
+tdb_status tdb_set_x_tile(tdb_ctx* ctx, int width);
+/* The X tile width in effect (0 while a context left to tune it has not stepped; -1 for
+ * NULL or a form without tensor-core products). */
+int tdb_x_tile(const tdb_ctx* ctx);
+
 /* Failure-detection probe (the paper has no counterpart: it tests this library's handling
  * of a device-side wait that gives up).  Enqueues on the context stream one kernel that
  * waits on an mbarrier nothing arrives on, polling at most `polls` times (>= 1, else

@@ -92,6 +92,8 @@ SIGNATURES = {
     "tdb_check": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     "tdb_last_launch_count": (ctypes.c_long, [ctypes.c_void_p]),
     "tdb_wait_probe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong]),
+    "tdb_set_x_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "tdb_x_tile": (ctypes.c_int, [ctypes.c_void_p]),
     "tdb_step_profiled": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_char_p), ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int)]),
     "tdb_split_gemm": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_int, _dp, _dp]),
@@ -435,6 +437,15 @@ def tdb_check(ctx: Context, tol_trace: float = 1e-10):
 def tdb_wait_probe(ctx: Context, polls: int):
     """Enqueue a kernel whose bounded device wait runs out (failure-detection probe)."""
     _check("tdb_wait_probe", load().tdb_wait_probe(ctx.handle, int(polls)))
+
+
+def tdb_set_x_tile(ctx: Context, width: int):
+    """Fix the X product's tile width (128, 176, 256), or 0 to time the candidates."""
+    _check("tdb_set_x_tile", load().tdb_set_x_tile(ctx.handle, int(width)))
+
+
+def tdb_x_tile(ctx: Context) -> int:
+    return int(load().tdb_x_tile(ctx.handle))
 
 
 def tdb_last_launch_count(ctx: Context) -> int:

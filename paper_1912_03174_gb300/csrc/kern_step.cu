@@ -812,17 +812,6 @@ __device__ __forceinline__ float2 mulliken_elem(float rh, float rl, float s) {
     const float p = rh * s;
     return make_float2(p, fmaf(rh, s, -p) + rl * s);
 }
-// Sum of the 32 element values of a tile row (column order fixed: four interleaved
-// partial sums, then combined), shared by the update and the master partials.
-__device__ __forceinline__ float2 tile_row_sum(const float2* row) {
-    float2 a[4] = {row[0], row[1], row[2], row[3]};
-#pragma unroll
-    for (int k = 4; k < kTile; k += 4)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) a[j] = df2_add(a[j], row[k + j]);
-    return df2_add(df2_add(a[0], a[1]), df2_add(a[2], a[3]));
-}
-
 // Power-of-two scale mapping a bound m into (63.5, 127] (FP32 form of tc::pscale; an
 // FP32 quotient that rounds up to a power of two gives a scale one step too large, which
 // only moves a little more of a value into its FP16 tails: the heads stay within +-127).
@@ -865,88 +854,78 @@ __device__ void field_at_f(const FieldDev& f, double t, float E[3]) {
     E[2] = a * (float)f.dir[2];
 }
 
-// Row-tile stage of the per-level evaluation (one block of 256 threads, tile r): deviation
-// charges dq_A of the tile's atoms (sums of their rows' partials in a fixed order), the
-// tile's partial potentials pv[r][A'] = sum_B gamma_A'B dq_B (eq:hscc), and its sums of
-// dq_A R_A and dq_A.
-__device__ void level_rowtile(const LevelArgs& a, int r, bool trace_only) {
-    __shared__ float2 dq_sh[kTile];
+// Counter increment with acquire-release semantics at GPU scope: after a block barrier it
+// publishes what the block wrote (release is cumulative over the barrier) and, for the block
+// that completes a count, makes what the others published visible (acquire; the barrier
+// that follows extends it to the block).  One such atomic per block replaces per-thread
+// fences, which serialise across the GPU.
+__device__ __forceinline__ int atom_add_acq_rel(int* p, int v) {
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v)
+                 : "memory");
+    return old;
+}
+
+// Evaluation of a level from its Mulliken row partials, in two kernels of one block per 32
+// atoms (eight threads per atom).
+//
+// Charges (block blk): dq_A = sum of the partials of atom A's rows (thread j of the atom
+// sums partials j, j + 8, ... in order, then the eight combine), into dq[A]; the block's
+// sums of dq_A R_A and dq_A into bsum[blk] (dipole and trace parts).
+__device__ void level_dq_block(const LevelArgs& a, int blk) {
+    __shared__ float2 red[8][4];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int apt = kTile / a.nper;
-    const int A0 = r * apt;
-    const int na = min(apt, a.nat - A0);
-    const int len = a.nper * a.nct;
-    const bool pv_on = !trace_only && a.scc;
     const float2 z = make_float2(0.f, 0.f);
-    // every load of the stage goes out first (one round trip): the row partials of this
-    // warp's first atom, gamma of this thread's first atom against the tile's atoms, and
-    // the positions of the tile's atoms
-    float2 pp[8], gv[8], rr[3] = {z, z, z};
-    {
-        const float2* p = a.partial + (size_t)(A0 + warp) * len;
+    const int A = blk * 32 + (tid >> 3), j = tid & 7;
+    const int len = a.nper * a.nct;
+    float2 s = z, r[3] = {z, z, z};
+    if (A < a.nat) {
+        const float2* p = a.partial + (size_t)A * len;
+        if (j == 0)
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
-            pp[u] = (warp < na && lane + 32 * u < len) ? ldcg2(p + lane + 32 * u) : z;
-        const float2* g = a.gam2 + (size_t)tid * a.nat + A0;
+            for (int k = 0; k < 3; ++k) r[k] = __ldg(a.R2 + 3 * A + k);
+        for (int k0 = j; k0 < len; k0 += 64) {
+            float2 v[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) gv[u] = (pv_on && tid < a.nat && u < na) ? __ldg(g + u) : z;
-        if (warp == 0 && lane < na)
+            for (int u = 0; u < 8; ++u) v[u] = k0 + 8 * u < len ? ldcg2(p + k0 + 8 * u) : z;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) rr[k] = __ldg(a.R2 + 3 * (A0 + lane) + k);
-    }
-    for (int i = warp; i < na; i += 8) {
-        float2 s = z;
-        if (i == warp) {
-#pragma unroll
-            for (int u = 0; u < 8; ++u) s = df2_add(s, pp[u]);
+            for (int u = 0; u < 8; ++u) s = df2_add(s, v[u]);
         }
-        // the rest of this atom's partials (long rows), then further atoms of this warp
-        for (int k = (i == warp ? lane + 256 : lane); k < len; k += 32)
-            s = df2_add(s, ldcg2(a.partial + (size_t)(A0 + i) * len + k));
-        s = df2_warp_sum(s);
-        if (lane == 0) dq_sh[i] = s;
     }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) s = df2_add(s, df2_shfl_xor(s, o));
+    float2 m[4] = {z, z, z, z};
+    if (A < a.nat && j == 0) {
+        a.dq[A] = s;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) m[k] = df2_mul(s, r[k]);
+        m[3] = s;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) m[k] = df2_warp_sum(m[k]);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) red[warp][k] = m[k];
     __syncthreads();
-    if (warp == 0) {
-        float2 m[4] = {};
-        if (lane < na) {
-            const float2 d = dq_sh[lane];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) m[k] = df2_mul(d, rr[k]);
-            m[3] = d;
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) m[k] = df2_warp_sum(m[k]);
-        if (lane < 4) a.part[4 * r + lane] = m[lane];
-    }
-    if (!pv_on) return;
-    for (int Ap = tid; Ap < a.nat; Ap += 256) {
-        const float2* g = a.gam2 + (size_t)Ap * a.nat + A0;
-        float2 s = z;
-        int i = 0;
-        if (Ap == tid) {
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (u < na) s = df2_add(s, df2_mul(gv[u], dq_sh[u]));
-            i = 8;
-        }
-        for (; i < na; ++i) s = df2_add(s, df2_mul(__ldg(g + i), dq_sh[i]));
-        a.pv[(size_t)r * a.nat + Ap] = s;
+    if (tid < 4) {
+        float2 t = red[0][tid];
+        for (int w = 1; w < 8; ++w) t = df2_add(t, red[w][tid]);
+        a.bsum[4 * blk + tid] = t;
     }
 }
 
-// Final stage, a kernel of its own after the tile stages (one block per 32 atoms, eight
-// threads per atom): v - v_ref per orbital (dv_f) from the tiles' partial potentials, the
-// maximum |dv| over the blocks; the block that finishes last takes Tr(rho S) and the
-// renormalisation factor of level `slot`, the FP16X6 scales of the next products, the dipole
-// mu = mu_ref - sum_A dq_A R_A into sc->mu and the history slot of step n_lvl, the field
-// record, and with step_end the step counter (to n_lvl) and the FP16X6 maxima (the new level
-// is in `slot`); it resets every counter.  trace_only (one block): only Tr(rho S) and f - 1.
-__device__ __forceinline__ int atom_add_acq_rel(int* p, int v);
-
+// Potentials and the level's scalars (block blk of nblk): dv_A = sum_B gamma_AB dq_B
+// (eq:hscc; thread j of atom A takes B = j, j + 8, ... in order, then the eight combine)
+// + R_A . E(t) + the SCC residual of rho_ref, written per orbital (dv_f), and max |dv| over
+// the blocks; the block that finishes last takes Tr(rho S) and the renormalisation factor of
+// level `slot`, the FP16X6 scales of the next products, the dipole mu = mu_ref - sum_A dq_A
+// R_A into sc->mu and the history slot of step n_lvl, the field record, and with step_end
+// the step counter (to n_lvl) and the FP16X6 maxima (the new level is in `slot`); it resets
+// the counters.  trace_only (one block): only Tr(rho S) and f - 1.
 __device__ void level_final_block(const LevelArgs& a, int slot, long long n_lvl, bool trace_only,
                                   bool step_end, int blk, int nblk) {
+    __shared__ float2 dq_sh[256];
     __shared__ float2 tot[4];
     __shared__ float E_sh[3];
     __shared__ float red[8];
@@ -955,7 +934,7 @@ __device__ void level_final_block(const LevelArgs& a, int slot, long long n_lvl,
     const int warp = tid >> 5, lane = tid & 31;
     DevScalars* sc = a.sc;
     const float2 z = make_float2(0.f, 0.f);
-    int* max_bits = a.count + a.nct + 1;     // max |dv| of this evaluation (float bits, >= 0)
+    int* max_bits = a.count + 1;     // max |dv| of this evaluation (float bits, >= 0)
     if (!trace_only) {
         if (tid == 0) {
             float E[3] = {0.f, 0.f, 0.f};
@@ -967,12 +946,7 @@ __device__ void level_final_block(const LevelArgs& a, int slot, long long n_lvl,
             E_sh[1] = E[1];
             E_sh[2] = E[2];
         }
-        // eight threads per atom, thread j of an atom summing tiles j, j + 8, ... in order
         const int A = blk * 32 + (tid >> 3), j = tid & 7;
-        float2 v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-            v[u] = (a.scc && A < a.nat && j + 8 * u < a.nct) ? ldcg2(a.pv + (size_t)(j + 8 * u) * a.nat + A) : z;
         float rx = 0.f, ry = 0.f, rz = 0.f, cr = 0.f;
         if (A < a.nat && j == 0) {
             rx = __ldg(&a.R2[3 * A].x);
@@ -981,10 +955,31 @@ __device__ void level_final_block(const LevelArgs& a, int slot, long long n_lvl,
             cr = __ldg(a.c_res + A);
         }
         float2 acc = z;
+        if (a.scc) {
+            const float2* g = a.gam2 + (size_t)(A < a.nat ? A : 0) * a.nat;
+            // chunks of 256 atoms: their charges staged in shared memory, this thread's 32
+            // products of a chunk with their gamma loads issued 16 at a time
+            for (int c0 = 0; c0 < a.nat; c0 += 256) {
+                __syncthreads();
+                dq_sh[tid] = c0 + tid < a.nat ? ldcg2(a.dq + c0 + tid) : z;
+                __syncthreads();
+                const int nb = min(256, a.nat - c0);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc = df2_add(acc, v[u]);
-        for (int r = j + 64; r < a.nct; r += 8)
-            if (a.scc && A < a.nat) acc = df2_add(acc, ldcg2(a.pv + (size_t)r * a.nat + A));
+                for (int h = 0; h < 2; ++h) {
+                    float2 gv[16];
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const int b = j + 8 * (16 * h + u);
+                        gv[u] = (A < a.nat && b < nb) ? __ldg(g + c0 + b) : z;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const int b = j + 8 * (16 * h + u);
+                        if (b < nb) acc = df2_add(acc, df2_mul(gv[u], dq_sh[b]));
+                    }
+                }
+            }
+        }
 #pragma unroll
         for (int o = 4; o > 0; o >>= 1) acc = df2_add(acc, df2_shfl_xor(acc, o));
         __syncthreads();
@@ -1002,15 +997,16 @@ __device__ void level_final_block(const LevelArgs& a, int slot, long long n_lvl,
             float m = red[0];
             for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w]);
             atomicMax(max_bits, __float_as_int(m));
-            last = atom_add_acq_rel(a.count + a.nct, 1) == nblk - 1;
+            last = atom_add_acq_rel(a.count, 1) == nblk - 1;
         }
         __syncthreads();
         if (!last) return;
     }
-    // the last block: sums of the tiles' dipole and trace parts (warps 0-3)
+    // the last block: sums of the charge blocks' dipole and trace parts (warps 0-3)
     if (warp < 4) {
+        const int nb = level_final_blocks(a.nat);
         float2 s = z;
-        for (int r = lane; r < a.nct; r += 32) s = df2_add(s, ldcg2(a.part + 4 * r + warp));
+        for (int r = lane; r < nb; r += 32) s = df2_add(s, ldcg2(a.bsum + 4 * r + warp));
         s = df2_warp_sum(s);
         if (lane == 0) tot[warp] = s;
     }
@@ -1060,41 +1056,9 @@ __device__ void level_final_block(const LevelArgs& a, int slot, long long n_lvl,
     }
     // the reset includes the maximum |dv| that thread 0 read above
     __syncthreads();
-    for (int i = tid; i <= a.nct + 1; i += 256) a.count[i] = 0;
+    if (tid < 2) a.count[tid] = 0;
 }
 
-// Counter increment with acquire-release semantics at GPU scope: after a block barrier it
-// publishes what the block wrote (release is cumulative over the barrier) and, for the block
-// that completes a count, makes what the others published visible (acquire; the barrier
-// that follows extends it to the block).  One such atomic per block replaces per-thread
-// fences, which serialise across the GPU.
-__device__ __forceinline__ int atom_add_acq_rel(int* p, int v) {
-    int old;
-    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v)
-                 : "memory");
-    return old;
-}
-
-// After a block has written its row partials: count it towards the row tiles it covered
-// (tile_target arrivals complete a tile); the block completing a tile runs the tile's stage,
-// reading what other blocks wrote through L2 (ld.global.cg).  The final stage is a kernel of
-// its own (level_final_block).
-__device__ void level_arrive(const LevelArgs& a, int t0, int t1, int tile_target, bool trace_only) {
-    __shared__ int done[2];
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    __syncthreads();
-    // the two tiles' counters by two threads at once
-    if (tid < 2) {
-        const int t = tid ? t1 : t0;
-        done[tid] = (tid == 0 || t1 != t0) ? atom_add_acq_rel(&a.count[t], 1) == tile_target - 1 : 0;
-    }
-    __syncthreads();
-    for (int k = 0; k < 2; ++k) {
-        if (!done[k]) continue;
-        level_rowtile(a, k ? t1 : t0, trace_only);
-        __syncthreads();
-    }
-}
 
 // Update of the FP32-pair master (eq:leapfrog, eq:eomrho, frozen nuclei): the same
 // tile-pair scheme and operands as k_update, with the increment factor * rhodot formed
@@ -1102,11 +1066,37 @@ __device__ void level_arrive(const LevelArgs& a, int t0, int t1, int tile_target
 // Every kRenormEvery steps the base level is first renormalised to Tr(rho S) = N_e:
 // rho_base <- f rho_base with f = 1 + eps from its trace (Sec. 2.3: the exact leapfrog
 // conserves the electron number; the reduced products do not, by ~1e-14 of N_e per step),
-// i.e. the deviation gains eps (rho_ref + deviation).  Mulliken row partials of the new deviation in FP32-pair
-// arithmetic; the last blocks evaluate the new level (level_arrive).
+// i.e. the deviation gains eps (rho_ref + deviation).  Mulliken row partials of the new
+// deviation in FP32-pair arithmetic, from which two small kernels evaluate the new level
+// (level_dq_block, level_final_block).
 // Steps between renormalisations of a leapfrog level (the reduced forms drift by ~1e-14 of
 // N_e per step, so Tr(rho S) stays within ~1e-12 of N_e in between).
 constexpr int kRenormEvery = 8;
+
+// Asynchronous 4-byte copy global -> shared (cp.async; src_size 0 fills zero), its group
+// commit and wait.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src),
+                 "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
+}
+
+// Shared memory of the update: the X parts of both tiles ([part][tile][row][col], rows
+// padded for transposed reads) and the second half's six operand arrays.
+__host__ __device__ inline int update_smem_bytes(int nparts) {
+    return (nparts * 2 * kTile * (kTile + 1) + 6 * kTile * kTile) * (int)sizeof(float);
+}
+
+// Row partials of one tile row: the 32 element values of a warp's lanes (lane = column),
+// summed by a butterfly (every lane ends with the same value); shared by the update and the
+// master partials.
+__device__ __forceinline__ float2 tile_row_sum_warp(float2 v) { return df2_warp_sum(v); }
 
 __device__ __forceinline__ void update_df_block(const UpdateDfArgs& A, int b) {
     const int N = A.N, nct = A.nct;
@@ -1114,21 +1104,69 @@ __device__ __forceinline__ void update_df_block(const UpdateDfArgs& A, int b) {
     const MasterPtrs& out = A.out;
     const float fh = A.fh, fl = A.fl;
     const double factor = A.factor;
-    const float* __restrict__ Sf = A.Sf;
-    const float* __restrict__ rgs = A.rgs;
     DevScalars* __restrict__ sc = A.sc;
     const UpdateOperands& ops = A.ops;
-    const LevelArgs& lv = A.lv;
-    const int out_slot = A.out_slot;
     // one block per tile pair bi <= bj: block b = bj (bj + 1) / 2 + bi
     int bj = (int)((sqrtf(8.0f * (float)b + 1.0f) - 1.0f) * 0.5f);
     while (bj * (bj + 1) / 2 > b) --bj;
     while ((bj + 1) * (bj + 2) / 2 <= b) ++bj;
     const int bi = b - bj * (bj + 1) / 2;
     constexpr int RPT = kTile / 8;
+    constexpr int XT = kTile * (kTile + 1), BT = kTile * kTile;
+    extern __shared__ float upd_smem[];
+    const int np = ops.nre + ops.nim;
+    float* xs = upd_smem;                   // [np][2][kTile][kTile + 1]: tile 0 (bi,bj), 1 (bj,bi)
+    float* bs = upd_smem + np * 2 * XT;     // [6][kTile][kTile]: second half's operands
     __shared__ float s_bound;
     __shared__ float eps_sh;
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const bool two = bi != bj;
+    // every load of the block goes out first: the X parts and the second half's operands
+    // as asynchronous copies, the first half's operands into registers
+    for (int q = 0; q < np; ++q) {
+        const float* src = q < ops.nre ? ops.xre[q] : ops.xim[q - ops.nre];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int tr = t ? bj : bi, tc = t ? bi : bj;
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                const int y = ty + 8 * k, r = tr * kTile + y, c = tc * kTile + tx;
+                const bool ok = r < N && c < N;
+                cp_async4(xs + (q * 2 + t) * XT + y * (kTile + 1) + tx, src + (ok ? (size_t)r * N + c : 0), ok);
+            }
+        }
+    }
+    cp_async_commit();
+    if (two) {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int y = ty + 8 * k, r = bj * kTile + y, c = bi * kTile + tx;
+            const bool ok = r < N && c < N;
+            const size_t i = ok ? (size_t)r * N + c : 0;
+            float* d = bs + y * kTile + tx;
+            cp_async4(d, base.re_hi + i, ok);
+            cp_async4(d + BT, base.re_lo + i, ok);
+            cp_async4(d + 2 * BT, base.im_hi + i, ok);
+            cp_async4(d + 3 * BT, base.im_lo + i, ok);
+            cp_async4(d + 4 * BT, A.Sf + i, ok);
+        }
+    }
+    cp_async_commit();
+    float brh[RPT], brl[RPT], bih[RPT], bil[RPT], sv[RPT], gv[RPT];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int r = bi * kTile + ty + 8 * k, c = bj * kTile + tx;
+        brh[k] = brl[k] = bih[k] = bil[k] = sv[k] = gv[k] = 0.f;
+        if (r < N && c < N) {
+            const size_t i = (size_t)r * N + c;
+            brh[k] = base.re_hi[i];
+            brl[k] = base.re_lo[i];
+            bih[k] = base.im_hi[i];
+            bil[k] = base.im_lo[i];
+            sv[k] = A.Sf[i];
+        }
+    }
+    if (tx == 0 && ty == 0) {
         // both leapfrog chains are renormalised once every kRenormEvery steps
         const long long n = sc->step;
         eps_sh = (n % kRenormEvery) < 2 ? sc->eps_lvl[ops.base_slot] : 0.f;
@@ -1146,52 +1184,51 @@ __device__ __forceinline__ void update_df_block(const UpdateDfArgs& A, int b) {
     __syncthreads();
     const float op_scale = ops.dyn ? s_bound : ops.scale;
     const float eps = eps_sh;
-    __shared__ float xr_ij[kTile][kTile + 1], xi_ij[kTile][kTile + 1];
-    __shared__ float xr_ji[kTile][kTile + 1], xi_ji[kTile][kTile + 1];
-    __shared__ float2 pv_s[kTile][kTile + 1];
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    // X = sum of its partial products, in a fixed order (all loads issued first)
-    auto load_x = [&](size_t i, float& a, float& b) {
-        float t[6];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) t[q] = q < ops.nre ? ops.xre[q][i] : 0.f;
-#pragma unroll
-        for (int q = 0; q < 2; ++q) t[4 + q] = q < ops.nim ? ops.xim[q][i] : 0.f;
-        a = ((t[0] + t[1]) + t[2]) + t[3];
-        b = t[4] + t[5];
-    };
-#pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-        const int y = ty + 8 * k;
-        int r = bi * kTile + y, c = bj * kTile + tx;
-        float a = 0.f, b = 0.f;
-        if (r < N && c < N) load_x((size_t)r * N + c, a, b);
-        xr_ij[y][tx] = a;
-        xi_ij[y][tx] = b;
-        r = bj * kTile + y;
-        c = bi * kTile + tx;
-        a = b = 0.f;
-        if (r < N && c < N) load_x((size_t)r * N + c, a, b);
-        xr_ji[y][tx] = a;
-        xi_ji[y][tx] = b;
-    }
-    __syncthreads();
-    float dmax = 0.f;
-    for (int half = 0; half < (bi == bj ? 1 : 2); ++half) {
-        const int ti = half ? bj : bi, tj = half ? bi : bj;
-        float brh[RPT], brl[RPT], bih[RPT], bil[RPT], sv[RPT], gv[RPT];
+    // renormalisation steps: rho_ref of both halves (the second one asynchronously)
+    if (eps != 0.f) {
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
-            const int r = ti * kTile + ty + 8 * k, c = tj * kTile + tx;
-            brh[k] = brl[k] = bih[k] = bil[k] = sv[k] = gv[k] = 0.f;
-            if (r < N && c < N) {
-                const size_t i = (size_t)r * N + c;
-                brh[k] = base.re_hi[i];
-                brl[k] = base.re_lo[i];
-                bih[k] = base.im_hi[i];
-                bil[k] = base.im_lo[i];
-                sv[k] = Sf[i];
-                if (eps != 0.f) gv[k] = rgs[i];
+            const int r = bi * kTile + ty + 8 * k, c = bj * kTile + tx;
+            if (r < N && c < N) gv[k] = A.rgs[(size_t)r * N + c];
+        }
+        if (two)
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                const int y = ty + 8 * k, r = bj * kTile + y, c = bi * kTile + tx;
+                const bool ok = r < N && c < N;
+                cp_async4(bs + 5 * BT + y * kTile + tx, A.rgs + (ok ? (size_t)r * N + c : 0), ok);
+            }
+    }
+    cp_async_commit();
+    cp_async_wait<2>();                      // the X parts (this thread's copies) ...
+    __syncthreads();                         // ... and everyone's
+    // X = sum of its partial products in a fixed order: Re ((x0 + x1) + x2) + x3, Im x4 + x5
+    auto x_re = [&](int t, int y, int x) {
+        const float* p = xs + t * XT + y * (kTile + 1) + x;
+        float a = p[0];
+        for (int q = 1; q < ops.nre; ++q) a = a + p[q * 2 * XT];
+        return a;
+    };
+    auto x_im = [&](int t, int y, int x) {
+        const float* p = xs + (ops.nre * 2 + t) * XT + y * (kTile + 1) + x;
+        float a = p[0];
+        for (int q = 1; q < ops.nim; ++q) a = a + p[q * 2 * XT];
+        return a;
+    };
+    float dmax = 0.f;
+    for (int half = 0; half < (two ? 2 : 1); ++half) {
+        const int ti = half ? bj : bi, tj = half ? bi : bj;
+        if (half) {
+            cp_async_wait<0>();              // this thread's own copies of the second half
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                const int o = (ty + 8 * k) * kTile + tx;
+                brh[k] = bs[o];
+                brl[k] = bs[o + BT];
+                bih[k] = bs[o + 2 * BT];
+                bil[k] = bs[o + 3 * BT];
+                sv[k] = bs[o + 4 * BT];
+                gv[k] = eps != 0.f ? bs[o + 5 * BT] : 0.f;
             }
         }
 #pragma unroll
@@ -1200,18 +1237,9 @@ __device__ __forceinline__ void update_df_block(const UpdateDfArgs& A, int b) {
             const int r = ti * kTile + y, c = tj * kTile + tx;
             float2 pv = make_float2(0.f, 0.f);
             if (r < N && c < N) {
-                float x_ij_re, x_ij_im, x_ji_re, x_ji_im;
-                if (!half) {
-                    x_ij_re = xr_ij[y][tx];
-                    x_ij_im = xi_ij[y][tx];
-                    x_ji_re = xr_ji[tx][y];
-                    x_ji_im = xi_ji[tx][y];
-                } else {
-                    x_ij_re = xr_ji[y][tx];
-                    x_ij_im = xi_ji[y][tx];
-                    x_ji_re = xr_ij[tx][y];
-                    x_ji_im = xi_ij[tx][y];
-                }
+                // tile `half` holds X_ij, the other X_ji (read transposed)
+                const float x_ij_re = x_re(half, y, tx), x_ij_im = x_im(half, y, tx);
+                const float x_ji_re = x_re(half ^ 1, tx, y), x_ji_im = x_im(half ^ 1, tx, y);
                 // rhodot = -i (X - X^dagger); the (j,i) element repeats these operations on
                 // the swapped operands, so the master stays exactly Hermitian
                 const float dre = x_ij_im + x_ji_im;
@@ -1260,25 +1288,24 @@ __device__ __forceinline__ void update_df_block(const UpdateDfArgs& A, int b) {
                     }
                 }
             }
-            pv_s[y][tx] = pv;
+            // Mulliken partial of row r over this column tile (lanes = columns)
+            const float2 sum = tile_row_sum_warp(pv);
+            if (tx == 0 && r < N) const_cast<float2*>(A.lv.partial)[(size_t)r * nct + tj] = sum;
         }
-        __syncthreads();
-        if (ty == 0) {
-            const int r = ti * kTile + tx;
-            const float2 sum = tile_row_sum(pv_s[tx]);
-            if (r < N) const_cast<float2*>(lv.partial)[(size_t)r * nct + tj] = sum;
-        }
-        __syncthreads();
     }
     if (ops.dyn) {
+        // one atomic per block (the warps' maxima through shared memory)
+        __shared__ float wmax[8];
         for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-        if (tx == 0)
+        if (tx == 0) wmax[ty] = dmax;
+        __syncthreads();
+        if (tx == 0 && ty == 0) {
+            for (int w = 1; w < 8; ++w) dmax = fmaxf(dmax, wmax[w]);
             atomicMax(reinterpret_cast<unsigned long long*>(&ops.dyn->max_drho[2]),
                       (unsigned long long)__double_as_longlong((double)dmax));
-        if (bi == 0 && bj == 0 && tx == 0 && ty == 0) ops.dyn->s_rho = op_scale;
+            if (bi == 0 && bj == 0) ops.dyn->s_rho = op_scale;
+        }
     }
-    __syncthreads();
-    level_arrive(lv, bi, bj, nct, false);
 }
 
 __global__ void __launch_bounds__(256, 4) k_update_df(UpdateDfArgs a) { update_df_block(a, blockIdx.x); }
@@ -1289,14 +1316,17 @@ __global__ void __launch_bounds__(256, 4)
     update_df_block(args[w.x], w.y);
 }
 
-// Per-level evaluation outside a step: block r runs the row-tile stage of tile r and the
-// block completing the last tile the final stage (the arithmetic of the update's tail).
-__global__ void __launch_bounds__(256) k_level(LevelArgs lv, int trace_only) {
-    level_arrive(lv, blockIdx.x, blockIdx.x, 1, trace_only != 0);
+// The charges of a level (after an update, or of the current level outside a step).
+__global__ void __launch_bounds__(256) k_level_dq(LevelArgs lv) { level_dq_block(lv, blockIdx.x); }
+
+__global__ void __launch_bounds__(256)
+    k_level_dq_grouped(const LevelFinalArgs* __restrict__ args, const int2* __restrict__ work) {
+    const int2 w = work[blockIdx.x];
+    level_dq_block(args[w.x].lv, w.y);
 }
 
-// The final stage of a level evaluation: after an update (step_end, the new level n + 1 in
-// slot) or after the tile stages of k_level (the current level).
+// The potentials and scalars of a level after k_level_dq: after an update (step_end, the new
+// level n + 1 in slot) or of the current level.
 __global__ void __launch_bounds__(256) k_level_final(LevelArgs lv, int slot, int trace_only, int step_end) {
     const long long n_lvl = lv.sc->step + (step_end ? 1 : 0);
     level_final_block(lv, slot, n_lvl, trace_only != 0, step_end != 0, blockIdx.x, gridDim.x);
@@ -1359,9 +1389,10 @@ __global__ void k_master_to_view(size_t n, MasterPtrs m, const double* __restric
 // k_update_df (exact high products, FP32-pair sums in the same column order)
 __global__ void k_master_partials(int N, int nct, MasterPtrs m, const float* __restrict__ Sf,
                                   float2* __restrict__ partial) {
-    __shared__ float2 pv_s[kTile][kTile + 1];
     const int ct = blockIdx.x;
     const int col = ct * kTile + threadIdx.x;
+    // warp y takes rows y, y + 8, ... of the row tile, its lanes the columns (the order of
+    // the update's row sums)
     for (int y = threadIdx.y; y < kTile; y += blockDim.y) {
         const int row = blockIdx.y * kTile + y;
         float2 v = make_float2(0.f, 0.f);
@@ -1369,13 +1400,8 @@ __global__ void k_master_partials(int N, int nct, MasterPtrs m, const float* __r
             const size_t i = (size_t)row * N + col;
             v = mulliken_elem(m.re_hi[i], m.re_lo[i], Sf[i]);
         }
-        pv_s[y][threadIdx.x] = v;
-    }
-    __syncthreads();
-    if (threadIdx.y == 0) {
-        const int row = blockIdx.y * kTile + threadIdx.x;
-        const float2 sum = tile_row_sum(pv_s[threadIdx.x]);
-        if (row < N) partial[(size_t)row * nct + ct] = sum;
+        const float2 sum = tile_row_sum_warp(v);
+        if (threadIdx.x == 0 && row < N) partial[(size_t)row * nct + ct] = sum;
     }
 }
 
@@ -1454,22 +1480,40 @@ UpdateDfArgs update_df_args(const Ctx& c, const MasterPtrs& base, const MasterPt
     return a;
 }
 
+cudaError_t prepare_update() {
+    // up to six X parts (two K slices)
+    const int bytes = update_smem_bytes(6);
+    cudaError_t e = cudaFuncSetAttribute(k_update_df, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_update_df_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+
 void launch_update_df(const Ctx& c, const MasterPtrs& base, const MasterPtrs& out, double factor,
                       DevScalars* sc, const UpdateOperands& ops, const LevelArgs& lv,
                       cudaStream_t st) {
-    k_update_df<<<c.nct * (c.nct + 1) / 2, dim3(kTile, 8), 0, st>>>(
+    k_update_df<<<c.nct * (c.nct + 1) / 2, dim3(kTile, 8), update_smem_bytes(ops.nre + ops.nim), st>>>(
         update_df_args(c, base, out, factor, sc, ops, lv));
 }
 
 void launch_update_df_grouped(const UpdateDfArgs* args, const int2* work, int nwork,
-                              cudaStream_t st) {
-    k_update_df_grouped<<<nwork, dim3(kTile, 8), 0, st>>>(args, work);
+                              int max_parts, cudaStream_t st) {
+    k_update_df_grouped<<<nwork, dim3(kTile, 8), update_smem_bytes(max_parts), st>>>(args, work);
 }
 
 void launch_level(const Ctx& c, const LevelArgs& lv, int slot, int trace_only, cudaStream_t st) {
-    k_level<<<c.nct, dim3(kTile, 8), 0, st>>>(lv, trace_only);
+    k_level_dq<<<level_final_blocks(c.nat), dim3(kTile, 8), 0, st>>>(lv);
     k_level_final<<<trace_only ? 1 : level_final_blocks(c.nat), dim3(kTile, 8), 0, st>>>(
         lv, slot, trace_only, 0);
+}
+
+void launch_level_dq(const Ctx& c, const LevelArgs& lv, cudaStream_t st) {
+    k_level_dq<<<level_final_blocks(c.nat), dim3(kTile, 8), 0, st>>>(lv);
+}
+
+void launch_level_dq_grouped(const LevelFinalArgs* args, const int2* work, int nwork,
+                             cudaStream_t st) {
+    k_level_dq_grouped<<<nwork, dim3(kTile, 8), 0, st>>>(args, work);
 }
 
 void launch_level_final(const Ctx& c, const LevelArgs& lv, int slot, cudaStream_t st) {

@@ -540,12 +540,17 @@ cudaError_t prepare() {
     return e;
 }
 
+bool launchable(int scheme, const GemmParams& p, int nparts, int bn) {
+    if (nparts < 1 || nparts > kMaxParts || (bn != 64 && bn != 128 && bn != 176 && bn != 256))
+        return false;
+    for (int z = 0; z < nparts; ++z)
+        if (p.part[z].K < 1 || tmem_cols(scheme, p.part[z].K, bn) > 512) return false;
+    return true;
+}
+
 cudaError_t launch(int scheme, const Maps& m, const GemmParams& p, int nparts, cudaStream_t st,
                    int bn) {
-    if (nparts < 1 || nparts > kMaxParts || (bn != 64 && bn != 128 && bn != 176 && bn != 256))
-        return cudaErrorInvalidValue;
-    for (int z = 0; z < nparts; ++z)
-        if (p.part[z].K < 1 || tmem_cols(scheme, p.part[z].K, bn) > 512) return cudaErrorInvalidValue;
+    if (!launchable(scheme, p, nparts, bn)) return cudaErrorInvalidValue;
     dim3 grid((p.N + bn - 1) / bn, (p.M + BM - 1) / BM, nparts);
     if (bn == 64) {
         if (scheme == kHiLo)

@@ -177,10 +177,10 @@ size_t carve(Ctx& c, char* base) {
         c.rref_f = k.take<float>(NN);
         c.gam2 = k.take<float2>(nat * nat);
         c.R2 = k.take<float2>(3 * nat);
-        c.lv_pv = k.take<float2>((size_t)c.nct * nat);
-        c.lv_part = k.take<float2>(4 * (size_t)c.nct);
+        c.lv_dq = k.take<float2>(nat);
+        c.lv_bsum = k.take<float2>(4 * (size_t)level_final_blocks(nat));
         c.c_res = k.take<float>(nat);
-        c.lv_count = k.take<int>((size_t)c.nct + 2);
+        c.lv_count = k.take<int>(2);
     }
     if (mixed(c)) {
         c.dv_f = k.take<float>(N);
@@ -543,8 +543,8 @@ LevelArgs level_args(Ctx& c) {
     a.gam2 = c.gam2;
     a.R2 = c.R2;
     a.c_res = c.c_res;
-    a.pv = c.lv_pv;
-    a.part = c.lv_part;
+    a.dq = c.lv_dq;
+    a.bsum = c.lv_bsum;
     a.dv_f = c.dv_f;
     a.dyn = head3(c) ? c.dyn : nullptr;
     a.has_scales = head3(c) ? 1 : 0;
@@ -615,6 +615,7 @@ tdb_status materialize(Ctx& c) {
 // and the dipole of rho_ref (host FP64, once).
 tdb_status setup_level_constants(Ctx& c) {
     const int nat = c.nat, N = c.N;
+    CK(prepare_update());
     std::vector<double> g((size_t)nat * nat), qb(nat), vref(N), q0v(nat);
     DevScalars h{};
     CK(cudaMemcpyAsync(g.data(), c.gamma, sizeof(double) * g.size(), cudaMemcpyDeviceToHost, c.stream));
@@ -648,7 +649,7 @@ tdb_status setup_level_constants(Ctx& c) {
     CK(cudaMemcpyAsync(c.gam2, g2.data(), sizeof(float2) * g2.size(), cudaMemcpyHostToDevice, c.stream));
     CK(cudaMemcpyAsync(c.R2, r2.data(), sizeof(float2) * r2.size(), cudaMemcpyHostToDevice, c.stream));
     CK(cudaMemcpyAsync(c.c_res, cres.data(), sizeof(float) * nat, cudaMemcpyHostToDevice, c.stream));
-    CK(cudaMemsetAsync(c.lv_count, 0, sizeof(int) * ((size_t)c.nct + 2), c.stream));
+    CK(cudaMemsetAsync(c.lv_count, 0, sizeof(int) * 2, c.stream));
     CK(cudaMemcpyAsync(c.sc, &h, sizeof h, cudaMemcpyHostToDevice, c.stream));
     CK(cudaStreamSynchronize(c.stream));
     return TDB_OK;
@@ -710,11 +711,11 @@ tdb_status setup_tensor(Ctx& c) {
 // 768 < N <= 1024 (one K slice) 176-wide tiles give 3 parts x 8 x 6 = 144 CTAs, one wave
 // on the 152 SMs (256-wide tiles: 96).
 // tune_x replaces this starting guess by the measured fastest width.
-int xbn(const Ctx& c) {
-    if (c.x_bn) return c.x_bn;
-    if (c.N > 768 && c.N <= 1024) return 176;
-    return c.N >= 512 ? 256 : 128;
+int default_xbn(int N) {
+    if (N > 768 && N <= 1024) return 176;
+    return N >= 512 ? 256 : 128;
 }
+int xbn(const Ctx& c) { return c.x_bn ? c.x_bn : default_xbn(c.N); }
 
 // Tensor maps of the X product's operands for B tiles of width bn.
 bool make_x_maps(const Ctx& c, int bn, tc::Maps& m) {
@@ -1141,9 +1142,11 @@ tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* t
         MARK("update");
         launch_update_df(c, ts.upd.base, ts.upd.out, factor, c.sc, ts.upd.ops, ts.upd.lv, c.stream);
         ++n;
+        MARK("level_dq");
+        launch_level_dq(c, ts.upd.lv, c.stream);
         MARK("level");
         launch_level_final(c, ts.upd.lv, ts.upd.out_slot, c.stream);
-        ++n;
+        n += 2;
     } else {
         const int N = c.N;
         // delta M = S^-1 delta H (left half of [dM | M]), M = M_gs + delta M (right half)
@@ -1170,9 +1173,11 @@ tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* t
         launch_update_df(c, euler ? c.ms[cur] : c.ms[prv], c.ms[prv], factor, c.sc, ops,
                          level_args(c), c.stream);
         ++n;
+        MARK("level_dq");
+        launch_level_dq(c, level_args(c), c.stream);
         MARK("level");
         launch_level_final(c, level_args(c), prv, c.stream);
-        ++n;
+        n += 2;
     }
     MARK("end");
     CKL();
@@ -2226,6 +2231,40 @@ tdb_status tdb_wait_probe(tdb_ctx* c, long long polls) {
     return TDB_OK;
 }
 
+tdb_status tdb_set_x_tile(tdb_ctx* c, int width) {
+    TRY(check_ctx(c, false, false));
+    if (!tensor(*c)) {
+        set_err("tdb_set_x_tile: the form has no tensor-core products");
+        return TDB_ERR_UNSUPPORTED;
+    }
+    if (width != 0 && width != 128 && width != 176 && width != 256) {
+        set_err("tdb_set_x_tile: width must be 0, 128, 176 or 256");
+        return TDB_ERR_ARG;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    const int bn = width ? width : 0;
+    tc::Maps m{};
+    tc::GemmParams x{};
+    const int probe = bn ? bn : default_xbn(c->N);
+    if (!make_x_maps(*c, probe, m) || !tc::launchable(c->scheme, x, x_params(*c, probe, x), probe)) {
+        set_err("tdb_set_x_tile: width %d cannot be used at N = %d", probe, c->N);
+        return TDB_ERR_ARG;
+    }
+    for (int g = 0; g < 2; ++g)
+        if (c->graph[g]) {
+            cudaGraphExecDestroy(c->graph[g]);
+            c->graph[g] = nullptr;
+        }
+    c->x_bn = bn;
+    c->maps_x = m;
+    return TDB_OK;
+}
+
+int tdb_x_tile(const tdb_ctx* c) {
+    if (!c || !tensor(*c)) return -1;
+    return c->x_bn;
+}
+
 tdb_status tdb_step_profiled(tdb_ctx* c, double* ms, const char** names, int cap, int* n_out) {
     TRY(check_ctx(c, true, false));
     if (!ms || !n_out || cap < 1) {
@@ -2317,6 +2356,7 @@ struct tdb_batch {
     LevelFinalArgs* d_fin[2] = {};
     int2 *w_split = nullptr, *w_dm = nullptr, *w_x = nullptr, *w_upd = nullptr, *w_fin = nullptr;
     int n_split = 0, n_dm = 0, n_x = 0, n_upd = 0, n_fin = 0;
+    int upd_parts = 1;                 // largest nre + nim of the contexts' updates
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
 };
 
@@ -2370,6 +2410,7 @@ tdb_status batch_layout(tdb_batch& b, int bn, int schedule) {
             dm[g].push_back(grouped(c.maps_dm, ts.dm, c.N, 64, 1));
             xg[g].push_back(grouped(mx, ts.x, c.N, bn, ts.x_parts));
             upd[g].push_back(ts.upd);
+            b.upd_parts = std::max(b.upd_parts, ts.upd.ops.nre + ts.upd.ops.nim);
             LevelFinalArgs f{};
             f.lv = ts.upd.lv;
             f.slot = ts.upd.out_slot;
@@ -2432,12 +2473,13 @@ tdb_status batch_layout(tdb_batch& b, int bn, int schedule) {
     return TDB_OK;
 }
 
-// One grouped step of global parity g: four launches over all contexts.
+// One grouped step of global parity g: six launches over all contexts.
 tdb_status batch_enqueue(tdb_batch& b, int g) {
     tc::launch_split_dham_grouped(b.scheme, b.d_split[g], b.w_split, b.n_split, b.stream);
     CK(tc::launch_grouped(b.scheme, b.d_dm[g], b.w_dm, b.n_dm, b.stream, 64));
     CK(tc::launch_grouped(b.scheme, b.d_x[g], b.w_x, b.n_x, b.stream, b.x_bn));
-    launch_update_df_grouped(b.d_upd[g], b.w_upd, b.n_upd, b.stream);
+    launch_update_df_grouped(b.d_upd[g], b.w_upd, b.n_upd, b.upd_parts, b.stream);
+    launch_level_dq_grouped(b.d_fin[g], b.w_fin, b.n_fin, b.stream);
     launch_level_final_grouped(b.d_fin[g], b.w_fin, b.n_fin, b.stream);
     CKL();
     return TDB_OK;
@@ -2572,7 +2614,7 @@ tdb_status tdb_batch_create(tdb_ctx* const* ctxs, int count, tdb_batch** out) {
         set_err("tdb_batch_create: stream or event creation failed");
         st = TDB_ERR_CUDA;
     }
-    if (st == TDB_OK && tc::prepare() != cudaSuccess) {
+    if (st == TDB_OK && (tc::prepare() != cudaSuccess || prepare_update() != cudaSuccess)) {
         cudaGetLastError();
         set_err("tdb_batch_create: kernel attributes");
         st = TDB_ERR_CUDA;
@@ -2639,7 +2681,7 @@ tdb_status tdb_batch_step(tdb_batch* b, long n) {
             c->cur ^= 1;
             c->n += 1;
             c->view_valid = false;
-            c->last_launches = 5;
+            c->last_launches = 6;
         }
     }
     CK(cudaEventRecord(b->ev, b->stream));

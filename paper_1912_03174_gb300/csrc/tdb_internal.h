@@ -58,13 +58,13 @@ struct LevelArgs {
     const float2* gam2;        // [nat][nat] gamma as (hi, lo)
     const float2* R2;          // [nat][3] positions as (hi, lo)
     const float* c_res;        // [nat] (gamma dq(rho_ref))_A - v_ref_A: SCC residual of rho_ref
-    float2* pv;                // [nct][nat] partial potentials of the row tiles
-    float2* part;              // [nct][4] per tile: sum dq R_x, R_y, R_z, sum dq
+    float2* dq;                // [nat] deviation charges of the level (written by k_level_dq)
+    float2* bsum;              // [level_final_blocks][4] per block of 32 atoms: sum dq R_x, R_y, R_z, sum dq
     float* dv_f;               // [N] v - v_ref per orbital (written by the final stage)
     tc::DynScales* dyn;        // FP16X6 scales (may be null)
     DevScalars* sc;
     double* hist;
-    int* count;                // [nct + 2] tile and block counters and max |dv| bits, zero between steps
+    int* count;                // [2] final-stage arrivals, max |dv| (float bits); zero between evaluations
     float inv_ne;              // 1 / N_e
     int has_scales;            // write s_dh, s_dm from max |dv| (FP16X6)
 };
@@ -127,7 +127,7 @@ struct Ctx {
     float *dM_f = nullptr, *M_f = nullptr;           // delta M, M = M_gs + delta M
     float *Xre_f = nullptr, *Xim_f = nullptr;
     // per-level evaluation of the reduced forms (LevelArgs)
-    float2 *gam2 = nullptr, *R2 = nullptr, *lv_pv = nullptr, *lv_part = nullptr;
+    float2 *gam2 = nullptr, *R2 = nullptr, *lv_dq = nullptr, *lv_bsum = nullptr;
     float* c_res = nullptr;
     int* lv_count = nullptr;
 
@@ -267,24 +267,31 @@ UpdateDfArgs update_df_args(const Ctx& c, const MasterPtrs& base, const MasterPt
                             double factor, DevScalars* sc, const UpdateOperands& ops,
                             const LevelArgs& lv);
 // Updates of many contexts in one launch: block b runs tile pair work[b].y of args[work[b].x].
+// max_parts: the largest number of X partial products (nre + nim) among the contexts.
 void launch_update_df_grouped(const UpdateDfArgs* args, const int2* work, int nwork,
-                              cudaStream_t st);
+                              int max_parts, cudaStream_t st);
 // The update of the reduced forms also renormalises its base level (f = N_e / Tr(rho S))
-// and, in its last blocks, evaluates the new level (LevelArgs) for the next step.
+// and writes the Mulliken row partials of the new level (LevelArgs::partial); the level
+// itself is evaluated by launch_level_dq and launch_level_final after it.
+// Shared-memory opt-in of the update kernels (once per process; before their first launch).
+cudaError_t prepare_update();
 void launch_update_df(const Ctx& c, const MasterPtrs& base, const MasterPtrs& out, double factor,
                       DevScalars* sc, const UpdateOperands& ops, const LevelArgs& lv,
                       cudaStream_t st);
 // Evaluation of the current level outside a step (after a ground state, kick, field change or
-// state load), with the arithmetic of the update's tail; trace_only: only Tr(rho S) and the
+// state load), the two kernels of a step's evaluation; trace_only: only Tr(rho S) and the
 // renormalisation factor of level `slot` (partials of that level in lv.partial).
 void launch_level(const Ctx& c, const LevelArgs& lv, int slot, int trace_only, cudaStream_t st);
-// The final stage of the level evaluation after an update (the new level in slot).
+// The level after an update (the new level in slot): charges, then potentials and scalars.
 __host__ __device__ inline int level_final_blocks(int nat) { return (nat + 31) / 32; }
+void launch_level_dq(const Ctx& c, const LevelArgs& lv, cudaStream_t st);
 void launch_level_final(const Ctx& c, const LevelArgs& lv, int slot, cudaStream_t st);
 struct LevelFinalArgs {
     LevelArgs lv;
     int slot, pad;
 };
+void launch_level_dq_grouped(const LevelFinalArgs* args, const int2* work, int nwork,
+                             cudaStream_t st);
 void launch_level_final_grouped(const LevelFinalArgs* args, const int2* work, int nwork,
                                 cudaStream_t st);
 void launch_view_to_master(const Ctx& c, const double* rre, const double* rim, const MasterPtrs& m,

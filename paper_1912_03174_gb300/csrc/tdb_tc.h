@@ -67,6 +67,8 @@ cudaError_t prepare();
 // Output tiles of 128 x bn (bn = 64, 128, 176 or 256; the B maps must have bn-row boxes); nparts <=
 // kMaxParts.  kHead3 needs (ceil(K / kHeadK) + 1) bn <= 512 TMEM columns for every part
 // (cudaErrorInvalidValue otherwise).
+// Whether launch() accepts these parts at tile width bn (sizes, accumulator columns).
+bool launchable(int scheme, const GemmParams& p, int nparts, int bn);
 cudaError_t launch(int scheme, const Maps& m, const GemmParams& p, int nparts, cudaStream_t st,
                    int bn = 128);
 

@@ -446,3 +446,33 @@ def test_a_bounded_device_wait_that_runs_out_makes_the_context_sticky(B):
         p.setup()
         p.step(5)
         assert p.observables()["step"] == 5
+
+
+def test_the_x_tile_width_changes_the_time_not_the_result(B):
+    # every output element of the X product keeps its order of accumulation whatever the
+    # tile width, so trajectories with 128-, 176- and 256-wide tiles agree bit for bit
+    sysm = I.small_flake(256, seed=7)
+    run = I.Run(dt=0.2, n_steps=0, scc=True, kick=1e-3, kT=I.SCC_KT)
+    got = {}
+    for w in (128, 176, 256, 0):
+        with B.Propagator(sysm, run, "fp16x6") as p:
+            p.setup()
+            B.tdb_set_x_tile(p.ctx, w)
+            assert B.tdb_x_tile(p.ctx) == w
+            p.step(40)
+            if w == 0:
+                assert B.tdb_x_tile(p.ctx) in (128, 176, 256)   # tuned at the first steps
+            got[w] = (B.tdb_get_rho(p.ctx), B.tdb_dipole_history(p.ctx, 40))
+    for w in (176, 256, 0):
+        assert np.array_equal(got[w][0], got[128][0])
+        assert np.array_equal(got[w][1], got[128][1])
+    with B.Propagator(sysm, run, "fp16x6") as p:
+        for bad in (64, 100, -1):
+            with pytest.raises(B.TdbError) as e:
+                B.tdb_set_x_tile(p.ctx, bad)
+            assert e.value.status == 1
+    with B.Propagator(I.small_flake(10, seed=3), run, "fp64") as p:
+        with pytest.raises(B.TdbError) as e:
+            B.tdb_set_x_tile(p.ctx, 128)
+        assert e.value.status == 10
+        assert B.tdb_x_tile(p.ctx) == -1
