@@ -5,6 +5,7 @@
 
 #include <cuda_fp16.h>
 
+#include "pdl.cuh"
 #include "tdb_internal.h"
 
 namespace tdb {
@@ -812,6 +813,17 @@ __device__ __forceinline__ float2 mulliken_elem(float rh, float rl, float s) {
     const float p = rh * s;
     return make_float2(p, fmaf(rh, s, -p) + rl * s);
 }
+// Sum of the 32 element values of a tile row (column order fixed: four interleaved
+// partial sums, then combined), shared by the update and the master partials.
+__device__ __forceinline__ float2 tile_row_sum(const float2* row) {
+    float2 a[4] = {row[0], row[1], row[2], row[3]};
+#pragma unroll
+    for (int k = 4; k < kTile; k += 4)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a[j] = df2_add(a[j], row[k + j]);
+    return df2_add(df2_add(a[0], a[1]), df2_add(a[2], a[3]));
+}
+
 // Power-of-two scale mapping a bound m into (63.5, 127] (FP32 form of tc::pscale; an
 // FP32 quotient that rounds up to a power of two gives a scale one step too large, which
 // only moves a little more of a value into its FP16 tails: the heads stay within +-127).
@@ -866,177 +878,134 @@ __device__ __forceinline__ int atom_add_acq_rel(int* p, int v) {
     return old;
 }
 
-// Evaluation of a level from its Mulliken row partials, in two kernels of one block per 32
-// atoms (eight threads per atom).
+// Evaluation of a level from its Mulliken row partials, in two kernels of one block per
+// kLvAtoms atoms (64 threads, two warps, per atom).
 //
-// Charges (block blk): dq_A = sum of the partials of atom A's rows (thread j of the atom
-// sums partials j, j + 8, ... in order, then the eight combine), into dq[A]; the block's
-// sums of dq_A R_A and dq_A into bsum[blk] (dipole and trace parts).
+// Charges (block blk): dq_A = sum of the partials of atom A's rows (thread t of the atom sums
+// partials t, t + 64, ... in order; each warp reduces by a butterfly, and the atom's two
+// warps are added), into dq[A]; the block's sums of dq_A R_A and dq_A into bsum[blk]
+// (dipole and trace parts).
 __device__ void level_dq_block(const LevelArgs& a, int blk) {
-    __shared__ float2 red[8][4];
+    __shared__ float2 half_sum[8];
+    __shared__ float2 red[kLvAtoms][4];
+    __shared__ float2 r_sh[3 * kLvAtoms];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const float2 z = make_float2(0.f, 0.f);
-    const int A = blk * 32 + (tid >> 3), j = tid & 7;
+    const int A0 = blk * kLvAtoms;
+    const int A = A0 + (warp >> 1), t = (warp & 1) * 32 + lane;
     const int len = a.nper * a.nct;
-    float2 s = z, r[3] = {z, z, z};
+    if (tid < 3 * kLvAtoms) r_sh[tid] = A0 * 3 + tid < 3 * a.nat ? __ldg(a.R2 + 3 * A0 + tid) : z;
+    // the potentials kernel may be scheduled now (it loads its constants, then waits)
+    pdl_launch_dependents();
+    pdl_wait();
+    float2 s = z;
     if (A < a.nat) {
         const float2* p = a.partial + (size_t)A * len;
-        if (j == 0)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) r[k] = __ldg(a.R2 + 3 * A + k);
-        for (int k0 = j; k0 < len; k0 += 64) {
+        for (int k0 = t; k0 < len; k0 += 512) {
             float2 v[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = k0 + 8 * u < len ? ldcg2(p + k0 + 8 * u) : z;
+            for (int u = 0; u < 8; ++u) v[u] = k0 + 64 * u < len ? ldcg2(p + k0 + 64 * u) : z;
 #pragma unroll
             for (int u = 0; u < 8; ++u) s = df2_add(s, v[u]);
         }
     }
+    s = df2_warp_sum(s);
+    if (lane == 0) half_sum[warp] = s;
+    __syncthreads();
+    if (tid < kLvAtoms) {
+        const int Aa = A0 + tid;
+        float2 m[4] = {z, z, z, z};
+        if (Aa < a.nat) {
+            const float2 d = df2_add(half_sum[2 * tid], half_sum[2 * tid + 1]);
+            a.dq[Aa] = d;
 #pragma unroll
-    for (int o = 4; o > 0; o >>= 1) s = df2_add(s, df2_shfl_xor(s, o));
-    float2 m[4] = {z, z, z, z};
-    if (A < a.nat && j == 0) {
-        a.dq[A] = s;
+            for (int k = 0; k < 3; ++k) m[k] = df2_mul(d, r_sh[3 * tid + k]);
+            m[3] = d;
+        }
 #pragma unroll
-        for (int k = 0; k < 3; ++k) m[k] = df2_mul(s, r[k]);
-        m[3] = s;
+        for (int k = 0; k < 4; ++k) red[tid][k] = m[k];
     }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) m[k] = df2_warp_sum(m[k]);
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) red[warp][k] = m[k];
     __syncthreads();
     if (tid < 4) {
-        float2 t = red[0][tid];
-        for (int w = 1; w < 8; ++w) t = df2_add(t, red[w][tid]);
-        a.bsum[4 * blk + tid] = t;
+        float2 x = red[0][tid];
+#pragma unroll
+        for (int i = 1; i < kLvAtoms; ++i) x = df2_add(x, red[i][tid]);
+        a.bsum[4 * blk + tid] = x;
     }
 }
 
-// Potentials and the level's scalars (block blk of nblk): dv_A = sum_B gamma_AB dq_B
-// (eq:hscc; thread j of atom A takes B = j, j + 8, ... in order, then the eight combine)
-// + R_A . E(t) + the SCC residual of rho_ref, written per orbital (dv_f), and max |dv| over
-// the blocks; the block that finishes last takes Tr(rho S) and the renormalisation factor of
-// level `slot`, the FP16X6 scales of the next products, the dipole mu = mu_ref - sum_A dq_A
-// R_A into sc->mu and the history slot of step n_lvl, the field record, and with step_end
-// the step counter (to n_lvl) and the FP16X6 maxima (the new level is in `slot`); it resets
-// the counters.  trace_only (one block): only Tr(rho S) and f - 1.
+// Potentials and the level's scalars.  Blocks 0 .. level_blocks(nat) - 1 (kLvAtoms atoms
+// each): dv_A = sum_B gamma_AB dq_B (eq:hscc; thread t of atom A takes B = t, t + 64, ...
+// in order, each warp reduces by a butterfly, the atom's two warps are added) + R_A . E(t)
+// + the SCC residual of rho_ref, written per orbital (dv_f), and the maximum |dv| over the
+// blocks.  Block level_blocks(nat) (the totals block): Tr(rho S) and the renormalisation
+// factor of level `slot` from the charge blocks' sums, the dipole mu = mu_ref - sum_A dq_A
+// R_A into sc->mu and the history slot of step n_lvl, the field record.  The block that
+// arrives last sets the FP16X6 scales of the next products and, with step_end, the step
+// counter (to n_lvl) and the FP16X6 maxima (the new level is in `slot`); it resets the
+// counters.  trace_only (one block): only Tr(rho S) and f - 1.
 __device__ void level_final_block(const LevelArgs& a, int slot, long long n_lvl, bool trace_only,
                                   bool step_end, int blk, int nblk) {
-    __shared__ float2 dq_sh[256];
+    __shared__ float2 half_sum[8];
     __shared__ float2 tot[4];
     __shared__ float E_sh[3];
-    __shared__ float red[8];
+    __shared__ float rc_sh[kLvAtoms][4];
+    __shared__ float mx_sh;
     __shared__ int last;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     DevScalars* sc = a.sc;
     const float2 z = make_float2(0.f, 0.f);
-    int* max_bits = a.count + 1;     // max |dv| of this evaluation (float bits, >= 0)
-    if (!trace_only) {
-        if (tid == 0) {
-            float E[3] = {0.f, 0.f, 0.f};
-            if (sc->field.on) {
-                const double t = sc->t_base + (double)(n_lvl - sc->n_base) * sc->dt;
-                field_at_f(sc->field, t, E);
-            }
-            E_sh[0] = E[0];
-            E_sh[1] = E[1];
-            E_sh[2] = E[2];
-        }
-        const int A = blk * 32 + (tid >> 3), j = tid & 7;
-        float rx = 0.f, ry = 0.f, rz = 0.f, cr = 0.f;
-        if (A < a.nat && j == 0) {
-            rx = __ldg(&a.R2[3 * A].x);
-            ry = __ldg(&a.R2[3 * A + 1].x);
-            rz = __ldg(&a.R2[3 * A + 2].x);
-            cr = __ldg(a.c_res + A);
-        }
-        float2 acc = z;
-        if (a.scc) {
-            const float2* g = a.gam2 + (size_t)(A < a.nat ? A : 0) * a.nat;
-            // chunks of 256 atoms: their charges staged in shared memory, this thread's 32
-            // products of a chunk with their gamma loads issued 16 at a time
-            for (int c0 = 0; c0 < a.nat; c0 += 256) {
-                __syncthreads();
-                dq_sh[tid] = c0 + tid < a.nat ? ldcg2(a.dq + c0 + tid) : z;
-                __syncthreads();
-                const int nb = min(256, a.nat - c0);
+    const int nab = level_blocks(a.nat);
+    // constants first (gamma of this thread's first products, positions, residuals); the
+    // charges and scalars of the previous kernels after pdl_wait
+    const int A0 = blk * kLvAtoms;
+    const int A = A0 + (warp >> 1), t = (warp & 1) * 32 + lane;
+    const bool atoms = !trace_only && blk < nab;
+    float2 gv[8];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    float2 gv[16];
-#pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        const int b = j + 8 * (16 * h + u);
-                        gv[u] = (A < a.nat && b < nb) ? __ldg(g + c0 + b) : z;
-                    }
-#pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        const int b = j + 8 * (16 * h + u);
-                        if (b < nb) acc = df2_add(acc, df2_mul(gv[u], dq_sh[b]));
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int o = 4; o > 0; o >>= 1) acc = df2_add(acc, df2_shfl_xor(acc, o));
-        __syncthreads();
-        float mx = 0.f;
-        if (A < a.nat && j == 0) {
-            const float ext = fmaf(rx, E_sh[0], fmaf(ry, E_sh[1], rz * E_sh[2]));
-            const float dv = acc.x + (acc.y + (ext + cr));
-            for (int k = 0; k < a.nper; ++k) a.dv_f[A * a.nper + k] = dv;
-            mx = fabsf(dv);
-        }
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) red[warp] = mx;
-        __syncthreads();
-        if (tid == 0) {
-            float m = red[0];
-            for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w]);
-            atomicMax(max_bits, __float_as_int(m));
-            last = atom_add_acq_rel(a.count, 1) == nblk - 1;
-        }
-        __syncthreads();
-        if (!last) return;
+    for (int u = 0; u < 8; ++u) {
+        const int b = t + 64 * u;
+        gv[u] = (atoms && a.scc && A < a.nat && b < a.nat) ? __ldg(a.gam2 + (size_t)A * a.nat + b) : z;
     }
-    // the last block: sums of the charge blocks' dipole and trace parts (warps 0-3)
-    if (warp < 4) {
-        const int nb = level_final_blocks(a.nat);
-        float2 s = z;
-        for (int r = lane; r < nb; r += 32) s = df2_add(s, ldcg2(a.bsum + 4 * r + warp));
-        s = df2_warp_sum(s);
-        if (lane == 0) tot[warp] = s;
+    if (atoms && tid < kLvAtoms) {
+        const int Aa = A0 + tid;
+        const bool ok = Aa < a.nat;
+        rc_sh[tid][0] = ok ? __ldg(&a.R2[3 * Aa].x) : 0.f;
+        rc_sh[tid][1] = ok ? __ldg(&a.R2[3 * Aa + 1].x) : 0.f;
+        rc_sh[tid][2] = ok ? __ldg(&a.R2[3 * Aa + 2].x) : 0.f;
+        rc_sh[tid][3] = ok ? __ldg(a.c_res + Aa) : 0.f;
     }
-    __syncthreads();
+    pdl_wait();
     if (tid == 0) {
-        // Tr(rho S) = N_e - c0 + sum_A dq_A;  f - 1 = (N_e - Tr) / Tr ~ (c0 - sum dq) / N_e
-        const float2 d = tot[3];
-        const float eps = (((float)sc->c0_trace - d.x) - d.y) * a.inv_ne;
-        sc->eps_lvl[slot] = eps;
-        sc->trace_lvl[slot] = (sc->n_e - sc->c0_trace) + ((double)d.x + (double)d.y);
-    }
-    if (!trace_only) {
-        if (tid == 0) {
-            const float m = __int_as_float(__ldcg(max_bits));
-            tc::DynScales* dy = a.dyn;
-            if (dy) {
-                dy->max_dv = (double)m;
-                if (a.has_scales) {
-                    dy->s_dh = pscale_f(m);
-                    dy->s_dm = pscale_f(m * (float)dy->sinv_norm);
-                }
-                for (int k = 0; k < tc::kMaxParts; ++k) dy->max_x[k] = 0.0;
-                if (step_end) {
-                    // the maximum the update's blocks accumulated (atomics, read through L2)
-                    dy->max_drho[slot] = __ldcg(&dy->max_drho[2]);
-                    dy->max_drho[2] = 0.0;
-                }
-            }
-            if (step_end) sc->step = n_lvl;
+        float E[3] = {0.f, 0.f, 0.f};
+        if (!trace_only && sc->field.on) {
+            const double t = sc->t_base + (double)(n_lvl - sc->n_base) * sc->dt;
+            field_at_f(sc->field, t, E);
         }
+        E_sh[0] = E[0];
+        E_sh[1] = E[1];
+        E_sh[2] = E[2];
+        mx_sh = 0.f;
+    }
+    if (trace_only || blk == nab) {
+        // the totals block: sums of the charge blocks' dipole and trace parts (warps 0-3)
+        if (warp < 4) {
+            float2 s = z;
+            for (int r = lane; r < nab; r += 32) s = df2_add(s, ldcg2(a.bsum + 4 * r + warp));
+            s = df2_warp_sum(s);
+            if (lane == 0) tot[warp] = s;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            // Tr(rho S) = N_e - c0 + sum_A dq_A;  f - 1 = (N_e - Tr) / Tr ~ (c0 - sum dq) / N_e
+            const float2 d = tot[3];
+            const float eps = (((float)sc->c0_trace - d.x) - d.y) * a.inv_ne;
+            sc->eps_lvl[slot] = eps;
+            sc->trace_lvl[slot] = (sc->n_e - sc->c0_trace) + ((double)d.x + (double)d.y);
+        }
+        if (trace_only) return;
         if (warp == 1) {
             // dipole (lanes 0-2, one component each) into sc and the history slot of step n_lvl
             const int k = lane < 3 ? lane : 0;
@@ -1053,12 +1022,74 @@ __device__ void level_final_block(const LevelArgs& a, int slot, long long n_lvl,
             }
             if (lane == 0) sc->e_ext = e_ext;
         }
+    } else {
+        float2 acc = z;
+        if (a.scc && A < a.nat) {
+            const float2* g = a.gam2 + (size_t)A * a.nat;
+            for (int b0 = t; b0 < a.nat; b0 += 512) {
+                float2 qv[8];
+                if (b0 != t)
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int b = b0 + 64 * u;
+                        gv[u] = b < a.nat ? __ldg(g + b) : z;
+                    }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int b = b0 + 64 * u;
+                    qv[u] = b < a.nat ? __ldg(a.dq + b) : z;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc = df2_add(acc, df2_mul(gv[u], qv[u]));
+            }
+        }
+        acc = df2_warp_sum(acc);
+        if (lane == 0) half_sum[warp] = acc;
+        __syncthreads();
+        if (warp == 0) {
+            float mx = 0.f;
+            const int Aa = A0 + lane;
+            if (lane < kLvAtoms && Aa < a.nat) {
+                const float2 s = df2_add(half_sum[2 * lane], half_sum[2 * lane + 1]);
+                const float ext = fmaf(rc_sh[lane][0], E_sh[0],
+                                       fmaf(rc_sh[lane][1], E_sh[1], rc_sh[lane][2] * E_sh[2]));
+                const float dv = s.x + (s.y + (ext + rc_sh[lane][3]));
+                for (int k = 0; k < a.nper; ++k) a.dv_f[Aa * a.nper + k] = dv;
+                mx = fabsf(dv);
+            }
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane == 0) mx_sh = mx;
+        }
     }
-    // the reset includes the maximum |dv| that thread 0 read above
+    // arrival of every block (atom blocks carry their maximum |dv|)
     __syncthreads();
-    if (tid < 2) a.count[tid] = 0;
+    int* max_bits = a.count + 1;     // max |dv| of this evaluation (float bits, >= 0)
+    if (tid == 0) {
+        if (blk < nab) atomicMax(max_bits, __float_as_int(mx_sh));
+        last = atom_add_acq_rel(a.count, 1) == nblk - 1;
+    }
+    __syncthreads();
+    if (!last || tid != 0) return;
+    const float m = __int_as_float(__ldcg(max_bits));
+    tc::DynScales* dy = a.dyn;
+    if (dy) {
+        dy->max_dv = (double)m;
+        if (a.has_scales) {
+            dy->s_dh = pscale_f(m);
+            dy->s_dm = pscale_f(m * (float)dy->sinv_norm);
+        }
+        for (int k = 0; k < tc::kMaxParts; ++k) dy->max_x[k] = 0.0;
+        if (step_end) {
+            // the maximum the update's blocks accumulated (atomics, read through L2)
+            dy->max_drho[slot] = __ldcg(&dy->max_drho[2]);
+            dy->max_drho[2] = 0.0;
+        }
+    }
+    if (step_end) sc->step = n_lvl;
+    // the counters, after this thread's read of the maximum
+    a.count[0] = 0;
+    a.count[1] = 0;
 }
-
 
 // Update of the FP32-pair master (eq:leapfrog, eq:eomrho, frozen nuclei): the same
 // tile-pair scheme and operands as k_update, with the increment factor * rhodot formed
@@ -1073,100 +1104,74 @@ __device__ void level_final_block(const LevelArgs& a, int slot, long long n_lvl,
 // N_e per step, so Tr(rho S) stays within ~1e-12 of N_e in between).
 constexpr int kRenormEvery = 8;
 
-// Asynchronous 4-byte copy global -> shared (cp.async; src_size 0 fills zero), its group
-// commit and wait.
-__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
-    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src),
-                 "r"(valid ? 4 : 0)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int PENDING>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
-}
-
-// Shared memory of the update: the X parts of both tiles ([part][tile][row][col], rows
-// padded for transposed reads) and the second half's six operand arrays.
-__host__ __device__ inline int update_smem_bytes(int nparts) {
-    return (nparts * 2 * kTile * (kTile + 1) + 6 * kTile * kTile) * (int)sizeof(float);
-}
-
-// Row partials of one tile row: the 32 element values of a warp's lanes (lane = column),
-// summed by a butterfly (every lane ends with the same value); shared by the update and the
-// master partials.
-__device__ __forceinline__ float2 tile_row_sum_warp(float2 v) { return df2_warp_sum(v); }
-
 __device__ __forceinline__ void update_df_block(const UpdateDfArgs& A, int b) {
     const int N = A.N, nct = A.nct;
     const MasterPtrs& base = A.base;
     const MasterPtrs& out = A.out;
     const float fh = A.fh, fl = A.fl;
     const double factor = A.factor;
+    const float* __restrict__ Sf = A.Sf;
+    const float* __restrict__ rgs = A.rgs;
     DevScalars* __restrict__ sc = A.sc;
     const UpdateOperands& ops = A.ops;
+    const LevelArgs& lv = A.lv;
     // one block per tile pair bi <= bj: block b = bj (bj + 1) / 2 + bi
     int bj = (int)((sqrtf(8.0f * (float)b + 1.0f) - 1.0f) * 0.5f);
     while (bj * (bj + 1) / 2 > b) --bj;
     while ((bj + 1) * (bj + 2) / 2 <= b) ++bj;
     const int bi = b - bj * (bj + 1) / 2;
     constexpr int RPT = kTile / 8;
-    constexpr int XT = kTile * (kTile + 1), BT = kTile * kTile;
-    extern __shared__ float upd_smem[];
-    const int np = ops.nre + ops.nim;
-    float* xs = upd_smem;                   // [np][2][kTile][kTile + 1]: tile 0 (bi,bj), 1 (bj,bi)
-    float* bs = upd_smem + np * 2 * XT;     // [6][kTile][kTile]: second half's operands
-    __shared__ float s_bound;
-    __shared__ float eps_sh;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const bool two = bi != bj;
-    // every load of the block goes out first: the X parts and the second half's operands
-    // as asynchronous copies, the first half's operands into registers
-    for (int q = 0; q < np; ++q) {
-        const float* src = q < ops.nre ? ops.xre[q] : ops.xim[q - ops.nre];
+    {
+        // every operand line of both halves (rows of 32 floats = one 128-byte line) is
+        // requested from DRAM at once; the loads below then hit L2
+        const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+        const int arr = tid >> 5, row = tid & 31;
+        if (arr < 5) {
+            const float* p = arr == 0 ? base.re_hi : arr == 1 ? base.re_lo : arr == 2 ? base.im_hi
+                             : arr == 3 ? base.im_lo : Sf;
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            const int tr = t ? bj : bi, tc = t ? bi : bj;
-#pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-                const int y = ty + 8 * k, r = tr * kTile + y, c = tc * kTile + tx;
-                const bool ok = r < N && c < N;
-                cp_async4(xs + (q * 2 + t) * XT + y * (kTile + 1) + tx, src + (ok ? (size_t)r * N + c : 0), ok);
+            for (int h = 0; h < 2; ++h) {
+                const int ti = h ? bj : bi, tj = h ? bi : bj;
+                const int r = ti * kTile + row, c = tj * kTile;
+                if ((h == 0 || bi != bj) && r < N && c < N)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(p + (size_t)r * N + c));
             }
         }
     }
-    cp_async_commit();
-    if (two) {
+    // X, the scalars and the outputs belong to the previous kernels from here on
+    pdl_wait();
+    __shared__ float xr_ij[kTile][kTile + 1], xi_ij[kTile][kTile + 1];
+    __shared__ float xr_ji[kTile][kTile + 1], xi_ji[kTile][kTile + 1];
+    __shared__ float2 pv_s[kTile][kTile + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    // X = sum of its partial products, in a fixed order (all loads issued first)
+    auto load_x = [&](size_t i, float& a, float& b) {
+        float t[6];
 #pragma unroll
-        for (int k = 0; k < RPT; ++k) {
-            const int y = ty + 8 * k, r = bj * kTile + y, c = bi * kTile + tx;
-            const bool ok = r < N && c < N;
-            const size_t i = ok ? (size_t)r * N + c : 0;
-            float* d = bs + y * kTile + tx;
-            cp_async4(d, base.re_hi + i, ok);
-            cp_async4(d + BT, base.re_lo + i, ok);
-            cp_async4(d + 2 * BT, base.im_hi + i, ok);
-            cp_async4(d + 3 * BT, base.im_lo + i, ok);
-            cp_async4(d + 4 * BT, A.Sf + i, ok);
-        }
-    }
-    cp_async_commit();
-    float brh[RPT], brl[RPT], bih[RPT], bil[RPT], sv[RPT], gv[RPT];
+        for (int q = 0; q < 4; ++q) t[q] = q < ops.nre ? ops.xre[q][i] : 0.f;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) t[4 + q] = q < ops.nim ? ops.xim[q][i] : 0.f;
+        a = ((t[0] + t[1]) + t[2]) + t[3];
+        b = t[4] + t[5];
+    };
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
-        const int r = bi * kTile + ty + 8 * k, c = bj * kTile + tx;
-        brh[k] = brl[k] = bih[k] = bil[k] = sv[k] = gv[k] = 0.f;
-        if (r < N && c < N) {
-            const size_t i = (size_t)r * N + c;
-            brh[k] = base.re_hi[i];
-            brl[k] = base.re_lo[i];
-            bih[k] = base.im_hi[i];
-            bil[k] = base.im_lo[i];
-            sv[k] = A.Sf[i];
-        }
+        const int y = ty + 8 * k;
+        int r = bi * kTile + y, c = bj * kTile + tx;
+        float a = 0.f, b = 0.f;
+        if (r < N && c < N) load_x((size_t)r * N + c, a, b);
+        xr_ij[y][tx] = a;
+        xi_ij[y][tx] = b;
+        r = bj * kTile + y;
+        c = bi * kTile + tx;
+        a = b = 0.f;
+        if (r < N && c < N) load_x((size_t)r * N + c, a, b);
+        xr_ji[y][tx] = a;
+        xi_ji[y][tx] = b;
     }
-    if (tx == 0 && ty == 0) {
+    __shared__ float s_bound;
+    __shared__ float eps_sh;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
         // both leapfrog chains are renormalised once every kRenormEvery steps
         const long long n = sc->step;
         eps_sh = (n % kRenormEvery) < 2 ? sc->eps_lvl[ops.base_slot] : 0.f;
@@ -1184,51 +1189,22 @@ __device__ __forceinline__ void update_df_block(const UpdateDfArgs& A, int b) {
     __syncthreads();
     const float op_scale = ops.dyn ? s_bound : ops.scale;
     const float eps = eps_sh;
-    // renormalisation steps: rho_ref of both halves (the second one asynchronously)
-    if (eps != 0.f) {
+    float dmax = 0.f;
+    for (int half = 0; half < (bi == bj ? 1 : 2); ++half) {
+        const int ti = half ? bj : bi, tj = half ? bi : bj;
+        float brh[RPT], brl[RPT], bih[RPT], bil[RPT], sv[RPT], gv[RPT];
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
-            const int r = bi * kTile + ty + 8 * k, c = bj * kTile + tx;
-            if (r < N && c < N) gv[k] = A.rgs[(size_t)r * N + c];
-        }
-        if (two)
-#pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-                const int y = ty + 8 * k, r = bj * kTile + y, c = bi * kTile + tx;
-                const bool ok = r < N && c < N;
-                cp_async4(bs + 5 * BT + y * kTile + tx, A.rgs + (ok ? (size_t)r * N + c : 0), ok);
-            }
-    }
-    cp_async_commit();
-    cp_async_wait<2>();                      // the X parts (this thread's copies) ...
-    __syncthreads();                         // ... and everyone's
-    // X = sum of its partial products in a fixed order: Re ((x0 + x1) + x2) + x3, Im x4 + x5
-    auto x_re = [&](int t, int y, int x) {
-        const float* p = xs + t * XT + y * (kTile + 1) + x;
-        float a = p[0];
-        for (int q = 1; q < ops.nre; ++q) a = a + p[q * 2 * XT];
-        return a;
-    };
-    auto x_im = [&](int t, int y, int x) {
-        const float* p = xs + (ops.nre * 2 + t) * XT + y * (kTile + 1) + x;
-        float a = p[0];
-        for (int q = 1; q < ops.nim; ++q) a = a + p[q * 2 * XT];
-        return a;
-    };
-    float dmax = 0.f;
-    for (int half = 0; half < (two ? 2 : 1); ++half) {
-        const int ti = half ? bj : bi, tj = half ? bi : bj;
-        if (half) {
-            cp_async_wait<0>();              // this thread's own copies of the second half
-#pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-                const int o = (ty + 8 * k) * kTile + tx;
-                brh[k] = bs[o];
-                brl[k] = bs[o + BT];
-                bih[k] = bs[o + 2 * BT];
-                bil[k] = bs[o + 3 * BT];
-                sv[k] = bs[o + 4 * BT];
-                gv[k] = eps != 0.f ? bs[o + 5 * BT] : 0.f;
+            const int r = ti * kTile + ty + 8 * k, c = tj * kTile + tx;
+            brh[k] = brl[k] = bih[k] = bil[k] = sv[k] = gv[k] = 0.f;
+            if (r < N && c < N) {
+                const size_t i = (size_t)r * N + c;
+                brh[k] = base.re_hi[i];
+                brl[k] = base.re_lo[i];
+                bih[k] = base.im_hi[i];
+                bil[k] = base.im_lo[i];
+                sv[k] = Sf[i];
+                if (eps != 0.f) gv[k] = rgs[i];
             }
         }
 #pragma unroll
@@ -1237,9 +1213,18 @@ __device__ __forceinline__ void update_df_block(const UpdateDfArgs& A, int b) {
             const int r = ti * kTile + y, c = tj * kTile + tx;
             float2 pv = make_float2(0.f, 0.f);
             if (r < N && c < N) {
-                // tile `half` holds X_ij, the other X_ji (read transposed)
-                const float x_ij_re = x_re(half, y, tx), x_ij_im = x_im(half, y, tx);
-                const float x_ji_re = x_re(half ^ 1, tx, y), x_ji_im = x_im(half ^ 1, tx, y);
+                float x_ij_re, x_ij_im, x_ji_re, x_ji_im;
+                if (!half) {
+                    x_ij_re = xr_ij[y][tx];
+                    x_ij_im = xi_ij[y][tx];
+                    x_ji_re = xr_ji[tx][y];
+                    x_ji_im = xi_ji[tx][y];
+                } else {
+                    x_ij_re = xr_ji[y][tx];
+                    x_ij_im = xi_ji[y][tx];
+                    x_ji_re = xr_ij[tx][y];
+                    x_ji_im = xi_ij[tx][y];
+                }
                 // rhodot = -i (X - X^dagger); the (j,i) element repeats these operations on
                 // the swapped operands, so the master stays exactly Hermitian
                 const float dre = x_ij_im + x_ji_im;
@@ -1288,10 +1273,15 @@ __device__ __forceinline__ void update_df_block(const UpdateDfArgs& A, int b) {
                     }
                 }
             }
-            // Mulliken partial of row r over this column tile (lanes = columns)
-            const float2 sum = tile_row_sum_warp(pv);
-            if (tx == 0 && r < N) const_cast<float2*>(A.lv.partial)[(size_t)r * nct + tj] = sum;
+            pv_s[y][tx] = pv;
         }
+        __syncthreads();
+        if (ty == 0) {
+            const int r = ti * kTile + tx;
+            const float2 sum = tile_row_sum(pv_s[tx]);
+            if (r < N) const_cast<float2*>(lv.partial)[(size_t)r * nct + tj] = sum;
+        }
+        __syncthreads();
     }
     if (ops.dyn) {
         // one atomic per block (the warps' maxima through shared memory)
@@ -1337,7 +1327,7 @@ __global__ void __launch_bounds__(256)
     const int2 w = work[blockIdx.x];
     const LevelFinalArgs& f = args[w.x];
     const long long n_lvl = f.lv.sc->step + 1;
-    level_final_block(f.lv, f.slot, n_lvl, false, true, w.y, level_final_blocks(f.lv.nat));
+    level_final_block(f.lv, f.slot, n_lvl, false, true, w.y, level_blocks(f.lv.nat) + 1);
 }
 
 // FP64 populations from the (hi, lo) row partials of the deviation: one warp per atom
@@ -1389,10 +1379,9 @@ __global__ void k_master_to_view(size_t n, MasterPtrs m, const double* __restric
 // k_update_df (exact high products, FP32-pair sums in the same column order)
 __global__ void k_master_partials(int N, int nct, MasterPtrs m, const float* __restrict__ Sf,
                                   float2* __restrict__ partial) {
+    __shared__ float2 pv_s[kTile][kTile + 1];
     const int ct = blockIdx.x;
     const int col = ct * kTile + threadIdx.x;
-    // warp y takes rows y, y + 8, ... of the row tile, its lanes the columns (the order of
-    // the update's row sums)
     for (int y = threadIdx.y; y < kTile; y += blockDim.y) {
         const int row = blockIdx.y * kTile + y;
         float2 v = make_float2(0.f, 0.f);
@@ -1400,8 +1389,13 @@ __global__ void k_master_partials(int N, int nct, MasterPtrs m, const float* __r
             const size_t i = (size_t)row * N + col;
             v = mulliken_elem(m.re_hi[i], m.re_lo[i], Sf[i]);
         }
-        const float2 sum = tile_row_sum_warp(v);
-        if (threadIdx.x == 0 && row < N) partial[(size_t)row * nct + ct] = sum;
+        pv_s[y][threadIdx.x] = v;
+    }
+    __syncthreads();
+    if (threadIdx.y == 0) {
+        const int row = blockIdx.y * kTile + threadIdx.x;
+        const float2 sum = tile_row_sum(pv_s[threadIdx.x]);
+        if (row < N) partial[(size_t)row * nct + ct] = sum;
     }
 }
 
@@ -1480,49 +1474,40 @@ UpdateDfArgs update_df_args(const Ctx& c, const MasterPtrs& base, const MasterPt
     return a;
 }
 
-cudaError_t prepare_update() {
-    // up to six X parts (two K slices)
-    const int bytes = update_smem_bytes(6);
-    cudaError_t e = cudaFuncSetAttribute(k_update_df, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_update_df_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    return e;
-}
-
 void launch_update_df(const Ctx& c, const MasterPtrs& base, const MasterPtrs& out, double factor,
                       DevScalars* sc, const UpdateOperands& ops, const LevelArgs& lv,
                       cudaStream_t st) {
-    k_update_df<<<c.nct * (c.nct + 1) / 2, dim3(kTile, 8), update_smem_bytes(ops.nre + ops.nim), st>>>(
-        update_df_args(c, base, out, factor, sc, ops, lv));
+    launch_pdl(k_update_df, dim3(c.nct * (c.nct + 1) / 2), dim3(kTile, 8), 0, st,
+               update_df_args(c, base, out, factor, sc, ops, lv));
 }
 
 void launch_update_df_grouped(const UpdateDfArgs* args, const int2* work, int nwork,
-                              int max_parts, cudaStream_t st) {
-    k_update_df_grouped<<<nwork, dim3(kTile, 8), update_smem_bytes(max_parts), st>>>(args, work);
+                              cudaStream_t st) {
+    launch_pdl(k_update_df_grouped, dim3(nwork), dim3(kTile, 8), 0, st, args, work);
 }
 
 void launch_level(const Ctx& c, const LevelArgs& lv, int slot, int trace_only, cudaStream_t st) {
-    k_level_dq<<<level_final_blocks(c.nat), dim3(kTile, 8), 0, st>>>(lv);
-    k_level_final<<<trace_only ? 1 : level_final_blocks(c.nat), dim3(kTile, 8), 0, st>>>(
+    k_level_dq<<<level_blocks(c.nat), dim3(kTile, 8), 0, st>>>(lv);
+    k_level_final<<<trace_only ? 1 : level_blocks(c.nat) + 1, dim3(kTile, 8), 0, st>>>(
         lv, slot, trace_only, 0);
 }
 
 void launch_level_dq(const Ctx& c, const LevelArgs& lv, cudaStream_t st) {
-    k_level_dq<<<level_final_blocks(c.nat), dim3(kTile, 8), 0, st>>>(lv);
+    launch_pdl(k_level_dq, dim3(level_blocks(c.nat)), dim3(kTile, 8), 0, st, lv);
 }
 
 void launch_level_dq_grouped(const LevelFinalArgs* args, const int2* work, int nwork,
                              cudaStream_t st) {
-    k_level_dq_grouped<<<nwork, dim3(kTile, 8), 0, st>>>(args, work);
+    launch_pdl(k_level_dq_grouped, dim3(nwork), dim3(kTile, 8), 0, st, args, work);
 }
 
 void launch_level_final(const Ctx& c, const LevelArgs& lv, int slot, cudaStream_t st) {
-    k_level_final<<<level_final_blocks(c.nat), dim3(kTile, 8), 0, st>>>(lv, slot, 0, 1);
+    launch_pdl(k_level_final, dim3(level_blocks(c.nat) + 1), dim3(kTile, 8), 0, st, lv, slot, 0, 1);
 }
 
 void launch_level_final_grouped(const LevelFinalArgs* args, const int2* work, int nwork,
                                 cudaStream_t st) {
-    k_level_final_grouped<<<nwork, dim3(kTile, 8), 0, st>>>(args, work);
+    launch_pdl(k_level_final_grouped, dim3(nwork), dim3(kTile, 8), 0, st, args, work);
 }
 
 void launch_charges_df(const Ctx& c, const float2* partial, double* q, double* dq, cudaStream_t st) {

@@ -24,6 +24,7 @@
 
 #include <cstdint>
 
+#include "pdl.cuh"
 #include "tc_ptx.cuh"
 #include "tc_split.cuh"
 #include "tdb_tc.h"
@@ -145,6 +146,9 @@ __device__ __forceinline__ void gemm_tile(const Maps& maps, const GemmParams& p,
             for (int u = 0; u < 8; ++u) mgs_pre[u] = __ldg(mg4 + u);
         }
     }
+    // everything above touches only constants and this CTA's own memory: the operands the
+    // previous kernel wrote are read from here on
+    pdl_wait();
     if (warp == 0 && lane == 0) {
         // TMA producer: A pieces then B pieces of one 64-wide K block per stage
         for (int kb = 0; kb < nkb; ++kb) {
@@ -203,6 +207,11 @@ __device__ __forceinline__ void gemm_tile(const Maps& maps, const GemmParams& p,
             mma_commit(empty0 + 8 * s);
         }
         mma_commit(done);
+    } else if (warp >= 2 && p.pf.n > 0) {
+        // this CTA's share of the lines to prefetch (CTAs numbered over tiles and parts)
+        const int tiles_x = (p.N + BN - 1) / BN, tiles_y = (p.M + BM - 1) / BM;
+        l2_prefetch_share(p.pf, ((long long)tz * tiles_y + ty) * tiles_x + tx, threadIdx.x - 64,
+                          kThreads - 64);
     }
     __syncwarp();
 
@@ -210,6 +219,8 @@ __device__ __forceinline__ void gemm_tile(const Maps& maps, const GemmParams& p,
     // may access) and every second 32-column chunk starting at chunk w / 4
     const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0, p.err, 3) ? 1 : 0) != 0;
     fence_after();
+    // the products are done: the next kernel may be scheduled while the epilogue runs
+    pdl_launch_dependents();
     if (ok) {
         const float sa = P.sa_dev ? *P.sa_dev : P.sa, sb = P.sb_dev ? *P.sb_dev : P.sb;
         const float inv = 1.0f / (sa * sb);
@@ -396,9 +407,13 @@ __device__ __forceinline__ void split_dham_block(int N, const float* __restrict_
                                                  const float* __restrict__ dv, float scale_const,
                                                  int bf16, const Pieces& out, int ld_out,
                                                  const DynScales* __restrict__ dyn, int* err,
-                                                 int bx, int by, int gy) {
+                                                 const L2Prefetch& pf, int bx, int by, int gy) {
     const int c = bx * blockDim.x + threadIdx.x;
     const int r = by * blockDim.y + threadIdx.y;
+    // the next product's constant operands towards L2 (this block's share)
+    if (pf.n > 0)
+        l2_prefetch_share(pf, (long long)by * ((N + 31) / 32) + bx,
+                          threadIdx.y * blockDim.x + threadIdx.x, blockDim.x * blockDim.y);
     // FP16X6: the scale of this step, pscale(max |dv|), written with dv by the evaluation
     // of the level (|delta H| <= max |dv| since |S_kj| <= 1)
     const float s = dyn ? dyn->s_dh : scale_const;
@@ -433,8 +448,8 @@ __device__ __forceinline__ void split_dham_block(int N, const float* __restrict_
 template <int SCHEME>
 __global__ void k_split_dham(int N, const float* __restrict__ S, const float* __restrict__ dv,
                              float scale_const, int bf16, Pieces out, int ld_out,
-                             DynScales* __restrict__ dyn, int* err) {
-    split_dham_block<SCHEME>(N, S, dv, scale_const, bf16, out, ld_out, dyn, err, blockIdx.x,
+                             DynScales* __restrict__ dyn, int* err, L2Prefetch pf) {
+    split_dham_block<SCHEME>(N, S, dv, scale_const, bf16, out, ld_out, dyn, err, pf, blockIdx.x,
                              blockIdx.y, gridDim.y);
 }
 
@@ -445,7 +460,7 @@ __global__ void k_split_dham_grouped(const SplitDhArgs* __restrict__ args,
     const SplitDhArgs& a = args[w.x];
     const int gx = (a.N + 31) / 32, gy = (a.N + 63) / 64;
     const Pieces out{{a.out[0], a.out[1], a.out[2]}};
-    split_dham_block<SCHEME>(a.N, a.S, a.dv, a.scale, a.bf16, out, a.ld_out, a.dyn, a.err,
+    split_dham_block<SCHEME>(a.N, a.S, a.dv, a.scale, a.bf16, out, a.ld_out, a.dyn, a.err, a.pf,
                              w.y % gx, w.y / gx, gy);
 }
 
@@ -552,35 +567,37 @@ cudaError_t launch(int scheme, const Maps& m, const GemmParams& p, int nparts, c
                    int bn) {
     if (!launchable(scheme, p, nparts, bn)) return cudaErrorInvalidValue;
     dim3 grid((p.N + bn - 1) / bn, (p.M + BM - 1) / BM, nparts);
+    cudaError_t e;
     if (bn == 64) {
         if (scheme == kHiLo)
-            k_split_gemm<kHiLo, 64><<<grid, kThreads, smem_total<kHiLo, 64>(), st>>>(m, p);
+            e = launch_pdl(k_split_gemm<kHiLo, 64>, grid, dim3(kThreads), smem_total<kHiLo, 64>(), st, m, p);
         else
-            k_split_gemm<kHead3, 64><<<grid, kThreads, smem_total<kHead3, 64>(), st>>>(m, p);
+            e = launch_pdl(k_split_gemm<kHead3, 64>, grid, dim3(kThreads), smem_total<kHead3, 64>(), st, m, p);
     } else if (bn == 256) {
         if (scheme == kHiLo)
-            k_split_gemm<kHiLo, 256><<<grid, kThreads, smem_total<kHiLo, 256>(), st>>>(m, p);
+            e = launch_pdl(k_split_gemm<kHiLo, 256>, grid, dim3(kThreads), smem_total<kHiLo, 256>(), st, m, p);
         else
-            k_split_gemm<kHead3, 256><<<grid, kThreads, smem_total<kHead3, 256>(), st>>>(m, p);
+            e = launch_pdl(k_split_gemm<kHead3, 256>, grid, dim3(kThreads), smem_total<kHead3, 256>(), st, m, p);
     } else if (bn == 176) {
         if (scheme == kHiLo)
-            k_split_gemm<kHiLo, 176><<<grid, kThreads, smem_total<kHiLo, 176>(), st>>>(m, p);
+            e = launch_pdl(k_split_gemm<kHiLo, 176>, grid, dim3(kThreads), smem_total<kHiLo, 176>(), st, m, p);
         else
-            k_split_gemm<kHead3, 176><<<grid, kThreads, smem_total<kHead3, 176>(), st>>>(m, p);
+            e = launch_pdl(k_split_gemm<kHead3, 176>, grid, dim3(kThreads), smem_total<kHead3, 176>(), st, m, p);
     } else {
         if (scheme == kHiLo)
-            k_split_gemm<kHiLo, 128><<<grid, kThreads, smem_total<kHiLo, 128>(), st>>>(m, p);
+            e = launch_pdl(k_split_gemm<kHiLo, 128>, grid, dim3(kThreads), smem_total<kHiLo, 128>(), st, m, p);
         else
-            k_split_gemm<kHead3, 128><<<grid, kThreads, smem_total<kHead3, 128>(), st>>>(m, p);
+            e = launch_pdl(k_split_gemm<kHead3, 128>, grid, dim3(kThreads), smem_total<kHead3, 128>(), st, m, p);
     }
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_grouped(int scheme, const GroupedGemm* g, const int2* work, int nwork,
                            cudaStream_t st, int bn) {
     if (nwork < 1 || (bn != 64 && bn != 128 && bn != 176 && bn != 256)) return cudaErrorInvalidValue;
+    cudaError_t e;
 #define TDB_GROUPED(S, W)                                                                     \
-    k_split_gemm_grouped<S, W><<<nwork, kThreads, smem_total<S, W>(), st>>>(g, work)
+    e = launch_pdl(k_split_gemm_grouped<S, W>, dim3(nwork), dim3(kThreads), smem_total<S, W>(), st, g, work)
     if (scheme == kHiLo) {
         if (bn == 64) TDB_GROUPED(kHiLo, 64);
         else if (bn == 128) TDB_GROUPED(kHiLo, 128);
@@ -593,7 +610,7 @@ cudaError_t launch_grouped(int scheme, const GroupedGemm* g, const int2* work, i
         else TDB_GROUPED(kHead3, 256);
     }
 #undef TDB_GROUPED
-    return cudaGetLastError();
+    return e;
 }
 
 void launch_split(int scheme, int rows, int cols, const double* in, int ld_in, float scale, int sign,
@@ -637,15 +654,17 @@ void launch_split_dham_grouped(int scheme, const SplitDhArgs* args, const int2* 
 
 void launch_split_dham(int scheme, int N, const float* S, const float* dv, float scale, int bf16,
                        uint16_t* const* pieces, int ld_out, DynScales* dyn, cudaStream_t st,
-                       int* err) {
+                       int* err, const L2Prefetch* pf) {
     dim3 b(32, 8);
     // about 8 rows per thread
     dim3 g((N + 31) / 32, (N + 63) / 64);
     Pieces o{{pieces[0], pieces[1], scheme == kHead3 ? pieces[2] : nullptr}};
+    L2Prefetch none{};
+    const L2Prefetch& p = pf ? *pf : none;
     if (scheme == kHiLo)
-        k_split_dham<kHiLo><<<g, b, 0, st>>>(N, S, dv, scale, bf16, o, ld_out, nullptr, err);
+        k_split_dham<kHiLo><<<g, b, 0, st>>>(N, S, dv, scale, bf16, o, ld_out, nullptr, err, p);
     else
-        k_split_dham<kHead3><<<g, b, 0, st>>>(N, S, dv, scale, bf16, o, ld_out, dyn, err);
+        k_split_dham<kHead3><<<g, b, 0, st>>>(N, S, dv, scale, bf16, o, ld_out, dyn, err, p);
 }
 
 }  // namespace tc

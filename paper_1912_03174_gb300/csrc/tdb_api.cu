@@ -178,7 +178,7 @@ size_t carve(Ctx& c, char* base) {
         c.gam2 = k.take<float2>(nat * nat);
         c.R2 = k.take<float2>(3 * nat);
         c.lv_dq = k.take<float2>(nat);
-        c.lv_bsum = k.take<float2>(4 * (size_t)level_final_blocks(nat));
+        c.lv_bsum = k.take<float2>(4 * (size_t)level_blocks(nat));
         c.c_res = k.take<float>(nat);
         c.lv_count = k.take<int>(2);
     }
@@ -615,7 +615,6 @@ tdb_status materialize(Ctx& c) {
 // and the dipole of rho_ref (host FP64, once).
 tdb_status setup_level_constants(Ctx& c) {
     const int nat = c.nat, N = c.N;
-    CK(prepare_update());
     std::vector<double> g((size_t)nat * nat), qb(nat), vref(N), q0v(nat);
     DevScalars h{};
     CK(cudaMemcpyAsync(g.data(), c.gamma, sizeof(double) * g.size(), cudaMemcpyDeviceToHost, c.stream));
@@ -1076,6 +1075,39 @@ TensorStep tensor_step_args(Ctx& c, int cur, bool euler, int bn) {
     const double factor = euler ? c.prm.dt : 2.0 * c.prm.dt;
     ts.upd = update_df_args(c, euler ? c.ms[cur] : c.ms[prv], c.ms[prv], factor, c.sc, ops,
                             level_args(c));
+    // each product prefetches into L2 the operands the next kernel reads from DRAM: delta M
+    // the B pieces of the X product, X the base level and S of the update
+    const size_t NN4 = sizeof(float) * (size_t)N * N;
+    L2Prefetch& d = ts.dm.pf;
+    d.n = 0;
+    for (int q = 0; q < c.npieces; ++q) {
+        d.ptr[d.n] = c.pc_bre[q];
+        d.bytes[d.n++] = sizeof(uint16_t) * (size_t)N * 2 * Np;
+    }
+    for (int q = 0; q < c.npieces && d.n < 6; ++q) {
+        d.ptr[d.n] = c.pc_bim[q];
+        d.bytes[d.n++] = sizeof(uint16_t) * (size_t)N * Np;
+    }
+    d.parts = ((N + 63) / 64) * ((N + 127) / 128);
+    L2Prefetch& x = ts.x.pf;
+    const MasterPtrs& bm = ts.upd.base;
+    const void* reg[5] = {bm.re_hi, bm.re_lo, bm.im_hi, bm.im_lo, c.S_f};
+    x.n = 5;
+    for (int r = 0; r < 5; ++r) {
+        x.ptr[r] = reg[r];
+        x.bytes[r] = NN4;
+    }
+    x.parts = ((N + bn - 1) / bn) * ((N + 127) / 128) * ts.x_parts;
+    // the split of delta H prefetches the delta-M product's constant operands
+    L2Prefetch& sp = ts.split.pf;
+    sp.n = 0;
+    for (int q = 0; q < c.npieces; ++q) {
+        sp.ptr[sp.n] = c.pc_sinv[q];
+        sp.bytes[sp.n++] = sizeof(uint16_t) * (size_t)N * Np;
+    }
+    sp.ptr[sp.n] = c.Mgs_f;
+    sp.bytes[sp.n++] = NN4;
+    sp.parts = tc::split_dham_blocks(N);
     return ts;
 }
 
@@ -1131,7 +1163,7 @@ tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* t
         MARK("split_dH");
         tc::launch_split_dham(c.scheme, ts.split.N, ts.split.S, ts.split.dv, ts.split.scale,
                               ts.split.bf16, ts.split.out, ts.split.ld_out, ts.split.dyn, c.stream,
-                              ts.split.err);
+                              ts.split.err, &ts.split.pf);
         ++n;
         MARK("tc_gemm_dM");
         CK(tc::launch(c.scheme, c.maps_dm, ts.dm, 1, c.stream, 64));
@@ -2354,9 +2386,9 @@ struct tdb_batch {
     tc::GroupedGemm* d_x[2] = {};
     UpdateDfArgs* d_upd[2] = {};
     LevelFinalArgs* d_fin[2] = {};
-    int2 *w_split = nullptr, *w_dm = nullptr, *w_x = nullptr, *w_upd = nullptr, *w_fin = nullptr;
-    int n_split = 0, n_dm = 0, n_x = 0, n_upd = 0, n_fin = 0;
-    int upd_parts = 1;                 // largest nre + nim of the contexts' updates
+    int2 *w_split = nullptr, *w_dm = nullptr, *w_x = nullptr, *w_upd = nullptr, *w_ldq = nullptr,
+         *w_fin = nullptr;
+    int n_split = 0, n_dm = 0, n_x = 0, n_upd = 0, n_ldq = 0, n_fin = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
 };
 
@@ -2396,7 +2428,7 @@ tdb_status batch_layout(tdb_batch& b, int bn, int schedule) {
     std::vector<tc::GroupedGemm> dm[2], xg[2];
     std::vector<UpdateDfArgs> upd[2];
     std::vector<LevelFinalArgs> fin[2];
-    std::vector<int> nb_split(P), nb_dm(P), nb_x(P), nb_upd(P), nb_fin(P);
+    std::vector<int> nb_split(P), nb_dm(P), nb_x(P), nb_upd(P), nb_ldq(P), nb_fin(P);
     for (int g = 0; g < 2; ++g)
         for (int p = 0; p < P; ++p) {
             Ctx& c = *b.ctxs[p];
@@ -2410,12 +2442,12 @@ tdb_status batch_layout(tdb_batch& b, int bn, int schedule) {
             dm[g].push_back(grouped(c.maps_dm, ts.dm, c.N, 64, 1));
             xg[g].push_back(grouped(mx, ts.x, c.N, bn, ts.x_parts));
             upd[g].push_back(ts.upd);
-            b.upd_parts = std::max(b.upd_parts, ts.upd.ops.nre + ts.upd.ops.nim);
             LevelFinalArgs f{};
             f.lv = ts.upd.lv;
             f.slot = ts.upd.out_slot;
             fin[g].push_back(f);
-            nb_fin[p] = level_final_blocks(c.nat);
+            nb_ldq[p] = level_blocks(c.nat);
+            nb_fin[p] = level_blocks(c.nat) + 1;
             nb_split[p] = tc::split_dham_blocks(c.N);
             nb_dm[p] = dm[g].back().tiles_x * dm[g].back().tiles_y;
             nb_x[p] = xg[g].back().tiles_x * xg[g].back().tiles_y * ts.x_parts;
@@ -2423,14 +2455,14 @@ tdb_status batch_layout(tdb_batch& b, int bn, int schedule) {
         }
     const std::vector<int2> ws = work_list(b, nb_split, schedule), wd = work_list(b, nb_dm, schedule),
                             wx = work_list(b, nb_x, schedule), wu = work_list(b, nb_upd, schedule),
-                            wf = work_list(b, nb_fin, schedule);
+                            wq = work_list(b, nb_ldq, schedule), wf = work_list(b, nb_fin, schedule);
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t s_split = up(sizeof(tc::SplitDhArgs) * P), s_gg = up(sizeof(tc::GroupedGemm) * P),
                  s_upd = up(sizeof(UpdateDfArgs) * P), s_fin = up(sizeof(LevelFinalArgs) * P);
     const size_t total = 2 * (s_split + 2 * s_gg + s_upd + s_fin) +
                          up(sizeof(int2) * ws.size()) + up(sizeof(int2) * wd.size()) +
                          up(sizeof(int2) * wx.size()) + up(sizeof(int2) * wu.size()) +
-                         up(sizeof(int2) * wf.size());
+                         up(sizeof(int2) * wq.size()) + up(sizeof(int2) * wf.size());
     if (b.dmem) {
         CK(cudaStreamSynchronize(b.stream));
         cudaFree(b.dmem);
@@ -2460,7 +2492,9 @@ tdb_status batch_layout(tdb_batch& b, int bn, int schedule) {
     b.w_dm = reinterpret_cast<int2*>(put(wd.data(), sizeof(int2) * wd.size(), up(sizeof(int2) * wd.size())));
     b.w_x = reinterpret_cast<int2*>(put(wx.data(), sizeof(int2) * wx.size(), up(sizeof(int2) * wx.size())));
     b.w_upd = reinterpret_cast<int2*>(put(wu.data(), sizeof(int2) * wu.size(), up(sizeof(int2) * wu.size())));
+    b.w_ldq = reinterpret_cast<int2*>(put(wq.data(), sizeof(int2) * wq.size(), up(sizeof(int2) * wq.size())));
     b.w_fin = reinterpret_cast<int2*>(put(wf.data(), sizeof(int2) * wf.size(), up(sizeof(int2) * wf.size())));
+    b.n_ldq = (int)wq.size();
     b.n_fin = (int)wf.size();
     b.n_split = (int)ws.size();
     b.n_dm = (int)wd.size();
@@ -2478,8 +2512,8 @@ tdb_status batch_enqueue(tdb_batch& b, int g) {
     tc::launch_split_dham_grouped(b.scheme, b.d_split[g], b.w_split, b.n_split, b.stream);
     CK(tc::launch_grouped(b.scheme, b.d_dm[g], b.w_dm, b.n_dm, b.stream, 64));
     CK(tc::launch_grouped(b.scheme, b.d_x[g], b.w_x, b.n_x, b.stream, b.x_bn));
-    launch_update_df_grouped(b.d_upd[g], b.w_upd, b.n_upd, b.upd_parts, b.stream);
-    launch_level_dq_grouped(b.d_fin[g], b.w_fin, b.n_fin, b.stream);
+    launch_update_df_grouped(b.d_upd[g], b.w_upd, b.n_upd, b.stream);
+    launch_level_dq_grouped(b.d_fin[g], b.w_ldq, b.n_ldq, b.stream);
     launch_level_final_grouped(b.d_fin[g], b.w_fin, b.n_fin, b.stream);
     CKL();
     return TDB_OK;
@@ -2614,7 +2648,7 @@ tdb_status tdb_batch_create(tdb_ctx* const* ctxs, int count, tdb_batch** out) {
         set_err("tdb_batch_create: stream or event creation failed");
         st = TDB_ERR_CUDA;
     }
-    if (st == TDB_OK && (tc::prepare() != cudaSuccess || prepare_update() != cudaSuccess)) {
+    if (st == TDB_OK && tc::prepare() != cudaSuccess) {
         cudaGetLastError();
         set_err("tdb_batch_create: kernel attributes");
         st = TDB_ERR_CUDA;

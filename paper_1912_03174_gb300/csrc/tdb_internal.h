@@ -59,7 +59,7 @@ struct LevelArgs {
     const float2* R2;          // [nat][3] positions as (hi, lo)
     const float* c_res;        // [nat] (gamma dq(rho_ref))_A - v_ref_A: SCC residual of rho_ref
     float2* dq;                // [nat] deviation charges of the level (written by k_level_dq)
-    float2* bsum;              // [level_final_blocks][4] per block of 32 atoms: sum dq R_x, R_y, R_z, sum dq
+    float2* bsum;              // [level_blocks][4] per charge block: sum dq R_x, R_y, R_z, sum dq
     float* dv_f;               // [N] v - v_ref per orbital (written by the final stage)
     tc::DynScales* dyn;        // FP16X6 scales (may be null)
     DevScalars* sc;
@@ -267,14 +267,11 @@ UpdateDfArgs update_df_args(const Ctx& c, const MasterPtrs& base, const MasterPt
                             double factor, DevScalars* sc, const UpdateOperands& ops,
                             const LevelArgs& lv);
 // Updates of many contexts in one launch: block b runs tile pair work[b].y of args[work[b].x].
-// max_parts: the largest number of X partial products (nre + nim) among the contexts.
 void launch_update_df_grouped(const UpdateDfArgs* args, const int2* work, int nwork,
-                              int max_parts, cudaStream_t st);
+                              cudaStream_t st);
 // The update of the reduced forms also renormalises its base level (f = N_e / Tr(rho S))
 // and writes the Mulliken row partials of the new level (LevelArgs::partial); the level
 // itself is evaluated by launch_level_dq and launch_level_final after it.
-// Shared-memory opt-in of the update kernels (once per process; before their first launch).
-cudaError_t prepare_update();
 void launch_update_df(const Ctx& c, const MasterPtrs& base, const MasterPtrs& out, double factor,
                       DevScalars* sc, const UpdateOperands& ops, const LevelArgs& lv,
                       cudaStream_t st);
@@ -283,7 +280,10 @@ void launch_update_df(const Ctx& c, const MasterPtrs& base, const MasterPtrs& ou
 // renormalisation factor of level `slot` (partials of that level in lv.partial).
 void launch_level(const Ctx& c, const LevelArgs& lv, int slot, int trace_only, cudaStream_t st);
 // The level after an update (the new level in slot): charges, then potentials and scalars.
-__host__ __device__ inline int level_final_blocks(int nat) { return (nat + 31) / 32; }
+// Atoms per block of the level kernels (64 threads per atom); the potentials kernel has one
+// block more (the totals block).
+constexpr int kLvAtoms = 4;
+__host__ __device__ inline int level_blocks(int nat) { return (nat + kLvAtoms - 1) / kLvAtoms; }
 void launch_level_dq(const Ctx& c, const LevelArgs& lv, cudaStream_t st);
 void launch_level_final(const Ctx& c, const LevelArgs& lv, int slot, cudaStream_t st);
 struct LevelFinalArgs {

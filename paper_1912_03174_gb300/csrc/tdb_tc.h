@@ -6,6 +6,8 @@
 
 #include <cstdint>
 
+#include "pdl.cuh"
+
 namespace tdb {
 namespace tc {
 
@@ -47,6 +49,9 @@ struct GemmParams {
     float s_m;
     const float* s_dm_dev;
     int* err;          // device error flag: 1-3 bounded-wait time-outs, 4 piece overflow
+    // L2 prefetch of the next kernel's operands, issued by the epilogue warps while the
+    // products run (parts = the CTAs of this product: tiles x parts)
+    L2Prefetch pf;
 };
 
 // A: maps of the A pieces; b[set][piece]: maps of the Bt pieces.
@@ -103,7 +108,7 @@ struct DynScales {
 };
 void launch_split_dham(int scheme, int N, const float* S, const float* dv, float scale, int bf16,
                        uint16_t* const* pieces, int ld_out, DynScales* dyn, cudaStream_t st,
-                       int* err);
+                       int* err, const L2Prefetch* pf = nullptr);
 // The same for many contexts in one launch: block b runs block work[b].y (of
 // split_dham_blocks(N) per problem) of args[work[b].x].
 struct SplitDhArgs {
@@ -114,6 +119,7 @@ struct SplitDhArgs {
     uint16_t* out[3];
     DynScales* dyn;
     int* err;
+    L2Prefetch pf;     // the delta-M product's constant operands, prefetched by the split
 };
 SplitDhArgs split_dham_args(int scheme, int N, const float* S, const float* dv, float scale,
                             int bf16, uint16_t* const* pieces, int ld_out, DynScales* dyn, int* err);
