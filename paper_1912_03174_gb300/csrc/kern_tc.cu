@@ -407,13 +407,9 @@ __device__ __forceinline__ void split_dham_block(int N, const float* __restrict_
                                                  const float* __restrict__ dv, float scale_const,
                                                  int bf16, const Pieces& out, int ld_out,
                                                  const DynScales* __restrict__ dyn, int* err,
-                                                 const L2Prefetch& pf, int bx, int by, int gy) {
+                                                 int bx, int by, int gy) {
     const int c = bx * blockDim.x + threadIdx.x;
     const int r = by * blockDim.y + threadIdx.y;
-    // the next product's constant operands towards L2 (this block's share)
-    if (pf.n > 0)
-        l2_prefetch_share(pf, (long long)by * ((N + 31) / 32) + bx,
-                          threadIdx.y * blockDim.x + threadIdx.x, blockDim.x * blockDim.y);
     // FP16X6: the scale of this step, pscale(max |dv|), written with dv by the evaluation
     // of the level (|delta H| <= max |dv| since |S_kj| <= 1)
     const float s = dyn ? dyn->s_dh : scale_const;
@@ -448,8 +444,8 @@ __device__ __forceinline__ void split_dham_block(int N, const float* __restrict_
 template <int SCHEME>
 __global__ void k_split_dham(int N, const float* __restrict__ S, const float* __restrict__ dv,
                              float scale_const, int bf16, Pieces out, int ld_out,
-                             DynScales* __restrict__ dyn, int* err, L2Prefetch pf) {
-    split_dham_block<SCHEME>(N, S, dv, scale_const, bf16, out, ld_out, dyn, err, pf, blockIdx.x,
+                             DynScales* __restrict__ dyn, int* err) {
+    split_dham_block<SCHEME>(N, S, dv, scale_const, bf16, out, ld_out, dyn, err, blockIdx.x,
                              blockIdx.y, gridDim.y);
 }
 
@@ -460,7 +456,7 @@ __global__ void k_split_dham_grouped(const SplitDhArgs* __restrict__ args,
     const SplitDhArgs& a = args[w.x];
     const int gx = (a.N + 31) / 32, gy = (a.N + 63) / 64;
     const Pieces out{{a.out[0], a.out[1], a.out[2]}};
-    split_dham_block<SCHEME>(a.N, a.S, a.dv, a.scale, a.bf16, out, a.ld_out, a.dyn, a.err, a.pf,
+    split_dham_block<SCHEME>(a.N, a.S, a.dv, a.scale, a.bf16, out, a.ld_out, a.dyn, a.err,
                              w.y % gx, w.y / gx, gy);
 }
 
@@ -654,17 +650,15 @@ void launch_split_dham_grouped(int scheme, const SplitDhArgs* args, const int2* 
 
 void launch_split_dham(int scheme, int N, const float* S, const float* dv, float scale, int bf16,
                        uint16_t* const* pieces, int ld_out, DynScales* dyn, cudaStream_t st,
-                       int* err, const L2Prefetch* pf) {
+                       int* err) {
     dim3 b(32, 8);
     // about 8 rows per thread
     dim3 g((N + 31) / 32, (N + 63) / 64);
     Pieces o{{pieces[0], pieces[1], scheme == kHead3 ? pieces[2] : nullptr}};
-    L2Prefetch none{};
-    const L2Prefetch& p = pf ? *pf : none;
     if (scheme == kHiLo)
-        k_split_dham<kHiLo><<<g, b, 0, st>>>(N, S, dv, scale, bf16, o, ld_out, nullptr, err, p);
+        k_split_dham<kHiLo><<<g, b, 0, st>>>(N, S, dv, scale, bf16, o, ld_out, nullptr, err);
     else
-        k_split_dham<kHead3><<<g, b, 0, st>>>(N, S, dv, scale, bf16, o, ld_out, dyn, err, p);
+        k_split_dham<kHead3><<<g, b, 0, st>>>(N, S, dv, scale, bf16, o, ld_out, dyn, err);
 }
 
 }  // namespace tc

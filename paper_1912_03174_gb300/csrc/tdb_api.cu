@@ -1098,16 +1098,6 @@ TensorStep tensor_step_args(Ctx& c, int cur, bool euler, int bn) {
         x.bytes[r] = NN4;
     }
     x.parts = ((N + bn - 1) / bn) * ((N + 127) / 128) * ts.x_parts;
-    // the split of delta H prefetches the delta-M product's constant operands
-    L2Prefetch& sp = ts.split.pf;
-    sp.n = 0;
-    for (int q = 0; q < c.npieces; ++q) {
-        sp.ptr[sp.n] = c.pc_sinv[q];
-        sp.bytes[sp.n++] = sizeof(uint16_t) * (size_t)N * Np;
-    }
-    sp.ptr[sp.n] = c.Mgs_f;
-    sp.bytes[sp.n++] = NN4;
-    sp.parts = tc::split_dham_blocks(N);
     return ts;
 }
 
@@ -1163,7 +1153,7 @@ tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* t
         MARK("split_dH");
         tc::launch_split_dham(c.scheme, ts.split.N, ts.split.S, ts.split.dv, ts.split.scale,
                               ts.split.bf16, ts.split.out, ts.split.ld_out, ts.split.dyn, c.stream,
-                              ts.split.err, &ts.split.pf);
+                              ts.split.err);
         ++n;
         MARK("tc_gemm_dM");
         CK(tc::launch(c.scheme, c.maps_dm, ts.dm, 1, c.stream, 64));

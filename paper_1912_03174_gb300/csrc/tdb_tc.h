@@ -108,7 +108,7 @@ struct DynScales {
 };
 void launch_split_dham(int scheme, int N, const float* S, const float* dv, float scale, int bf16,
                        uint16_t* const* pieces, int ld_out, DynScales* dyn, cudaStream_t st,
-                       int* err, const L2Prefetch* pf = nullptr);
+                       int* err);
 // The same for many contexts in one launch: block b runs block work[b].y (of
 // split_dham_blocks(N) per problem) of args[work[b].x].
 struct SplitDhArgs {
@@ -119,7 +119,6 @@ struct SplitDhArgs {
     uint16_t* out[3];
     DynScales* dyn;
     int* err;
-    L2Prefetch pf;     // the delta-M product's constant operands, prefetched by the split
 };
 SplitDhArgs split_dham_args(int scheme, int N, const float* S, const float* dv, float scale,
                             int bf16, uint16_t* const* pieces, int ld_out, DynScales* dyn, int* err);
