@@ -190,13 +190,30 @@ def test_invariant_monitor_flags_a_corrupted_state(B):
         p.observables()                     # still readable
 
 
-def test_c2_flake_full_size_prefix_fp64(B):
-    # the N = 1024 SCC flake at its full size: a 10-step prefix against the oracle
+_C2_ORACLE = {}
+
+
+@pytest.mark.parametrize("form,tol", [("fp64", 1e-10), ("fp16x6", 1e-6)])
+def test_c2_flake_full_size_prefix(B, form, tol):
+    # the N = 1024 SCC flake at its full size, in the bench's launch configuration (FP16X6:
+    # 176-wide X tiles, the width the tuner picks there): a 12-step prefix against the oracle
+    # (the oracle run is shared by both forms)
     sysm, run = I.flake_c2()
-    n = 10
-    g = _gpu_run(B, sysm, run, n)
-    rho0, gs, tr = _oracle(sysm, run, n)
-    _compare(g, rho0, tr, n, tol_rho=1e-10, tol_mu=1e-10)
+    n = 12
+    if form == "fp16x6":
+        with B.Propagator(sysm, run, form) as p:
+            B.tdb_set_x_tile(p.ctx, 176)
+            p.setup()
+            rho0 = B.tdb_get_rho(p.ctx)
+            p.step(n)
+            g = dict(rho0=rho0, hist=B.tdb_dipole_history(p.ctx, n), obs=p.observables())
+            g["rho"], g["prev"] = B.tdb_get_rho(p.ctx, prev=True)
+    else:
+        g = _gpu_run(B, sysm, run, n)
+    if not _C2_ORACLE:
+        _C2_ORACLE["r"] = _oracle(sysm, run, n)
+    rho0, gs, tr = _C2_ORACLE["r"]
+    _compare(g, rho0, tr, n, tol_rho=tol, tol_mu=tol)
 
 
 # reduced-precision forms: (form, dipole tolerance in a.u., rho tolerance)
