@@ -557,7 +557,7 @@ LevelArgs level_args(Ctx& c) {
 
 // Reduced forms: partials and operands of rho_n from the master, then the evaluation of
 // both levels (Tr(rho S) of rho_{n-1}; charges, potential, dipole and trace of rho_n), with
-// the arithmetic the update's tail uses, so that a loaded state continues bit for bit.
+// the kernels a step uses after its update, so that a loaded state continues bit for bit.
 // With `restored` (FP16X6 resuming from a checkpoint of the same form) the scales saved
 // with the state are kept.
 tdb_status derived_from_master(Ctx& c, bool restored = false) {
@@ -1108,8 +1108,8 @@ tdb_status enqueue_step(Ctx& c, int cur, bool euler, int* launches, StepTimer* t
     const double* bim = euler ? c.rho_im[cur] : c.rho_im[prv];
     int n = 0;
     if (!mixed(c)) {
-        // charges and SCC potential of rho_n (the reduced forms evaluate the new level in the
-        // update's tail, and the current one after a ground state, kick or state load)
+        // charges and SCC potential of rho_n (the reduced forms evaluate the new level after
+        // the update, and the current one after a ground state, kick or state load)
         MARK("charges");
         launch_charges(c, c.partial, c.q, c.dq, c.stream);
         ++n;
