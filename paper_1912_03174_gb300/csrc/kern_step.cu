@@ -1138,7 +1138,6 @@ __device__ __forceinline__ void update_df_block(const UpdateDfArgs& A, int b) {
             }
         }
     }
-    if (A.early_dependents) pdl_launch_dependents();
     // X, the scalars and the outputs belong to the previous kernels from here on
     pdl_wait();
     __shared__ float xr_ij[kTile][kTile + 1], xi_ij[kTile][kTile + 1];
@@ -1461,16 +1460,6 @@ UpdateDfArgs update_df_args(const Ctx& c, const MasterPtrs& base, const MasterPt
     UpdateDfArgs a{};
     a.N = c.N;
     a.nct = c.nct;
-    // four resident blocks per SM: with one wave of tile pairs the charge kernel's blocks
-    // can wait in the free slots instead of being launched after the update
-    static int n_sm = 0;
-    if (!n_sm) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            n_sm = -1;
-    }
-    a.early_dependents = n_sm > 0 && c.nct * (c.nct + 1) / 2 + level_blocks(c.nat) <= 4 * n_sm;
     a.out_slot = out.re_hi == c.ms[0].re_hi ? 0 : 1;
     a.base = base;
     a.out = out;

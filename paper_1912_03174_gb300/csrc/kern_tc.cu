@@ -408,9 +408,11 @@ __device__ __forceinline__ void split_dham_block(int N, const float* __restrict_
                                                  int bf16, const Pieces& out, int ld_out,
                                                  const DynScales* __restrict__ dyn, int* err,
                                                  int bx, int by, int gy) {
-    // the delta-M product may be scheduled now: its CTAs set up their barriers and tensor
-    // memory and load M_gs while this kernel runs, then wait for it
-    pdl_launch_dependents();
+    // FP16X6: the delta-M product may be scheduled now (its CTAs set up their barriers and
+    // tensor memory and load M_gs while this kernel runs, then wait for it).  Its CTAs cannot
+    // share an SM with this kernel's, so they start as SMs drain; the smaller two-piece CTAs
+    // can, and slowed the split (measured: FP16X6 +1.6%, BF16X3 -7% steps/s)
+    if (SCHEME == kHead3) pdl_launch_dependents();
     const int c = bx * blockDim.x + threadIdx.x;
     const int r = by * blockDim.y + threadIdx.y;
     // FP16X6: the scale of this step, pscale(max |dv|), written with dv by the evaluation

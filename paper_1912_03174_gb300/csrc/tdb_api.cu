@@ -2432,7 +2432,6 @@ tdb_status batch_layout(tdb_batch& b, int bn, int schedule) {
             dm[g].push_back(grouped(c.maps_dm, ts.dm, c.N, 64, 1));
             xg[g].push_back(grouped(mx, ts.x, c.N, bn, ts.x_parts));
             upd[g].push_back(ts.upd);
-            upd[g].back().early_dependents = 0;   // the grouped grid may span several waves
             LevelFinalArgs f{};
             f.lv = ts.upd.lv;
             f.slot = ts.upd.out_slot;

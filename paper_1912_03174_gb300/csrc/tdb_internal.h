@@ -253,8 +253,7 @@ void launch_vv(const Ctx& c, const double* F, cudaStream_t st);
 // reduced-precision master (kern_step.cu)
 // Arguments of one update of the reduced forms (one problem of a grouped launch).
 struct UpdateDfArgs {
-    int N, nct, out_slot;
-    int early_dependents;      // the grid fits one wave: let the next kernel be scheduled at once
+    int N, nct, out_slot, pad;
     MasterPtrs base, out;
     float fh, fl;
     double factor;
