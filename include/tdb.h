@@ -247,10 +247,10 @@ tdb_status tdb_step_batch(tdb_ctx* const* ctxs, int count, long n);
 /* A grouped batch: count independent contexts of one tensor-core form (TDB_BF16X3,
  * TDB_FP16X3 or TDB_FP16X6), frozen nuclei, one time step, each after its ground state
  * (the probe runs of a pump-probe scan, Sec. 3.2, branched with tdb_clone).  Every phase of
- * a step (delta H pieces, delta M = S^-1 delta H, X = M rho, the update with the charges,
- * potential and dipole of the new level) is one launch over all contexts, whatever their
+ * a step (delta H pieces, delta M = S^-1 delta H, X = M rho, the update, the charges of the
+ * new level, its potential and dipole) is one launch over all contexts, whatever their
  * sizes: per-context tensor maps and arguments live in device arrays, a work list maps each
- * block to (context, tile), and the four launches of a step are one CUDA graph.  Creating
+ * block to (context, tile), and the six launches of a step are one CUDA graph.  Creating
  * the batch runs an autotuner over the X tile width (128, 176, 256) and the schedule (the
  * contexts in the given order, or the largest first) on the contexts' current operands;
  * the choice changes the time, not the result.  Each context keeps its own state, stream
