@@ -18,7 +18,7 @@ What it computes, following the paper (Bonafe et al., arXiv 1912.03174):
                        polarizability along the delay axis
 * Sec. 3.3, eq:deltaa  Delta A(tau) = A(tau) - A(t_p)
 
-Readings where the paper leaves the discrete form open (listed in the design doc as well):
+Readings where the paper leaves the discrete form open:
 
 * The Fourier transform of a sampled signal x_n = x(n dt), n = 0..K-1, is the rectangle
   rule with the damping inside: F(w) = dt sum_n x_n exp(-n dt / tau_damp) exp(+i w n dt).
