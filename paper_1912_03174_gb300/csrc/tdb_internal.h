@@ -50,8 +50,8 @@ struct DevScalars {
 
 // Per-level evaluation of the reduced-precision forms: the Mulliken charges of a master
 // level and what follows from them (SCC potential, dipole, trace), evaluated in FP32-pair
-// arithmetic.  Row-tile stage (one block per 32-row tile): deviation charges of the tile's
-// atoms and their partial potentials; final stage (one block): sums over the tiles.
+// arithmetic by two kernels: the charges (k_level_dq, from the row partials) and the
+// potentials with the level's scalars (k_level_final).
 struct LevelArgs {
     int nat, nper, nct, scc;
     const float2* partial;     // [N][nct] Mulliken row partials of the deviation (hi, lo)
